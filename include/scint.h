@@ -1,0 +1,189 @@
+/*
+ * scint.h -- C ABI of the GB300 Fresnel-scintillation library (libscint.so).
+ *
+ * The library computes the data-parallel hot path of the optical interstellar
+ * scintillation simulation of Habibi, Moniez, Ansari & Rahvar (A&A 2013,
+ * arXiv:1301.0514): a power-law phase screen synthesised from seeded Gaussian
+ * noise (Sect. 3.1, Eq. spectre, Eq. densite), its Fresnel propagation to the
+ * observer plane (Eq. hxy) with the edge taper of Sect. 3.2.1, the intensity
+ * |A|^2 co-added over a passband (Sect. 3.2.4), smoothed by the projected
+ * stellar disk (Sect. 3.2.3, Eq. iprh), and sampled along straight tracks
+ * (Sect. 3.3), plus the modulation index m = sigma_I / mean(I) (Sect. 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grids are square, N x N, N a power of two; arrays are row-major with the
+ *    row index y: element (y, x) sits at [y * N + x].  Pixel (ix, iy) has its
+ *    centre at ((ix + 1/2) Delta, (iy + 1/2) Delta) on the screen.
+ *  - Lengths are in km, wavelengths in nm, distances in pc.
+ *  - Pointers named "device" must be CUDA device memory of the current device;
+ *    pointers named "host" are ordinary host memory read before the call
+ *    returns.  The caller owns every buffer it passes; the library never
+ *    frees or keeps caller memory past the call.
+ *  - Every call is asynchronous and ordered on `stream` (a cudaStream_t, NULL
+ *    for the legacy default stream).  Inputs are never modified unless the
+ *    argument is documented as in/out.
+ *  - Return value: SCINT_OK, or an error code; scint_last_error() then gives a
+ *    message for the calling thread.  Parameter errors are detected on the host
+ *    before anything is launched, so a failing call leaves outputs untouched.
+ *  - Workspace: entry points taking (workspace, workspace_bytes) need device
+ *    scratch memory.  Pass a device buffer of scint_workspace_bytes() bytes for
+ *    the call's parameters, or a smaller one (>= the minimum that call
+ *    reports), in which case wavelengths are processed in groups that fit.
+ *    Passing workspace == NULL makes the library use its own per-device pool,
+ *    grown with cudaMalloc on first need (not allowed inside stream capture).
+ */
+#ifndef SCINT_H
+#define SCINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SCINT_OK           0
+#define SCINT_EINVAL       1   /* invalid argument (checked on the host) */
+#define SCINT_ENOMEM       2   /* workspace too small or allocation failed */
+#define SCINT_ECUDA        3   /* a CUDA runtime call failed */
+#define SCINT_ETIMEOUT     4   /* a bounded device-side wait gave up */
+#define SCINT_EUNSUPPORTED 5   /* valid parameters this build does not support */
+
+#define SCINT_MAX_LAMBDA   128 /* wavelengths per passband call */
+#define SCINT_MIN_N        16
+#define SCINT_MAX_N        16384
+
+/*
+ * Parameters of one screen and observation.
+ *   n                 grid size N (power of two, SCINT_MIN_N..SCINT_MAX_N)
+ *   pixel_km          pixel side Delta_1 (km)
+ *   r_diff_km         diffraction radius R_diff at lambda_ref_nm (Eq. dphi)
+ *   beta              spectral index of S_phi, 2 < beta < 4 (11/3 = Kolmogorov)
+ *   lambda_nm         wavelength of single-wavelength calls (and of the
+ *                     fiducial zone of scint_modulation_index)
+ *   lambda_ref_nm     wavelength at which the screen phase is defined; the
+ *                     phase at lambda is phi * lambda_ref / lambda (Eq. phiNl)
+ *   z_pc              screen-observer distance z_0
+ *   source_radius_km  projected source radius R_s (Eq. iprh); 0 = point source
+ *   margin_km         taper margin L_m of Sect. 3.2.1: < 0 selects the default
+ *                     min(10 R_F(lambda), L/4); 0 switches the taper off
+ *   seed, screen_id   select the Philox4x32-10 noise stream of the screen
+ */
+typedef struct scint_params {
+    int32_t  n;
+    int32_t  reserved0;        /* must be 0 */
+    double   pixel_km;
+    double   r_diff_km;
+    double   beta;
+    double   lambda_nm;
+    double   lambda_ref_nm;
+    double   z_pc;
+    double   source_radius_km;
+    double   margin_km;
+    uint64_t seed;
+    uint32_t screen_id;
+    uint32_t reserved1;        /* must be 0 */
+} scint_params;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int scint_version(void);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* scint_last_error(void);
+
+/* Device scratch bytes that the calls below need for grid p->n when a passband
+ * of n_lambda wavelengths is processed in one group (n_lambda >= 1). */
+size_t scint_workspace_bytes(const scint_params* p, int n_lambda);
+
+/*
+ * Phase screen synthesis (Sect. 3.1, Eq. spectre, Eq. densite).
+ * For every FFT bin k (row ky, column kx) draws two normals from
+ * Philox4x32-10 with counter (kx, ky, screen_id, 0) and key (seed low word,
+ * seed high word) by the Box-Muller transform, forms
+ *   F_k = sqrt(L^2 S_phi(q_k)) (g_re + i g_im) / sqrt(2),  F_0 = 0,
+ * and writes phi_j = sqrt(2)/L^2 Re sum_k F_k exp(+2 pi i k.x_j)  (radians, at
+ * lambda_ref).  The synthesis runs in FP64.
+ *   phi   device, N*N doubles, written.
+ * Needs workspace (16 N^2 bytes).
+ */
+int scint_make_screen(const scint_params* p, double* phi,
+                      void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Monochromatic point-source intensity at p->lambda_nm (Eq. hxy, Sect. 3.2.1):
+ *   A_in  = SF(x) SF(y) exp(i phi lambda_ref/lambda),
+ *   A_out = IDFT(DFT(A_in) H),  H(k) = exp(-i pi lambda z |k|^2),
+ *   I     = |A_out|^2   (1 for an unobstructed plane wave).
+ * The phase is reduced modulo 2 pi exactly (64-bit fixed point) before the
+ * FP32 sine/cosine; FFTs and intensity are FP32.
+ *   phi        device, N*N doubles (radians at lambda_ref), read.
+ *   intensity  device, N*N floats, written.
+ */
+int scint_propagate(const scint_params* p, const double* phi, float* intensity,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Passband co-addition (Sect. 3.2.4): intensity = sum_l w_l I(lambda_l) with
+ * the same screen phase scaled by lambda_ref/lambda_l.
+ *   lambdas_nm  host, n_lambda wavelengths (1..SCINT_MAX_LAMBDA).
+ *   weights     host, n_lambda weights, or NULL for 1/n_lambda each.
+ *   intensity   device, N*N floats, written (accumulate == 0) or added to
+ *               (accumulate != 0).
+ */
+int scint_sum_passband(const scint_params* p, const double* phi,
+                       const double* lambdas_nm, const double* weights, int n_lambda,
+                       float* intensity, int accumulate,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Extended source (Sect. 3.2.3, Eq. iprh): periodic convolution of the
+ * intensity with the uniform disk of radius p->source_radius_km, applied in
+ * Fourier space as K(q) = 2 J1(2 pi q R_s)/(2 pi q R_s).  R_s = 0 leaves the
+ * map unchanged.
+ *   intensity  device, N*N floats, in/out.
+ */
+int scint_smooth_source(const scint_params* p, float* intensity,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Light curves (Sect. 3.3): sample the map along straight tracks at constant
+ * speed, bilinear interpolation with periodic wrap.  Pixel (ix, iy) sits at
+ * integer coordinates (ix, iy).
+ *   tracks   host, n_tracks records of 4 doubles (x0, y0, theta, ds) in pixels
+ *            and radians; sample s is at (x0 + s ds cos theta, y0 + s ds sin theta).
+ *   curves   device, n_tracks * n_samples floats, written row by row.
+ */
+int scint_lightcurve(const scint_params* p, const float* intensity,
+                     const double* tracks, int n_tracks, int n_samples,
+                     float* curves, void* stream);
+
+/*
+ * Modulation index m = sigma_I / mean(I) (Sect. 4, population sigma) of a map
+ * over its fiducial zone: pixels whose centres are at least
+ * L_m + R_ref(lambda)/2 + R_s from every border (Sect. 3.2.1, 3.2.3), with
+ * lambda = p->lambda_nm and R_ref = lambda z / R_diff(lambda).  The whole map
+ * is used when the taper is off or that zone is empty.
+ *   out   device, 4 doubles written: m, mean, sigma, pixel count.
+ * Accumulation is FP64.  Needs workspace (a few KB).
+ */
+int scint_modulation_index(const scint_params* p, const float* intensity, double* out,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Modulation index of each light curve: out[c] = {m, mean, sigma} for curve c
+ * of curves (n_curves x n_samples, row-major).
+ *   out   device, 3 * n_curves doubles, written.
+ */
+int scint_curve_modulation(const float* curves, int n_curves, int n_samples,
+                           double* out, void* stream);
+
+/* Release the library's internal per-device workspace pools and tables. */
+void scint_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCINT_H */

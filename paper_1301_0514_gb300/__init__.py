@@ -1,0 +1,26 @@
+"""GB300-native Fresnel-scintillation library (Habibi et al. 2013, arXiv:1301.0514).
+
+The computation runs in libscint.so (hand-written CUDA for sm_103a) behind the
+C ABI of include/scint.h; this package only marshals arguments to it.
+"""
+from ._lib import (  # noqa: F401
+    MAX_LAMBDA,
+    ScintError,
+    ScintParams,
+    curve_modulation,
+    fft_lines,
+    lib,
+    lightcurve,
+    make_screen,
+    modulation_index,
+    noise_spectrum,
+    noise_words,
+    params,
+    propagate,
+    release,
+    smooth_source,
+    sum_passband,
+    workspace_bytes,
+)
+
+__version__ = "0.1.0"

@@ -1,0 +1,240 @@
+"""ctypes binding of libscint.so: argument marshalling only.
+
+Every function here forwards to the C entry point of the same name in
+include/scint.h (or include/scint_testing.h).  PyTorch supplies device memory,
+the current CUDA stream and workspace buffers; all computation happens in the
+library's CUDA kernels.  If the library is missing or fails to load, every
+call raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libscint.so")
+
+SCINT_OK = 0
+ERRORS = {1: "SCINT_EINVAL", 2: "SCINT_ENOMEM", 3: "SCINT_ECUDA", 4: "SCINT_ETIMEOUT", 5: "SCINT_EUNSUPPORTED"}
+MAX_LAMBDA = 128
+
+
+class ScintError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ScintParams(ctypes.Structure):
+    """Mirror of struct scint_params (include/scint.h)."""
+    _fields_ = [
+        ("n", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("pixel_km", ctypes.c_double),
+        ("r_diff_km", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("lambda_nm", ctypes.c_double),
+        ("lambda_ref_nm", ctypes.c_double),
+        ("z_pc", ctypes.c_double),
+        ("source_radius_km", ctypes.c_double),
+        ("margin_km", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("screen_id", ctypes.c_uint32),
+        ("reserved1", ctypes.c_uint32),
+    ]
+
+    def replace(self, **kw) -> "ScintParams":
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d.update(kw)
+        return ScintParams(**d)
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
+
+
+def params(n: int, pixel_km: float, r_diff_km: float, beta: float = 11.0 / 3.0, lambda_nm: float = 500.0,
+           lambda_ref_nm: Optional[float] = None, z_pc: float = 160.0, source_radius_km: float = 0.0,
+           seed: int = 0, screen_id: int = 0, margin_km: float = -1.0) -> ScintParams:
+    return ScintParams(n=n, reserved0=0, pixel_km=pixel_km, r_diff_km=r_diff_km, beta=beta,
+                       lambda_nm=lambda_nm, lambda_ref_nm=lambda_nm if lambda_ref_nm is None else lambda_ref_nm,
+                       z_pc=z_pc, source_radius_km=source_radius_km, margin_km=margin_km,
+                       seed=seed, screen_id=screen_id, reserved1=0)
+
+
+_lib = None
+_P = ctypes.POINTER(ScintParams)
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_i = ctypes.c_int
+
+
+def lib() -> ctypes.CDLL:
+    """Load libscint.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1301_0514_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "scint_version": ([], _i),
+        "scint_last_error": ([], ctypes.c_char_p),
+        "scint_workspace_bytes": ([_P, _i], _sz),
+        "scint_make_screen": ([_P, _vp, _vp, _sz, _vp], _i),
+        "scint_propagate": ([_P, _vp, _vp, _vp, _sz, _vp], _i),
+        "scint_sum_passband": ([_P, _vp, _vp, _vp, _i, _vp, _i, _vp, _sz, _vp], _i),
+        "scint_smooth_source": ([_P, _vp, _vp, _sz, _vp], _i),
+        "scint_lightcurve": ([_P, _vp, _vp, _i, _i, _vp, _vp], _i),
+        "scint_modulation_index": ([_P, _vp, _vp, _vp, _sz, _vp], _i),
+        "scint_curve_modulation": ([_vp, _i, _i, _vp, _vp], _i),
+        "scint_release": ([], None),
+        "scint_noise_words": ([_P, _vp, _vp], _i),
+        "scint_noise_spectrum": ([_P, _vp, _vp], _i),
+        "scint_fft_lines32": ([_i, _i, _vp, _i, _vp], _i),
+        "scint_fft_lines64": ([_i, _i, _vp, _i, _vp], _i),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != SCINT_OK:
+        raise ScintError(rc, lib().scint_last_error().decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t: torch.Tensor, dtype, numel: int, name: str):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+            and t.numel() == numel):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor with {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def workspace_bytes(p: ScintParams, n_lambda: int = 1) -> int:
+    return int(lib().scint_workspace_bytes(ctypes.byref(p), n_lambda))
+
+
+def _workspace(p: ScintParams, n_lambda: int, workspace, device):
+    if workspace is None:
+        workspace = torch.empty(workspace_bytes(p, n_lambda), dtype=torch.uint8, device=device)
+    return workspace, ctypes.c_void_p(workspace.data_ptr()), workspace.numel()
+
+
+def make_screen(p: ScintParams, out: Optional[torch.Tensor] = None, workspace=None, stream=None,
+                device="cuda") -> torch.Tensor:
+    if out is None:
+        out = torch.empty((p.n, p.n), dtype=torch.float64, device=device)
+    ws, wp, wb = _workspace(p, 1, workspace, out.device)
+    _check(lib().scint_make_screen(ctypes.byref(p), _dev(out, torch.float64, p.n * p.n, "phi"),
+                                   wp, wb, _stream(stream)))
+    return out
+
+
+def propagate(p: ScintParams, phi: torch.Tensor, out: Optional[torch.Tensor] = None, workspace=None,
+              stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty((p.n, p.n), dtype=torch.float32, device=phi.device)
+    ws, wp, wb = _workspace(p, 1, workspace, phi.device)
+    _check(lib().scint_propagate(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
+                                 _dev(out, torch.float32, p.n * p.n, "intensity"), wp, wb, _stream(stream)))
+    return out
+
+
+def sum_passband(p: ScintParams, phi: torch.Tensor, lambdas_nm: Sequence[float], weights=None,
+                 out: Optional[torch.Tensor] = None, accumulate: bool = False, workspace=None,
+                 stream=None) -> torch.Tensor:
+    lam = np.ascontiguousarray(lambdas_nm, dtype=np.float64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    if w is not None and w.shape != lam.shape:
+        raise ValueError("weights must match lambdas")
+    if out is None:
+        out = torch.empty((p.n, p.n), dtype=torch.float32, device=phi.device)
+    ws, wp, wb = _workspace(p, len(lam), workspace, phi.device)
+    _check(lib().scint_sum_passband(
+        ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
+        lam.ctypes.data_as(ctypes.c_void_p), None if w is None else w.ctypes.data_as(ctypes.c_void_p),
+        len(lam), _dev(out, torch.float32, p.n * p.n, "intensity"), int(bool(accumulate)), wp, wb,
+        _stream(stream)))
+    return out
+
+
+def smooth_source(p: ScintParams, intensity: torch.Tensor, workspace=None, stream=None) -> torch.Tensor:
+    ws, wp, wb = _workspace(p, 1, workspace, intensity.device)
+    _check(lib().scint_smooth_source(ctypes.byref(p), _dev(intensity, torch.float32, p.n * p.n, "intensity"),
+                                     wp, wb, _stream(stream)))
+    return intensity
+
+
+def lightcurve(p: ScintParams, intensity: torch.Tensor, tracks, n_samples: int,
+               out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    tr = np.ascontiguousarray(tracks, dtype=np.float64).reshape(-1, 4)
+    if out is None:
+        out = torch.empty((tr.shape[0], n_samples), dtype=torch.float32, device=intensity.device)
+    _check(lib().scint_lightcurve(ctypes.byref(p), _dev(intensity, torch.float32, p.n * p.n, "intensity"),
+                                  tr.ctypes.data_as(ctypes.c_void_p), tr.shape[0], n_samples,
+                                  _dev(out, torch.float32, tr.shape[0] * n_samples, "curves"),
+                                  _stream(stream)))
+    return out
+
+
+def modulation_index(p: ScintParams, intensity: torch.Tensor, out: Optional[torch.Tensor] = None,
+                     workspace=None, stream=None) -> torch.Tensor:
+    """Device tensor (m, mean, sigma, count) over the fiducial zone."""
+    if out is None:
+        out = torch.empty(4, dtype=torch.float64, device=intensity.device)
+    ws, wp, wb = _workspace(p, 1, workspace, intensity.device)
+    _check(lib().scint_modulation_index(ctypes.byref(p), _dev(intensity, torch.float32, p.n * p.n, "intensity"),
+                                        _dev(out, torch.float64, 4, "out"), wp, wb, _stream(stream)))
+    return out
+
+
+def curve_modulation(curves: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    nc, ns = curves.shape
+    if out is None:
+        out = torch.empty((nc, 3), dtype=torch.float64, device=curves.device)
+    _check(lib().scint_curve_modulation(_dev(curves, torch.float32, nc * ns, "curves"), nc, ns,
+                                        _dev(out, torch.float64, nc * 3, "out"), _stream(stream)))
+    return out
+
+
+def noise_words(p: ScintParams, stream=None, device="cuda") -> torch.Tensor:
+    out = torch.empty((p.n, p.n, 4), dtype=torch.int32, device=device)
+    _check(lib().scint_noise_words(ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def noise_spectrum(p: ScintParams, stream=None, device="cuda") -> torch.Tensor:
+    out = torch.empty((p.n, p.n), dtype=torch.complex128, device=device)
+    _check(lib().scint_noise_spectrum(ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def fft_lines(x: torch.Tensor, direction: int, stream=None) -> torch.Tensor:
+    """In-place line FFT of a contiguous (lines, n) complex64/complex128 CUDA tensor."""
+    if not (x.is_cuda and x.is_contiguous() and x.dim() == 2):
+        raise ValueError("x must be a contiguous 2-D CUDA tensor")
+    n_lines, n = x.shape
+    if x.dtype == torch.complex64:
+        _check(lib().scint_fft_lines32(n, direction, ctypes.c_void_p(x.data_ptr()), n_lines, _stream(stream)))
+    elif x.dtype == torch.complex128:
+        _check(lib().scint_fft_lines64(n, direction, ctypes.c_void_p(x.data_ptr()), n_lines, _stream(stream)))
+    else:
+        raise ValueError("complex64 or complex128 expected")
+    return x
+
+
+def release():
+    lib().scint_release()

@@ -1,0 +1,461 @@
+// C-ABI entry points: host-side parameter checks, derived physical scalars,
+// workspace carving and kernel sequencing.  Declarations and the contract of
+// every function are in include/scint.h and include/scint_testing.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/scint.h"
+#include "../../include/scint_testing.h"
+#include "kernels.cuh"
+
+namespace scint {
+cudaError_t launch_fft_lines32(int n, int dir, float2* data, int n_lines, const float2* tw, cudaStream_t s);
+cudaError_t launch_fft_lines64(int n, int dir, double2* data, int n_lines, const double2* tw, cudaStream_t s);
+}
+
+using namespace scint;
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return code;
+}
+
+int ok() {
+    g_error.clear();
+    return SCINT_OK;
+}
+
+#define SCINT_CUDA(call)                                                                      \
+    do {                                                                                      \
+        const cudaError_t e_ = (call);                                                        \
+        if (e_ == cudaErrorNotSupported)                                                      \
+            return fail(SCINT_EUNSUPPORTED, "%s: not supported for this grid size", #call);   \
+        if (e_ != cudaSuccess) return fail(SCINT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int check_params(const scint_params* p) {
+    if (!p) return fail(SCINT_EINVAL, "params is NULL");
+    if (!pow2(p->n) || p->n < SCINT_MIN_N || p->n > SCINT_MAX_N)
+        return fail(SCINT_EINVAL, "n=%d must be a power of two in [%d, %d]", p->n, SCINT_MIN_N, SCINT_MAX_N);
+    if (p->reserved0 || p->reserved1) return fail(SCINT_EINVAL, "reserved fields must be 0");
+    if (!(p->pixel_km > 0) || !std::isfinite(p->pixel_km)) return fail(SCINT_EINVAL, "pixel_km must be > 0");
+    if (!(p->r_diff_km > 0) || !std::isfinite(p->r_diff_km)) return fail(SCINT_EINVAL, "r_diff_km must be > 0");
+    if (!(p->beta > 2.0 && p->beta < 4.0)) return fail(SCINT_EINVAL, "beta=%g must be in (2, 4)", p->beta);
+    if (!(p->lambda_nm > 0) || !std::isfinite(p->lambda_nm)) return fail(SCINT_EINVAL, "lambda_nm must be > 0");
+    if (!(p->lambda_ref_nm > 0) || !std::isfinite(p->lambda_ref_nm))
+        return fail(SCINT_EINVAL, "lambda_ref_nm must be > 0");
+    if (!(p->z_pc > 0) || !std::isfinite(p->z_pc)) return fail(SCINT_EINVAL, "z_pc must be > 0");
+    if (!(p->source_radius_km >= 0) || !std::isfinite(p->source_radius_km))
+        return fail(SCINT_EINVAL, "source_radius_km must be >= 0");
+    if (!std::isfinite(p->margin_km)) return fail(SCINT_EINVAL, "margin_km must be finite");
+    if (p->margin_km > 0.5 * p->n * p->pixel_km) return fail(SCINT_EINVAL, "margin_km exceeds half the screen");
+    return SCINT_OK;
+}
+
+// ---- physics scalars (same formulas as the paper; units km) ----------------------
+double lz_km2(double lambda_nm, double z_pc) { return lambda_nm * kKmPerNm * z_pc * kKmPerPc; }
+double fresnel_radius(double lambda_nm, double z_pc) { return std::sqrt(lz_km2(lambda_nm, z_pc) / (2.0 * kPi)); }
+double screen_len(const scint_params* p) { return p->n * p->pixel_km; }
+// taper margin L_m (Sect. 3.2.1): default 10 R_F clamped to L/4
+double taper_margin(const scint_params* p, double lambda_nm) {
+    if (p->margin_km >= 0.0) return p->margin_km;
+    return std::fmin(10.0 * fresnel_radius(lambda_nm, p->z_pc), screen_len(p) / 4.0);
+}
+double diffraction_radius(const scint_params* p, double lambda_nm) {
+    return p->r_diff_km * std::pow(lambda_nm / p->lambda_ref_nm, 2.0 / (p->beta - 2.0));
+}
+double refraction_radius(const scint_params* p, double lambda_nm) {
+    return lz_km2(lambda_nm, p->z_pc) / diffraction_radius(p, lambda_nm);
+}
+double f_beta(double beta) {
+    return std::pow(2.0, -beta) * beta * std::tgamma(-beta / 2.0) / std::tgamma(beta / 2.0);
+}
+
+// ---- workspace ------------------------------------------------------------------
+constexpr size_t kAlign = 256;
+size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+
+size_t ws_synth(int n) { return up((size_t)n * 16) + up((size_t)n * n * 16); }
+size_t ws_prop(int n, int g) {
+    return up((size_t)n * 8) + up((size_t)g * n * 8) + up((size_t)g * n * 4) + up((size_t)g * n * n * 8);
+}
+size_t ws_smooth(int n) { return up((size_t)n * 8) + up((size_t)(n / 2 + 1) * n * 8); }
+size_t ws_moments() { return up((size_t)kMomentBlocks * 2 * sizeof(double)); }
+
+struct Carver {
+    char* base;
+    size_t size, used = 0;
+    template <typename T> T* take(size_t bytes) {
+        T* r = reinterpret_cast<T*>(base + used);
+        used += up(bytes);
+        return r;
+    }
+};
+
+// per-device pool used when the caller passes no workspace
+struct Pool {
+    std::mutex mu;
+    std::vector<void*> ptr;
+    std::vector<size_t> size;
+};
+Pool g_pool;
+
+int pool_get(size_t bytes, cudaStream_t stream, void** out) {
+    int dev = 0;
+    SCINT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_pool.mu);
+    if ((int)g_pool.ptr.size() <= dev) {
+        g_pool.ptr.resize(dev + 1, nullptr);
+        g_pool.size.resize(dev + 1, 0);
+    }
+    if (g_pool.size[dev] < bytes) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        SCINT_CUDA(cudaStreamIsCapturing(stream, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(SCINT_ENOMEM, "internal workspace must grow to %zu bytes during stream capture; "
+                                      "pass a workspace or call once before capturing", bytes);
+        if (g_pool.ptr[dev]) {
+            SCINT_CUDA(cudaDeviceSynchronize());
+            SCINT_CUDA(cudaFree(g_pool.ptr[dev]));
+            g_pool.ptr[dev] = nullptr;
+            g_pool.size[dev] = 0;
+        }
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SCINT_ENOMEM, "cudaMalloc of %zu bytes for the internal workspace failed", bytes);
+        }
+        g_pool.ptr[dev] = p;
+        g_pool.size[dev] = bytes;
+    }
+    *out = g_pool.ptr[dev];
+    return SCINT_OK;
+}
+
+// Resolve (workspace, bytes) against a requirement; NULL -> pool.
+int resolve_ws(void* ws, size_t bytes, size_t need, cudaStream_t s, Carver* c) {
+    if (!ws) {
+        const int rc = pool_get(need, s, &ws);
+        if (rc) return rc;
+        bytes = need;
+    } else if (bytes < need) {
+        return fail(SCINT_ENOMEM, "workspace of %zu bytes is smaller than the %zu bytes needed", bytes, need);
+    }
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign)
+        return fail(SCINT_EINVAL, "workspace must be %zu-byte aligned", kAlign);
+    *c = Carver{static_cast<char*>(ws), bytes};
+    return SCINT_OK;
+}
+
+// Propagate one wavelength group [l0, l0 + g) into the intensity map.
+int run_group(const scint_params* p, const double* phi, const double* lam, const double* wts,
+              int l0, int g, float* intensity, int accumulate, Carver& c, const float2* tw,
+              cudaStream_t s) {
+    const int n = p->n;
+    const double L = screen_len(p);
+    static_assert(kMaxLambda >= SCINT_MAX_LAMBDA, "lambda table size");
+    TableArgs ta{};
+    ta.n = n;
+    ta.count = g;
+    PropArgs pa{};
+    pa.n = n;
+    pa.phi = phi;
+    pa.tw = tw;
+    pa.lam.count = g;
+    for (int i = 0; i < g; ++i) {
+        const double l = lam[l0 + i];
+        ta.lz_over_2L2[i] = lz_km2(l, p->z_pc) / (2.0 * L * L);
+        ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
+        pa.lam.scale_fx[i] = (uint64_t)std::llround(p->lambda_ref_nm / l * 4294967296.0);
+        pa.lam.weight[i] = (float)wts[l0 + i];
+    }
+    Carver cg = c;   // group buffers restart at the same offset for every group
+    ta.h = cg.take<float2>((size_t)g * n * 8);
+    ta.sf = cg.take<float>((size_t)g * n * 4);
+    pa.h = ta.h;
+    pa.sf = ta.sf;
+    pa.work = cg.take<float2>((size_t)g * n * n * 8);
+    pa.intensity = intensity;
+    pa.accumulate = accumulate;
+    SCINT_CUDA(launch_prop_tables(ta, s));
+    SCINT_CUDA(launch_prop_rows(pa, s));
+    SCINT_CUDA(launch_prop_cols(pa, s));
+    return SCINT_OK;
+}
+
+int passband_impl(const scint_params* p, const double* phi, const double* lambdas, const double* weights,
+                  int n_lambda, float* intensity, int accumulate, void* ws, size_t ws_bytes,
+                  cudaStream_t s) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!phi || !intensity) return fail(SCINT_EINVAL, "phi and intensity must be device pointers");
+    if (!lambdas || n_lambda < 1 || n_lambda > SCINT_MAX_LAMBDA)
+        return fail(SCINT_EINVAL, "n_lambda=%d must be in [1, %d]", n_lambda, SCINT_MAX_LAMBDA);
+    std::vector<double> w(n_lambda, 1.0 / n_lambda);
+    for (int i = 0; i < n_lambda; ++i) {
+        if (!(lambdas[i] > 0) || !std::isfinite(lambdas[i])) return fail(SCINT_EINVAL, "lambda %d must be > 0", i);
+        if (weights) {
+            if (!std::isfinite(weights[i])) return fail(SCINT_EINVAL, "weight %d is not finite", i);
+            w[i] = weights[i];
+        }
+        if (taper_margin(p, lambdas[i]) > 0.5 * screen_len(p))
+            return fail(SCINT_EINVAL, "taper margin exceeds half the screen");
+    }
+    const int n = p->n;
+    // group size: all wavelengths if the workspace allows, else the largest that fits
+    int g = n_lambda;
+    if (ws) {
+        while (g > 1 && ws_prop(n, g) > ws_bytes) --g;
+    }
+    Carver c{};
+    rc = resolve_ws(ws, ws_bytes, ws_prop(n, g), s, &c);
+    if (rc) return rc;
+    float2* tw = c.take<float2>((size_t)n * 8);
+    SCINT_CUDA(launch_twiddles32(tw, n, s));
+    for (int l0 = 0; l0 < n_lambda; l0 += g) {
+        const int gg = std::min(g, n_lambda - l0);
+        rc = run_group(p, phi, lambdas, w.data(), l0, gg, intensity, accumulate || l0 > 0, c, tw, s);
+        if (rc) return rc;
+    }
+    return ok();
+}
+
+SynthArgs synth_args(const scint_params* p) {
+    SynthArgs a{};
+    const double L = screen_len(p);
+    const double rd = p->r_diff_km, beta = p->beta;
+    const double C = rd * rd / (2.0 * std::pow(2.0 * kPi, beta - 1.0) * f_beta(beta));
+    a.n = p->n;
+    a.screen_id = p->screen_id;
+    a.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);
+    a.key1 = (uint32_t)(p->seed >> 32);
+    // sigma_k = sqrt(L^2 S(q_k)) with q_k = sqrt(m2)/L, times the 1/sqrt(2) of Eq. densite
+    a.amp = L * std::sqrt(C) * std::pow(rd / L, -beta / 2.0) / std::sqrt(2.0);
+    a.neg_beta_4 = -beta / 4.0;
+    a.out_scale = std::sqrt(2.0) / (L * L);
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int scint_version(void) { return 100; }
+
+const char* scint_last_error(void) { return g_error.c_str(); }
+
+size_t scint_workspace_bytes(const scint_params* p, int n_lambda) {
+    if (check_params(p) || n_lambda < 1) return 0;
+    const int n = p->n;
+    size_t b = ws_synth(n);
+    b = std::max(b, ws_prop(n, std::min(n_lambda, SCINT_MAX_LAMBDA)));
+    b = std::max(b, ws_smooth(n));
+    b = std::max(b, ws_moments());
+    return b;
+}
+
+int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_t workspace_bytes,
+                      void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!phi) return fail(SCINT_EINVAL, "phi must be a device pointer");
+    if (p->n > 8192) return fail(SCINT_EUNSUPPORTED, "screen synthesis supports n <= 8192 in this build");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Carver c{};
+    rc = resolve_ws(workspace, workspace_bytes, ws_synth(p->n), s, &c);
+    if (rc) return rc;
+    SynthArgs a = synth_args(p);
+    a.tw = c.take<double2>((size_t)p->n * 16);
+    a.work = c.take<double2>((size_t)p->n * p->n * 16);
+    a.phi = phi;
+    SCINT_CUDA(launch_twiddles64(const_cast<double2*>(a.tw), p->n, s));
+    SCINT_CUDA(launch_synth(a, s));
+    return ok();
+}
+
+int scint_propagate(const scint_params* p, const double* phi, float* intensity, void* workspace,
+                    size_t workspace_bytes, void* stream) {
+    if (!p) return fail(SCINT_EINVAL, "params is NULL");
+    const double lam = p->lambda_nm, w = 1.0;
+    return passband_impl(p, phi, &lam, &w, 1, intensity, 0, workspace, workspace_bytes,
+                         static_cast<cudaStream_t>(stream));
+}
+
+int scint_sum_passband(const scint_params* p, const double* phi, const double* lambdas_nm,
+                       const double* weights, int n_lambda, float* intensity, int accumulate,
+                       void* workspace, size_t workspace_bytes, void* stream) {
+    return passband_impl(p, phi, lambdas_nm, weights, n_lambda, intensity, accumulate, workspace,
+                         workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int scint_smooth_source(const scint_params* p, float* intensity, void* workspace, size_t workspace_bytes,
+                        void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!intensity) return fail(SCINT_EINVAL, "intensity must be a device pointer");
+    if (p->source_radius_km == 0.0) return ok();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Carver c{};
+    rc = resolve_ws(workspace, workspace_bytes, ws_smooth(p->n), s, &c);
+    if (rc) return rc;
+    SmoothArgs a{};
+    a.n = p->n;
+    a.radius_over_L = p->source_radius_km / screen_len(p);
+    float2* tw = c.take<float2>((size_t)p->n * 8);
+    a.tw = tw;
+    a.spec = c.take<float2>((size_t)(p->n / 2 + 1) * p->n * 8);
+    a.intensity = intensity;
+    SCINT_CUDA(launch_twiddles32(tw, p->n, s));
+    SCINT_CUDA(launch_smooth(a, s));
+    return ok();
+}
+
+int scint_lightcurve(const scint_params* p, const float* intensity, const double* tracks, int n_tracks,
+                     int n_samples, float* curves, void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!intensity || !curves) return fail(SCINT_EINVAL, "intensity and curves must be device pointers");
+    if (n_tracks < 0 || n_samples < 0) return fail(SCINT_EINVAL, "negative track or sample count");
+    if (n_tracks > 0 && !tracks) return fail(SCINT_EINVAL, "tracks is NULL");
+    for (int i = 0; i < 4 * n_tracks; ++i)
+        if (!std::isfinite(tracks[i])) return fail(SCINT_EINVAL, "track parameters must be finite");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int t0 = 0; t0 < n_tracks; t0 += kTracksPerLaunch) {
+        CurveArgs a{};
+        a.n = p->n;
+        a.n_tracks = std::min(kTracksPerLaunch, n_tracks - t0);
+        a.n_samples = n_samples;
+        a.intensity = intensity;
+        a.curves = curves + (size_t)t0 * n_samples;
+        for (int i = 0; i < a.n_tracks; ++i) {
+            const double* tr = tracks + 4 * (t0 + i);
+            a.tr[i] = Track{tr[0], tr[1], std::cos(tr[2]), std::sin(tr[2]), tr[3]};
+        }
+        SCINT_CUDA(launch_lightcurve(a, s));
+    }
+    return ok();
+}
+
+int scint_modulation_index(const scint_params* p, const float* intensity, double* out, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!intensity || !out) return fail(SCINT_EINVAL, "intensity and out must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Carver c{};
+    rc = resolve_ws(workspace, workspace_bytes, ws_moments(), s, &c);
+    if (rc) return rc;
+    const int n = p->n;
+    int i0 = 0, i1 = n;
+    if (p->margin_km != 0.0) {
+        // fiducial zone: pixel centres at least L_m + R_ref/2 + R_s from both borders
+        const double L = screen_len(p);
+        const double m = taper_margin(p, p->lambda_nm) + 0.5 * refraction_radius(p, p->lambda_nm) +
+                         p->source_radius_km;
+        int a = -1, b = -1;
+        for (int i = 0; i < n; ++i) {
+            const double x = (i + 0.5) * p->pixel_km;
+            if (x >= m && x <= L - m) {
+                if (a < 0) a = i;
+                b = i;
+            }
+        }
+        if (a >= 0) {
+            i0 = a;
+            i1 = b + 1;
+        }
+    }
+    double* partial = c.take<double>((size_t)kMomentBlocks * 2 * sizeof(double));
+    SCINT_CUDA(launch_map_moments(intensity, n, i0, i1, i0, i1, partial, out, s));
+    return ok();
+}
+
+int scint_curve_modulation(const float* curves, int n_curves, int n_samples, double* out, void* stream) {
+    if (n_curves < 0 || n_samples < 1) return fail(SCINT_EINVAL, "need n_curves >= 0 and n_samples >= 1");
+    if (n_curves > 0 && (!curves || !out)) return fail(SCINT_EINVAL, "curves and out must be device pointers");
+    SCINT_CUDA(launch_curve_moments(curves, n_curves, n_samples, out, static_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+void scint_release(void) {
+    std::lock_guard<std::mutex> lk(g_pool.mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t d = 0; d < g_pool.ptr.size(); ++d) {
+        if (g_pool.ptr[d]) {
+            cudaSetDevice((int)d);
+            cudaDeviceSynchronize();
+            cudaFree(g_pool.ptr[d]);
+            g_pool.ptr[d] = nullptr;
+            g_pool.size[d] = 0;
+        }
+    }
+    cudaSetDevice(cur);
+}
+
+// ---- inspection entry points ----------------------------------------------------
+int scint_noise_words(const scint_params* p, uint32_t* words, void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!words) return fail(SCINT_EINVAL, "words must be a device pointer");
+    SCINT_CUDA(launch_noise_words(p->n, p->screen_id, (uint32_t)(p->seed & 0xFFFFFFFFu),
+                                  (uint32_t)(p->seed >> 32), words, static_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int scint_noise_spectrum(const scint_params* p, double* F, void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!F) return fail(SCINT_EINVAL, "F must be a device pointer");
+    SCINT_CUDA(launch_noise_spectrum(synth_args(p), reinterpret_cast<double2*>(F),
+                                     static_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int scint_fft_lines32(int n, int dir, float* data, int n_lines, void* stream) {
+    if (!pow2(n) || n < SCINT_MIN_N || n > SCINT_MAX_N) return fail(SCINT_EINVAL, "bad n=%d", n);
+    if (dir != -1 && dir != 1) return fail(SCINT_EINVAL, "dir must be -1 or +1");
+    if (!data || n_lines < 0) return fail(SCINT_EINVAL, "bad data or n_lines");
+    if (n_lines == 0) return ok();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* ws = nullptr;
+    int rc = pool_get(up((size_t)n * 8), s, &ws);
+    if (rc) return rc;
+    float2* tw = static_cast<float2*>(ws);
+    SCINT_CUDA(launch_twiddles32(tw, n, s));
+    SCINT_CUDA(launch_fft_lines32(n, dir, reinterpret_cast<float2*>(data), n_lines, tw, s));
+    return ok();
+}
+
+int scint_fft_lines64(int n, int dir, double* data, int n_lines, void* stream) {
+    if (!pow2(n) || n < SCINT_MIN_N || n > SCINT_MAX_N) return fail(SCINT_EINVAL, "bad n=%d", n);
+    if (dir != -1 && dir != 1) return fail(SCINT_EINVAL, "dir must be -1 or +1");
+    if (!data || n_lines < 0) return fail(SCINT_EINVAL, "bad data or n_lines");
+    if (n_lines == 0) return ok();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* ws = nullptr;
+    int rc = pool_get(up((size_t)n * 16), s, &ws);
+    if (rc) return rc;
+    double2* tw = static_cast<double2*>(ws);
+    SCINT_CUDA(launch_twiddles64(tw, n, s));
+    SCINT_CUDA(launch_fft_lines64(n, dir, reinterpret_cast<double2*>(data), n_lines, tw, s));
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// Shared-memory Stockham FFT for one line of N points held by a team of
+// threads (FP32 float2 or FP64 double2).
+//
+// A team of T = N/E threads (E = 16 or 32) transforms one line; thread t holds the E values at
+// positions t + m*T (m = 0..E-1) in registers, both on entry and on exit (the
+// Stockham autosort keeps that distribution, so a forward transform, a pointwise
+// multiply and an inverse transform chain with no extra data movement).
+//
+// Radix plan: the first stage is radix 16 (or N for N < 16), then radix-16
+// stages, then one radix 2/4/8 stage for the remaining bits.  Between stages the
+// line goes through the team's shared-memory buffer, padded by one element per
+// 16 so that the stride-16 stores of the first stage are bank-conflict free.
+//
+// Stage s with radix R and span P (product of the radices before it) computes,
+// for each butterfly i in [0, N/R):  k = i mod P,
+//   u_r = x[i + r N/R] * W_{PR}^{r k},  y = DFT_R(u),  out[(i/P) P R + k + r P] = y_r.
+// DIR = -1 is the forward transform exp(-2 pi i k x / N); DIR = +1 the inverse
+// (unnormalised).  Twiddles come from a table tw[j] = exp(-2 pi i j / N).
+#pragma once
+
+#include "common.cuh"
+
+namespace scint {
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
+
+// cos(2 pi j / 16) for any integer j; sin(2 pi j/16) = cos(2 pi (j-4)/16)
+__host__ __device__ constexpr double cos16(int j) {
+    switch (((j % 16) + 16) % 16) {
+        case 0: return 1.0;
+        case 1: return 0.92387953251128675613;
+        case 2: return 0.70710678118654752440;
+        case 3: return 0.38268343236508977173;
+        case 4: return 0.0;
+        case 5: return -0.38268343236508977173;
+        case 6: return -0.70710678118654752440;
+        case 7: return -0.92387953251128675613;
+        case 8: return -1.0;
+        case 9: return -0.92387953251128675613;
+        case 10: return -0.70710678118654752440;
+        case 11: return -0.38268343236508977173;
+        case 12: return 0.0;
+        case 13: return 0.38268343236508977173;
+        case 14: return 0.70710678118654752440;
+        default: return 0.92387953251128675613;
+    }
+}
+
+// a * exp(DIR * 2 pi i J16 / 16), J16 a compile-time multiple of 1/16 turn
+template <int J16, int DIR, typename C>
+SCINT_DEV C rot16(C a) {
+    constexpr int j = ((J16 % 16) + 16) % 16;
+    using Rl = typename real_of<C>::type;
+    if constexpr (j == 0) {
+        return a;
+    } else if constexpr (j == 4) {
+        return mul_i<DIR>(a);
+    } else if constexpr (j == 8) {
+        return make_c<C>(0, 0) - a;
+    } else if constexpr (j == 12) {
+        return mul_i<-DIR>(a);
+    } else {
+        constexpr Rl c = (Rl)cos16(j);
+        constexpr Rl s = (Rl)(DIR * cos16(j - 4));
+        C r;
+        r.x = a.x * c - a.y * s;
+        r.y = a.x * s + a.y * c;
+        return r;
+    }
+}
+
+// ---- in-register DFTs, natural order in and out ---------------------------
+template <int DIR, typename C>
+SCINT_DEV void dft2(C& a, C& b) {
+    const C t = a - b;
+    a = a + b;
+    b = t;
+}
+
+template <int DIR, typename C>
+SCINT_DEV void dft4(C& a0, C& a1, C& a2, C& a3) {
+    const C t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3;
+    const C t3 = mul_i<DIR>(a1 - a3);
+    a0 = t0 + t2;
+    a2 = t0 - t2;
+    a1 = t1 + t3;
+    a3 = t1 - t3;
+}
+
+template <int R, int DIR, typename C>
+SCINT_DEV void dft(C* x) {
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) {
+        dft2<DIR>(x[0], x[1]);
+    } else if constexpr (R == 4) {
+        dft4<DIR>(x[0], x[1], x[2], x[3]);
+    } else if constexpr (R == 8) {
+        // n = n1 + 2 n2, k = 4 k1 + k2
+#pragma unroll
+        for (int n1 = 0; n1 < 2; ++n1) dft4<DIR>(x[n1], x[n1 + 2], x[n1 + 4], x[n1 + 6]);
+        x[3] = rot16<2, DIR>(x[3]);   // W8^1
+        x[5] = rot16<4, DIR>(x[5]);   // W8^2
+        x[7] = rot16<6, DIR>(x[7]);   // W8^3
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) dft2<DIR>(x[2 * k2], x[2 * k2 + 1]);
+        C y[8];
+#pragma unroll
+        for (int k1 = 0; k1 < 2; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) y[4 * k1 + k2] = x[k1 + 2 * k2];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = y[i];
+    } else if constexpr (R == 16) {
+        // n = n1 + 4 n2, k = 4 k1 + k2
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) dft4<DIR>(x[n1], x[n1 + 4], x[n1 + 8], x[n1 + 12]);
+        // a[n1][k2] sits at x[n1 + 4 k2]; multiply by W16^(n1 k2)
+        x[5] = rot16<1, DIR>(x[5]);
+        x[9] = rot16<2, DIR>(x[9]);
+        x[13] = rot16<3, DIR>(x[13]);
+        x[6] = rot16<2, DIR>(x[6]);
+        x[10] = rot16<4, DIR>(x[10]);
+        x[14] = rot16<6, DIR>(x[14]);
+        x[7] = rot16<3, DIR>(x[7]);
+        x[11] = rot16<6, DIR>(x[11]);
+        x[15] = rot16<9, DIR>(x[15]);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) dft4<DIR>(x[4 * k2], x[4 * k2 + 1], x[4 * k2 + 2], x[4 * k2 + 3]);
+        C y[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) y[4 * k1 + k2] = x[k1 + 4 * k2];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = y[i];
+    }
+}
+
+// ---- plan ----------------------------------------------------------------
+// EPT = values held per thread (16 or 32); each stage's butterflies are spread
+// over the T = N/E threads of the line, E/R butterflies per thread.
+template <int N, int EPT = 16>
+struct FftPlan {
+    static_assert(N >= 2 && (N & (N - 1)) == 0, "N must be a power of two");
+    static_assert(EPT == 16 || EPT == 32, "16 or 32 values per thread");
+    static constexpr int LOG2N = ilog2(N);
+    static constexpr int E = N < EPT ? N : EPT;          // values per thread
+    static constexpr int T = N / E;                      // threads per line
+    static constexpr int R0 = N < 16 ? N : 16;           // radix of the first stage
+    static constexpr int REST = LOG2N - ilog2(R0);
+    static constexpr int N16 = REST / 4;                 // radix-16 stages after the first
+    static constexpr int TAIL = REST % 4;                // bits of the last small stage
+    static constexpr int NSTAGE = 1 + N16 + (TAIL ? 1 : 0);
+    static constexpr int BUF = N + N / 16;               // padded buffer length
+    __host__ __device__ static constexpr int radix(int s) { return s == 0 ? R0 : (s <= N16 ? 16 : (1 << TAIL)); }
+    __host__ __device__ static constexpr int span(int s) { return s == 0 ? 1 : span(s - 1) * radix(s - 1); }
+};
+
+SCINT_DEV int pad16(int a) { return a + (a >> 4); }
+
+template <typename C>
+SCINT_DEV C ld_tw(const C* __restrict__ p) { return __ldg(p); }
+
+template <typename C, int N, int DIR, int EPT, int S>
+SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw) {
+    using Pl = FftPlan<N, EPT>;
+    constexpr int E = Pl::E, T = Pl::T;
+    constexpr int R = Pl::radix(S), P = Pl::span(S), NB = E / R;
+    constexpr bool FIRST = (S == 0), LAST = (S == Pl::NSTAGE - 1);
+    C u[E];
+    if constexpr (FIRST) {
+        // butterfly b takes positions t + b T + r N/R = t + (b + r NB) T
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[b * R + r] = v[b + r * NB];
+    } else {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            // N/R is a multiple of 16 here, so pad16(i + r N/R) = pad16(i) + r (N/R)(17/16)
+            const C* src = buf + pad16(t + b * T);
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[b * R + r] = src[r * ((N / R) + (N / R) / 16)];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int i = t + b * T;
+        if constexpr (!FIRST) {
+            const int k = i & (P - 1);
+            const int step = k * (N / (P * R));      // W_{PR}^{r k} = tw[r * step]
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const C w = ld_tw(tw + r * step);
+                u[b * R + r] = DIR < 0 ? cmul(u[b * R + r], w) : cmulc(u[b * R + r], w);
+            }
+        }
+        dft<R, DIR>(&u[b * R]);
+    }
+    if constexpr (LAST) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b + r * NB] = u[b * R + r];
+    } else {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int i = t + b * T;
+            const int k = i & (P - 1);
+            const int j = (i - k) * R + k;
+            // P >= 16: pad16(j + r P) = pad16(j) + r P (17/16); P == 1: j = i R and r < R <= 16
+            C* dst = buf + pad16(j);
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[P >= 16 ? r * (P + P / 16) : r] = u[b * R + r];
+        }
+        __syncthreads();
+        fft_stage<C, N, DIR, EPT, S + 1>(v, buf, t, tw);
+    }
+}
+
+// Transform the team's line in place (registers v, distribution t + m*T).
+// Every thread of the block must call this the same number of times.
+template <typename C, int N, int DIR, int EPT = 16>
+SCINT_DEV void fft_line(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw) {
+    fft_stage<C, N, DIR, EPT, 0>(v, buf, t, tw);
+}
+
+}  // namespace scint

@@ -1,0 +1,108 @@
+// Internal launch interface between the C-ABI layer (api.cu) and the kernel
+// translation units.  Every launcher enqueues on `stream` and returns the
+// cudaError_t of the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace scint {
+
+constexpr int kMaxLambda = 128;
+
+// Line-tile sizes (complex elements staged in shared memory per block).
+constexpr int kTileRow32 = 4096;    // FP32 line passes over rows
+constexpr int kTileCol32 = 8192;    // FP32 line passes over columns
+constexpr int kTile64 = 4096;       // FP64 synthesis passes
+
+// Intermediates between a row pass and a column pass use the "strip layout":
+// element (y, x) of an N x N field sits at (x / W) * N * W + y * W + x % W, W the
+// number of columns one column-pass block holds, so that block reads one
+// contiguous strip.
+
+// -------- tables ------------------------------------------------------------
+// tw[j] = exp(-2 pi i j / n), j < n, rounded from FP64.
+cudaError_t launch_twiddles32(float2* tw, int n, cudaStream_t s);
+cudaError_t launch_twiddles64(double2* tw, int n, cudaStream_t s);
+
+// -------- synthesis (FP64) -------------------------------------------------
+struct SynthArgs {
+    int n;
+    uint32_t screen_id, key0, key1;
+    double amp;          // sigma(k) = amp * (mx^2 + my^2)^(-beta/4), includes 1/sqrt(2)
+    double neg_beta_4;   // -beta/4
+    double out_scale;    // sqrt(2) / L^2
+    const double2* tw;   // FP64 twiddles for n
+    double2* work;       // n*n complex128, strip layout
+    double* phi;         // n*n, row-major
+};
+cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s);
+
+// Test hooks: raw Philox words and the shaped spectrum F (row-major, FFT order).
+cudaError_t launch_noise_words(int n, uint32_t screen_id, uint32_t k0, uint32_t k1,
+                               uint32_t* words, cudaStream_t s);
+cudaError_t launch_noise_spectrum(const SynthArgs& a, double2* F, cudaStream_t s);
+
+// -------- propagation (FP32 with fixed-point phase reduction) --------------
+struct LambdaSet {
+    int count;                       // wavelengths in this group
+    uint64_t scale_fx[kMaxLambda];   // round(lambda_ref/lambda * 2^32)
+    float weight[kMaxLambda];        // passband weight w_l
+};
+
+struct PropArgs {
+    int n;
+    const double* phi;       // n*n radians at lambda_ref
+    const float2* tw;        // FP32 twiddles
+    const float2* h;         // per lambda: n entries exp(-i pi lambda z k^2) / n
+    const float* sf;         // per lambda: n taper values
+    float2* work;            // per lambda: n*n complex64, strip layout
+    float* intensity;        // n*n
+    int accumulate;          // add to intensity instead of overwriting
+    LambdaSet lam;
+};
+// h, sf tables for a wavelength group from host-side scalars.
+struct TableArgs {
+    int n, count;
+    double lz_over_2L2[kMaxLambda];   // lambda z / (2 L^2): H phase in turns per index^2
+    double margin_px[kMaxLambda];     // taper margin in pixels (0 = no taper)
+    float2* h;
+    float* sf;
+};
+cudaError_t launch_prop_tables(const TableArgs& a, cudaStream_t s);
+cudaError_t launch_prop_rows(const PropArgs& a, cudaStream_t s);
+cudaError_t launch_prop_cols(const PropArgs& a, cudaStream_t s);
+
+// -------- source smoothing ---------------------------------------------------
+struct SmoothArgs {
+    int n;
+    double radius_over_L;    // R_s / L: K depends on 2 pi R_s sqrt(mx^2 + my^2) / L
+    const float2* tw;
+    float2* spec;            // (n/2 + 1) x n complex64, row-major [ky][x]
+    float* intensity;        // n*n in/out
+};
+cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t s);
+
+// -------- observables --------------------------------------------------------
+struct Track { double x0, y0, c, s, ds; };
+constexpr int kTracksPerLaunch = 64;
+struct CurveArgs {
+    int n, n_tracks, n_samples;
+    const float* intensity;
+    float* curves;           // n_tracks * n_samples (this launch's slice)
+    Track tr[kTracksPerLaunch];
+};
+cudaError_t launch_lightcurve(const CurveArgs& a, cudaStream_t s);
+
+// FP64 moments of a rectangular region [r0, r1) x [c0, c1) of an n x n map;
+// out = {m, mean, sigma, count}.  partial: workspace of >= kMomentBlocks*2 doubles.
+constexpr int kMomentBlocks = 304;
+cudaError_t launch_map_moments(const float* map, int n, int r0, int r1, int c0, int c1,
+                               double* partial, double* out, cudaStream_t s);
+// per-curve {m, mean, sigma}
+cudaError_t launch_curve_moments(const float* curves, int n_curves, int n_samples,
+                                 double* out, cudaStream_t s);
+
+}  // namespace scint

@@ -1,0 +1,134 @@
+// Light curves (Sect. 3.3) and the modulation index m = sigma_I / mean(I) (Sect. 4).
+#include "kernels.cuh"
+
+namespace scint {
+
+// One thread per sample: bilinear interpolation with periodic wrap; positions
+// in FP64 so that the fractional offsets stay exact on large grids.
+__global__ void lightcurve_kernel(CurveArgs a) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (s >= a.n_samples || c >= a.n_tracks) return;
+    const Track tr = a.tr[c];
+    const double d = (double)s * tr.ds;
+    const double x = fma(d, tr.c, tr.x0);
+    const double y = fma(d, tr.s, tr.y0);
+    const double fx = floor(x), fy = floor(y);
+    const float tx = (float)(x - fx), ty = (float)(y - fy);
+    const int n = a.n;
+    long long ix = (long long)fx % n, iy = (long long)fy % n;
+    if (ix < 0) ix += n;
+    if (iy < 0) iy += n;
+    const int ix1 = (int)(ix + 1 == n ? 0 : ix + 1), iy1 = (int)(iy + 1 == n ? 0 : iy + 1);
+    const float* I = a.intensity;
+    const float i00 = __ldg(I + iy * n + ix), i01 = __ldg(I + iy * n + ix1);
+    const float i10 = __ldg(I + (size_t)iy1 * n + ix), i11 = __ldg(I + (size_t)iy1 * n + ix1);
+    const float top = fmaf(tx, i01 - i00, i00);
+    const float bot = fmaf(tx, i11 - i10, i10);
+    a.curves[(size_t)c * a.n_samples + s] = fmaf(ty, bot - top, top);
+}
+
+cudaError_t launch_lightcurve(const CurveArgs& a, cudaStream_t s) {
+    if (a.n_tracks <= 0 || a.n_samples <= 0) return cudaSuccess;
+    dim3 grid((a.n_samples + 255) / 256, a.n_tracks);
+    lightcurve_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// block-wide FP64 sum of two values (blockDim.x == 256)
+__device__ void block_sum2(double& a, double& b) {
+    __shared__ double sa[8], sb[8];
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = l < 8 ? sa[l] : 0.0;
+        b = l < 8 ? sb[l] : 0.0;
+        for (int o = 4; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+// Pass 1: each block sums a contiguous share of the region's rows.
+__global__ void __launch_bounds__(256) map_moments_kernel(const float* map, int n, int r0, int r1,
+                                                          int c0, int c1, double* partial) {
+    const int rows = r1 - r0, cols = c1 - c0;
+    const long long tot = (long long)rows * cols;
+    double s = 0.0, s2 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i % cols);
+        const double v = (double)__ldg(map + (size_t)(r0 + r) * n + c0 + c);
+        s += v;
+        s2 = fma(v, v, s2);
+    }
+    block_sum2(s, s2);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s;
+        partial[2 * blockIdx.x + 1] = s2;
+    }
+}
+
+// Pass 2: one block reduces the partial sums (fixed order: deterministic).
+__global__ void __launch_bounds__(256) moments_final_kernel(const double* partial, int nblocks,
+                                                            double count, double* out) {
+    double s = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+        s += partial[2 * i];
+        s2 += partial[2 * i + 1];
+    }
+    block_sum2(s, s2);
+    if (threadIdx.x == 0) {
+        const double mean = s / count;
+        const double var = fmax(s2 / count - mean * mean, 0.0);
+        const double sd = sqrt(var);
+        out[0] = sd / mean;
+        out[1] = mean;
+        out[2] = sd;
+        out[3] = count;
+    }
+}
+
+cudaError_t launch_map_moments(const float* map, int n, int r0, int r1, int c0, int c1,
+                               double* partial, double* out, cudaStream_t s) {
+    map_moments_kernel<<<kMomentBlocks, 256, 0, s>>>(map, n, r0, r1, c0, c1, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    moments_final_kernel<<<1, 256, 0, s>>>(partial, kMomentBlocks, (double)(r1 - r0) * (c1 - c0), out);
+    return cudaGetLastError();
+}
+
+// One block per curve.
+__global__ void __launch_bounds__(256) curve_moments_kernel(const float* curves, int n_samples,
+                                                            double* out) {
+    const float* c = curves + (size_t)blockIdx.x * n_samples;
+    double s = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < n_samples; i += blockDim.x) {
+        const double v = (double)c[i];
+        s += v;
+        s2 = fma(v, v, s2);
+    }
+    block_sum2(s, s2);
+    if (threadIdx.x == 0) {
+        const double mean = s / n_samples;
+        const double sd = sqrt(fmax(s2 / n_samples - mean * mean, 0.0));
+        out[3 * blockIdx.x] = sd / mean;
+        out[3 * blockIdx.x + 1] = mean;
+        out[3 * blockIdx.x + 2] = sd;
+    }
+}
+
+cudaError_t launch_curve_moments(const float* curves, int n_curves, int n_samples, double* out,
+                                 cudaStream_t s) {
+    if (n_curves <= 0) return cudaSuccess;
+    curve_moments_kernel<<<n_curves, 256, 0, s>>>(curves, n_samples, out);
+    return cudaGetLastError();
+}
+
+}  // namespace scint

@@ -1,0 +1,178 @@
+// Fresnel propagation of a phase screen by the transfer function (Eq. hxy)
+// with the edge taper of Sect. 3.2.1 and passband co-addition (Sect. 3.2.4).
+//
+// The transfer function H(k) = exp(-i pi lambda z (kx^2 + ky^2)) factors into
+// H_x(kx) H_y(ky), so the 2D propagator is a 1D propagator along x followed by
+// one along y.  Each 1D propagator is FFT -> multiply -> inverse FFT on a line
+// held in registers and shared memory, so a wavelength costs two HBM passes:
+//   row pass:    phi (read once per wavelength group) -> exact phase reduction
+//                -> sin/cos -> taper -> FFT_x -> H_x/N -> IFFT_x -> field (write)
+//   column pass: field (read) -> FFT_y -> H_y/N -> IFFT_y -> w |A|^2, summed over
+//                the group in registers -> intensity (one write per group)
+//
+// Phase reduction: phi is converted once per pixel to 64-bit fixed point in
+// turns, P = round(phi 2^32 / 2 pi); for each wavelength the low 64 bits of
+// P * round(s 2^32) (s = lambda_ref / lambda) are the fractional turns of
+// phi s scaled by 2^64, so the reduction modulo 2 pi is exact integer
+// arithmetic (error |phi s| 2^-33 / 2 pi turns from rounding s) and only the
+// reduced angle goes to the FP32 sine/cosine.
+#include "dispatch.cuh"
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace scint {
+
+template <int N> __host__ __device__ constexpr int prow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N ? kTileRow32 / N : N); }
+template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T; }
+template <int N> __host__ __device__ constexpr int pcol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N ? kTileCol32 / N : N); }
+constexpr int kColEPT = 16;   // values per thread in the column pass
+template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_lines<N>() * FftPlan<N, kColEPT>::T; }
+
+SCINT_DEV int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// ---- tables -----------------------------------------------------------------
+__global__ void prop_tables_kernel(TableArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = blockIdx.y;
+    if (i >= a.n) return;
+    const int n = a.n;
+    // H(k)/n with the phase in turns reduced in FP64 before sincospi
+    const double m = (double)sfreq(i, n);
+    const double turns = a.lz_over_2L2[l] * m * m;
+    const double fr = turns - rint(turns);
+    double s, c;
+    sincospi(-2.0 * fr, &s, &c);
+    a.h[(size_t)l * n + i] = make_float2((float)(c / n), (float)(s / n));
+    // raised-sine taper SF at the pixel centre (i + 1/2), symmetric about the centre
+    const double lm = a.margin_px[l];
+    double sf = 1.0;
+    if (lm > 0.0) {
+        const double u = fmin((double)i + 0.5, (double)n - (double)i - 0.5);
+        if (u <= lm) {
+            const double sn = sinpi(u / (2.0 * lm));
+            sf = sn * sn;
+        }
+    }
+    a.sf[(size_t)l * n + i] = (float)sf;
+}
+
+cudaError_t launch_prop_tables(const TableArgs& a, cudaStream_t s) {
+    dim3 grid((a.n + 255) / 256, a.count);
+    prop_tables_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---- row pass ------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
+prop_rows_kernel(PropArgs a) {
+    using Pl = FftPlan<N>;
+    constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), W = pcol_lines<N>();
+    extern __shared__ float2 smem32[];
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const int y = blockIdx.x * B + team;
+    float2* buf = smem32 + team * Pl::BUF;
+    // fixed-point phase of this thread's pixels, kept in shared memory across the
+    // wavelength loop (each thread reads back only the entries it wrote)
+    long long* P = reinterpret_cast<long long*>(smem32 + B * Pl::BUF) + team * N + t;
+    const double to_fixed = 4294967296.0 / (2.0 * kPi);
+#pragma unroll
+    for (int m = 0; m < E; ++m) P[m * T] = __double2ll_rn(a.phi[(size_t)y * N + t + m * T] * to_fixed);
+
+#pragma unroll 1
+    for (int l = 0; l < a.lam.count; ++l) {
+        const unsigned long long S = a.lam.scale_fx[l];
+        const float* sf = a.sf + (size_t)l * N;
+        const float2* h = a.h + (size_t)l * N;
+        const float sfy = sf[y];
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const unsigned long long prod = (unsigned long long)P[m * T] * S;   // frac(phi s) * 2^64
+            const float tt = (float)(int)(prod >> 32) * 0x1.0p-32f;          // turns in [-1/2, 1/2)
+            float sn, cs;
+            sincospif(2.0f * tt, &sn, &cs);
+            const float amp = sfy * __ldg(sf + t + m * T);
+            v[m] = make_float2(amp * cs, amp * sn);
+        }
+        fft_line<float2, N, -1>(v, buf, t, a.tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
+        fft_line<float2, N, +1>(v, buf, t, a.tw);
+        float2* dst = a.work + (size_t)l * N * N;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int x = t + m * T;
+            dst[(size_t)(x / W) * N * W + (size_t)y * W + (x % W)] = v[m];
+        }
+    }
+}
+
+// ---- column pass ---------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(pcol_threads<N>(), 1)
+prop_cols_kernel(PropArgs a) {
+    using Pl = FftPlan<N, kColEPT>;
+    constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>();
+    extern __shared__ float2 smem32[];
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int x = blockIdx.x * W + w;
+    float2* buf = smem32 + w * Pl::BUF;
+    // passband accumulator of this thread's pixels (own entries only)
+    float* acc = reinterpret_cast<float*>(smem32 + W * Pl::BUF) + w * N + t;
+#pragma unroll
+    for (int m = 0; m < E; ++m) acc[m * T] = 0.0f;
+#pragma unroll 1
+    for (int l = 0; l < a.lam.count; ++l) {
+        const float2* src = a.work + (size_t)l * N * N + (size_t)blockIdx.x * N * W;
+        const float2* h = a.h + (size_t)l * N;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * W + w];
+        fft_line<float2, N, -1, kColEPT>(v, buf, t, a.tw);
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
+        fft_line<float2, N, +1, kColEPT>(v, buf, t, a.tw);
+        const float wl = a.lam.weight[l];
+#pragma unroll
+        for (int m = 0; m < E; ++m) acc[m * T] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m * T]);
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        float* o = a.intensity + (size_t)(t + m * T) * N + x;
+        *o = a.accumulate ? *o + acc[m * T] : acc[m * T];
+    }
+}
+
+template <int N> constexpr size_t prow_smem() {
+    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long));
+}
+template <int N> constexpr size_t pcol_smem() {
+    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float));
+}
+
+constexpr size_t kMaxSmem = 227 * 1024;
+
+cudaError_t launch_prop_rows(const PropArgs& a, cudaStream_t s) {
+    return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
+        constexpr int N = decltype(nc)::value;
+        if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) return cudaErrorNotSupported;
+        cudaError_t e = set_smem(prop_rows_kernel<N>, prow_smem<N>());
+        if (e != cudaSuccess) return e;
+        prop_rows_kernel<N><<<N / prow_lines<N>(), prow_threads<N>(), prow_smem<N>(), s>>>(a);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_prop_cols(const PropArgs& a, cudaStream_t s) {
+    return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
+        constexpr int N = decltype(nc)::value;
+        if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) return cudaErrorNotSupported;
+        cudaError_t e = set_smem(prop_cols_kernel<N>, pcol_smem<N>());
+        if (e != cudaSuccess) return e;
+        prop_cols_kernel<N><<<N / pcol_lines<N>(), pcol_threads<N>(), pcol_smem<N>(), s>>>(a);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace scint

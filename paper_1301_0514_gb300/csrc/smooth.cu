@@ -1,0 +1,141 @@
+// Extended-source smoothing (Sect. 3.2.3, Eq. iprh): periodic convolution of a
+// real N x N intensity map with the uniform disk of radius R_s, done as
+//   column pass: two real columns packed as one complex line, FFT_y, split into
+//                the two half spectra (ky = 0..N/2) -> spec[ky][x]
+//   row pass:    each half-spectrum row: FFT_x, times K(q)/N^2, IFFT_x, in place
+//   column pass: rebuild the full ky range from Hermitian symmetry, pack two
+//                columns, IFFT_y, unpack real and imaginary parts -> intensity
+// with K(q) = 2 J1(2 pi q R_s) / (2 pi q R_s), K(0) = 1.
+#include "dispatch.cuh"
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace scint {
+
+template <int N> __host__ __device__ constexpr int scol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N / 2 ? kTileCol32 / N : N / 2); }
+template <int N> __host__ __device__ constexpr int scol_threads() { return scol_lines<N>() * FftPlan<N>::T; }
+template <int N> __host__ __device__ constexpr int srow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N / 2 ? kTileRow32 / N : N / 2); }
+template <int N> __host__ __device__ constexpr int srow_threads() { return srow_lines<N>() * FftPlan<N>::T; }
+
+// forward: two real columns (xa, xa+1) -> half spectra rows 0..N/2 of spec
+template <int N>
+__global__ void __launch_bounds__(scol_threads<N>(), 1)
+smooth_fwd_cols_kernel(SmoothArgs a) {
+    using Pl = FftPlan<N>;
+    constexpr int T = Pl::T, E = Pl::E, W = scol_lines<N>();
+    extern __shared__ float2 smem32[];
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int xa = (blockIdx.x * W + w) * 2;
+    float2* buf = smem32 + w * Pl::BUF;
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+        v[m] = *reinterpret_cast<const float2*>(a.intensity + (size_t)(t + m * T) * N + xa);
+    fft_line<float2, N, -1>(v, buf, t, a.tw);
+    // Z[N-k] lives in another thread: go through shared memory (natural order)
+#pragma unroll
+    for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int k = t + m * T;
+        if (k <= N / 2) {
+            const float2 z = v[m];
+            const float2 zc = conjc(buf[pad16((N - k) & (N - 1))]);
+            // X_a = (Z + conj Z(-k))/2, X_b = (Z - conj Z(-k))/(2i)
+            const float2 xa_ = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y + zc.y));
+            const float2 xb_ = make_float2(0.5f * (z.y - zc.y), -0.5f * (z.x - zc.x));
+            *reinterpret_cast<float4*>(a.spec + (size_t)k * N + xa) = make_float4(xa_.x, xa_.y, xb_.x, xb_.y);
+        }
+    }
+    __syncthreads();
+}
+
+// rows of the half spectrum: FFT_x, times K/N^2, IFFT_x
+template <int N>
+__global__ void __launch_bounds__(srow_threads<N>(), 1)
+smooth_rows_kernel(SmoothArgs a) {
+    using Pl = FftPlan<N>;
+    constexpr int T = Pl::T, E = Pl::E, B = srow_lines<N>();
+    extern __shared__ float2 smem32[];
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const int ky = blockIdx.x * B + team;
+    const bool live = ky <= N / 2;
+    float2* row = a.spec + (size_t)(live ? ky : 0) * N;
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = live ? row[t + m * T] : make_float2(0.f, 0.f);
+    fft_line<float2, N, -1>(v, smem32 + team * Pl::BUF, t, a.tw);
+    // mx^2 + my^2 <= N^2/2 is exact in FP32 for N <= 4096 and within one rounding above
+    const float inv = 1.0f / ((float)N * (float)N);
+    const float twopi_r = (float)(2.0 * kPi * a.radius_over_L);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int kx = t + m * T;
+        const int mx = kx < N / 2 ? kx : kx - N;
+        const float u = twopi_r * sqrtf((float)(mx * mx + ky * ky));
+        const float K = u > 0.0f ? 2.0f * j1f(u) / u : 1.0f;
+        v[m] = v[m] * (K * inv);
+    }
+    fft_line<float2, N, +1>(v, smem32 + team * Pl::BUF, t, a.tw);
+    if (live) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) row[t + m * T] = v[m];
+    }
+}
+
+// inverse: half spectra -> two real columns
+template <int N>
+__global__ void __launch_bounds__(scol_threads<N>(), 1)
+smooth_inv_cols_kernel(SmoothArgs a) {
+    using Pl = FftPlan<N>;
+    constexpr int T = Pl::T, E = Pl::E, W = scol_lines<N>();
+    extern __shared__ float2 smem32[];
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int xa = (blockIdx.x * W + w) * 2;
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int k = t + m * T;
+        const bool lo = k <= N / 2;
+        const float4 q = *reinterpret_cast<const float4*>(a.spec + (size_t)(lo ? k : N - k) * N + xa);
+        // X(k) for k > N/2 is conj X(N-k) (real columns)
+        const float2 Xa = lo ? make_float2(q.x, q.y) : make_float2(q.x, -q.y);
+        const float2 Xb = lo ? make_float2(q.z, q.w) : make_float2(q.z, -q.w);
+        v[m] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);   // Z = X_a + i X_b
+    }
+    fft_line<float2, N, +1>(v, smem32 + w * Pl::BUF, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+        *reinterpret_cast<float2*>(a.intensity + (size_t)(t + m * T) * N + xa) = v[m];
+}
+
+template <int N> constexpr size_t scol_smem() { return (size_t)scol_lines<N>() * FftPlan<N>::BUF * sizeof(float2); }
+template <int N> constexpr size_t srow_smem() { return (size_t)srow_lines<N>() * FftPlan<N>::BUF * sizeof(float2); }
+
+cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t s) {
+    return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
+        constexpr int N = decltype(nc)::value;
+        if constexpr (N < 32) {
+            return cudaErrorNotSupported;
+        } else {
+            cudaError_t e;
+            if ((e = set_smem(smooth_fwd_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
+            if ((e = set_smem(smooth_rows_kernel<N>, srow_smem<N>())) != cudaSuccess) return e;
+            if ((e = set_smem(smooth_inv_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
+            // every block of the column passes holds W line pairs = 2W real columns
+            const int col_blocks = N / (2 * scol_lines<N>());
+            if (col_blocks < 1) return cudaErrorNotSupported;
+            smooth_fwd_cols_kernel<N><<<col_blocks, scol_threads<N>(), scol_smem<N>(), s>>>(a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            const int rows = N / 2 + 1;
+            smooth_rows_kernel<N><<<(rows + srow_lines<N>() - 1) / srow_lines<N>(), srow_threads<N>(),
+                                    srow_smem<N>(), s>>>(a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            smooth_inv_cols_kernel<N><<<col_blocks, scol_threads<N>(), scol_smem<N>(), s>>>(a);
+            return cudaGetLastError();
+        }
+    });
+}
+
+}  // namespace scint

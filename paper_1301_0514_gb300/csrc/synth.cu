@@ -1,0 +1,147 @@
+// FP64 phase-screen synthesis (Sect. 3.1, Eq. spectre, Eq. densite).
+//
+// Pass 1 (rows of the spectrum): each team generates the shaped Gaussian noise
+// F[ky][kx] of one spectral row in registers (Philox4x32-10 + Box-Muller,
+// amplitude sqrt(L^2 S_phi(q))), inverse-transforms it along x and writes the
+// half-transformed row into the strip-layout intermediate.  The noise is never
+// stored.
+// Pass 2 (columns): inverse transform along y and write phi = sqrt(2)/L^2 Re(.).
+#include "dispatch.cuh"
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace scint {
+
+__global__ void twiddles32_kernel(float2* tw, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        double s, c;
+        sincospi(-2.0 * (double)j / (double)n, &s, &c);
+        tw[j] = make_float2((float)c, (float)s);
+    }
+}
+__global__ void twiddles64_kernel(double2* tw, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        double s, c;
+        sincospi(-2.0 * (double)j / (double)n, &s, &c);
+        tw[j] = make_double2(c, s);
+    }
+}
+cudaError_t launch_twiddles32(float2* tw, int n, cudaStream_t s) {
+    twiddles32_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_twiddles64(double2* tw, int n, cudaStream_t s) {
+    twiddles64_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+    return cudaGetLastError();
+}
+
+// Uniform in (0,1) from the 64-bit word (hi:lo): top 53 bits plus one half, times 2^-53.
+SCINT_DEV double uniform53(uint32_t hi, uint32_t lo) {
+    const uint64_t w = ((uint64_t)hi << 32) | lo;
+    return ((double)(w >> 11) + 0.5) * 0x1.0p-53;
+}
+
+SCINT_DEV int signed_freq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// Shaped spectral value F[ky][kx] (times sqrt(2)/... folded into amp).
+SCINT_DEV double2 spectrum_bin(const SynthArgs& a, int kx, int ky) {
+    const u32x4 w = philox4x32_10(u32x4{(uint32_t)kx, (uint32_t)ky, a.screen_id, 0u}, a.key0, a.key1);
+    const double ua = uniform53(w.y, w.x);
+    const double ub = uniform53(w.w, w.z);
+    const double r = sqrt(-2.0 * log(ua));
+    double sn, cs;
+    sincospi(2.0 * ub, &sn, &cs);
+    const int mx = signed_freq(kx, a.n), my = signed_freq(ky, a.n);
+    const int m2 = mx * mx + my * my;
+    const double sig = m2 ? a.amp * pow((double)m2, a.neg_beta_4) : 0.0;
+    return make_double2(sig * r * cs, sig * r * sn);
+}
+
+template <int N> __host__ __device__ constexpr int synth_lines() { return N >= kTile64 ? 1 : (kTile64 / N < N ? kTile64 / N : N); }
+template <int N> __host__ __device__ constexpr int synth_threads() { return synth_lines<N>() * FftPlan<N>::T; }
+
+template <int N>
+__global__ void __launch_bounds__(synth_threads<N>())
+synth_rows_kernel(SynthArgs a) {
+    using Pl = FftPlan<N>;
+    constexpr int T = Pl::T, E = Pl::E, B = synth_lines<N>(), W = B;
+    extern __shared__ double2 smem64[];
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const int ky = blockIdx.x * B + team;
+    double2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = spectrum_bin(a, t + m * T, ky);
+    fft_line<double2, N, +1>(v, smem64 + team * Pl::BUF, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int x = t + m * T;
+        a.work[(size_t)(x / W) * N * W + (size_t)ky * W + (x % W)] = v[m];
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(synth_threads<N>())
+synth_cols_kernel(SynthArgs a) {
+    using Pl = FftPlan<N>;
+    constexpr int T = Pl::T, E = Pl::E, W = synth_lines<N>();
+    extern __shared__ double2 smem64[];
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int x = blockIdx.x * W + w;
+    const double2* src = a.work + (size_t)blockIdx.x * N * W;
+    double2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * W + w];
+    fft_line<double2, N, +1>(v, smem64 + w * Pl::BUF, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < E; ++m) a.phi[(size_t)(t + m * T) * N + x] = a.out_scale * v[m].x;
+}
+
+cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s) {
+    return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
+        constexpr int N = decltype(nc)::value;
+        if constexpr (N > 8192) {
+            return cudaErrorNotSupported;
+        } else {
+            constexpr int threads = synth_threads<N>();
+            constexpr size_t smem = (size_t)synth_lines<N>() * FftPlan<N>::BUF * sizeof(double2);
+            cudaError_t e = set_smem(synth_rows_kernel<N>, smem);
+            if (e != cudaSuccess) return e;
+            e = set_smem(synth_cols_kernel<N>, smem);
+            if (e != cudaSuccess) return e;
+            synth_rows_kernel<N><<<N / synth_lines<N>(), threads, smem, s>>>(a);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            synth_cols_kernel<N><<<N / synth_lines<N>(), threads, smem, s>>>(a);
+            return cudaGetLastError();
+        }
+    });
+}
+
+// ---- test hooks --------------------------------------------------------------
+__global__ void noise_words_kernel(int n, uint32_t sid, uint32_t k0, uint32_t k1, uint32_t* out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)n * n) return;
+    const int kx = (int)(i % n), ky = (int)(i / n);
+    const u32x4 w = philox4x32_10(u32x4{(uint32_t)kx, (uint32_t)ky, sid, 0u}, k0, k1);
+    reinterpret_cast<uint4*>(out)[i] = make_uint4(w.x, w.y, w.z, w.w);
+}
+__global__ void noise_spectrum_kernel(SynthArgs a, double2* F) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)a.n * a.n) return;
+    F[i] = spectrum_bin(a, (int)(i % a.n), (int)(i / a.n));
+}
+cudaError_t launch_noise_words(int n, uint32_t sid, uint32_t k0, uint32_t k1, uint32_t* words,
+                               cudaStream_t s) {
+    const size_t tot = (size_t)n * n;
+    noise_words_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, sid, k0, k1, words);
+    return cudaGetLastError();
+}
+cudaError_t launch_noise_spectrum(const SynthArgs& a, double2* F, cudaStream_t s) {
+    const size_t tot = (size_t)a.n * a.n;
+    noise_spectrum_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a, F);
+    return cudaGetLastError();
+}
+
+}  // namespace scint

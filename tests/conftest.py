@@ -29,3 +29,23 @@ def read_golden(name):
 @pytest.fixture(scope="session")
 def golden():
     return read_golden
+
+
+_PARAM_KEYS = ("n", "pixel_km", "r_diff_km", "beta", "lambda_nm", "lambda_ref_nm", "z_pc",
+               "source_radius_km", "seed", "screen_id", "margin_km")
+
+
+def oracle_params(item, **kw):
+    """Workload record -> oracle ScreenParams."""
+    import oracle as O
+    d = {k: item[k] for k in _PARAM_KEYS}
+    d.update(kw)
+    return O.ScreenParams(**d)
+
+
+def gpu_params(item, **kw):
+    """Workload record -> library ScintParams."""
+    import paper_1301_0514_gb300 as S
+    d = {k: item[k] for k in _PARAM_KEYS}
+    d.update(kw)
+    return S.params(**d)

@@ -1,0 +1,113 @@
+"""The C-ABI library loads and exports every declared entry point; host-side checks (CPU only).
+
+No compute is launched here: invalid parameters are rejected on the host
+before any CUDA call, so these run without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1301_0514_gb300 as S
+from paper_1301_0514_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def _declared_functions():
+    names = set()
+    for h in os.listdir(INCLUDE):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(INCLUDE, h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(scint_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_1301_0514_gb300 import build
+        build.build()
+    return S.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert lib.scint_version() >= 100
+
+
+def test_params_struct_layout_matches_header():
+    # int32 n, int32 reserved, 8 doubles, uint64 seed, uint32 id, uint32 reserved
+    assert ctypes.sizeof(_lib.ScintParams) == 4 + 4 + 8 * 8 + 8 + 4 + 4
+    assert _lib.ScintParams.seed.offset == 72
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(n=100), "power of two"),
+    (dict(n=8), "power of two"),
+    (dict(n=32768), "power of two"),
+    (dict(pixel_km=0.0), "pixel_km"),
+    (dict(r_diff_km=-1.0), "r_diff_km"),
+    (dict(beta=2.0), "beta"),
+    (dict(beta=4.5), "beta"),
+    (dict(lambda_nm=0.0), "lambda_nm"),
+    (dict(z_pc=float("nan")), "z_pc"),
+    (dict(source_radius_km=-3.0), "source_radius_km"),
+    (dict(margin_km=1e9), "margin_km"),
+])
+def test_invalid_parameters_rejected_on_host(lib, kw, msg):
+    p = S.params(n=256, pixel_km=20.0, r_diff_km=100.0).replace(**kw)
+    rc = lib.scint_make_screen(ctypes.byref(p), ctypes.c_void_p(16), None, 0, None)
+    assert rc == 1
+    assert msg in lib.scint_last_error().decode()
+    rc = lib.scint_propagate(ctypes.byref(p), ctypes.c_void_p(16), ctypes.c_void_p(16), None, 0, None)
+    assert rc == 1
+
+
+def test_reserved_fields_and_null_pointers(lib):
+    p = S.params(n=256, pixel_km=20.0, r_diff_km=100.0)
+    bad = p.replace(reserved0=1)
+    assert lib.scint_make_screen(ctypes.byref(bad), ctypes.c_void_p(16), None, 0, None) == 1
+    assert lib.scint_make_screen(ctypes.byref(p), None, None, 0, None) == 1
+    assert lib.scint_make_screen(None, ctypes.c_void_p(16), None, 0, None) == 1
+    lam = np.array([500.0])
+    assert lib.scint_sum_passband(ctypes.byref(p), ctypes.c_void_p(16), lam.ctypes.data_as(ctypes.c_void_p),
+                                  None, 0, ctypes.c_void_p(16), 0, None, 0, None) == 1
+    lam = np.array([500.0, -1.0])
+    assert lib.scint_sum_passband(ctypes.byref(p), ctypes.c_void_p(16), lam.ctypes.data_as(ctypes.c_void_p),
+                                  None, 2, ctypes.c_void_p(16), 0, None, 0, None) == 1
+    tr = np.array([0.0, 0.0, float("inf"), 1.0])
+    assert lib.scint_lightcurve(ctypes.byref(p), ctypes.c_void_p(16), tr.ctypes.data_as(ctypes.c_void_p),
+                                1, 10, ctypes.c_void_p(16), None) == 1
+
+
+def test_workspace_too_small_rejected(lib):
+    p = S.params(n=1024, pixel_km=10.0, r_diff_km=50.0)
+    need1 = S.workspace_bytes(p, 1)
+    assert need1 > 1024 * 1024 * 8
+    assert S.workspace_bytes(p, 32) > S.workspace_bytes(p, 8) > need1 - 1
+    # a workspace that cannot hold even one wavelength group
+    rc = lib.scint_propagate(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                             ctypes.c_void_p(256), 1024, None)
+    assert rc == 2 and "workspace" in lib.scint_last_error().decode()
+
+
+def test_workloads_are_seeded_and_shaped():
+    from paper_1301_0514_gb300 import workloads as W
+    c3 = W.config3()
+    assert len(c3) == 48 and sorted({it["n"] for it in c3}) == [1024, 2048, 4096]
+    assert all(len(it["lambdas_nm"]) == 32 for it in c3)
+    assert all(30.0 <= it["r_diff_km"] <= 300.0 for it in c3)
+    again = W.config3()
+    assert all(a["seed"] == b["seed"] and a["r_diff_km"] == b["r_diff_km"] for a, b in zip(c3, again))
+    c2 = W.config2()
+    assert [it["r_diff_km"] for it in c2] == [30.0, 100.0, 300.0] and c2[0]["tracks"].shape == (64, 4)
