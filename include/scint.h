@@ -154,6 +154,8 @@ int scint_smooth_source(const scint_params* p, float* intensity,
  *   tracks   host, n_tracks records of 4 doubles (x0, y0, theta, ds) in pixels
  *            and radians; sample s is at (x0 + s ds cos theta, y0 + s ds sin theta).
  *   curves   device, n_tracks * n_samples floats, written row by row.
+ * With n_tracks == 0 or n_samples == 0 nothing is read or written and the
+ * pointers may be NULL.
  */
 int scint_lightcurve(const scint_params* p, const float* intensity,
                      const double* tracks, int n_tracks, int n_samples,

@@ -248,6 +248,8 @@ SynthArgs synth_args(const scint_params* p) {
     // sigma_k = sqrt(L^2 S(q_k)) with q_k = sqrt(m2)/L, times the 1/sqrt(2) of Eq. densite
     a.amp = L * std::sqrt(C) * std::pow(rd / L, -beta / 2.0) / std::sqrt(2.0);
     a.neg_beta_4 = -beta / 4.0;
+    a.amp32 = (float)a.amp;
+    a.neg_beta_4_32 = (float)a.neg_beta_4;
     a.out_scale = std::sqrt(2.0) / (L * L);
     return a;
 }
@@ -330,8 +332,9 @@ int scint_lightcurve(const scint_params* p, const float* intensity, const double
                      int n_samples, float* curves, void* stream) {
     int rc = check_params(p);
     if (rc) return rc;
-    if (!intensity || !curves) return fail(SCINT_EINVAL, "intensity and curves must be device pointers");
     if (n_tracks < 0 || n_samples < 0) return fail(SCINT_EINVAL, "negative track or sample count");
+    if (n_tracks == 0 || n_samples == 0) return ok();   // nothing to sample: pointers may be NULL
+    if (!intensity || !curves) return fail(SCINT_EINVAL, "intensity and curves must be device pointers");
     if (n_tracks > 0 && !tracks) return fail(SCINT_EINVAL, "tracks is NULL");
     for (int i = 0; i < 4 * n_tracks; ++i)
         if (!std::isfinite(tracks[i])) return fail(SCINT_EINVAL, "track parameters must be finite");

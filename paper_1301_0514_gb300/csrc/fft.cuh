@@ -161,7 +161,33 @@ SCINT_DEV int pad16(int a) { return a + (a >> 4); }
 template <typename C>
 SCINT_DEV C ld_tw(const C* __restrict__ p) { return __ldg(p); }
 
-template <typename C, int N, int DIR, int EPT, int S>
+
+// Twiddles W_{PR}^{r k} = tw[r step], r = 1..R-1, from at most two table loads
+// (r = 1 and r = 4); the rest are products of depth <= 3 (a few ulp).
+template <int R, int DIR, typename C>
+SCINT_DEV void twiddle_set(const C* __restrict__ tw, int step, C (&w)[R]) {
+    if constexpr (R >= 2) w[1] = ld_tw(tw + step);
+    if constexpr (R >= 4) { w[2] = cmul(w[1], w[1]); w[3] = cmul(w[1], w[2]); }
+    if constexpr (R >= 8) {
+        w[4] = ld_tw(tw + 4 * step);
+        w[5] = cmul(w[4], w[1]);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+    }
+    if constexpr (R >= 16) {
+        w[8] = cmul(w[4], w[4]);
+#pragma unroll
+        for (int r = 9; r < 12; ++r) w[r] = cmul(w[8], w[r - 8]);
+        w[12] = cmul(w[8], w[4]);
+#pragma unroll
+        for (int r = 13; r < 16; ++r) w[r] = cmul(w[12], w[r - 12]);
+    }
+}
+
+// LW: lane width of the buffer.  Element e of the line sits at buf[pad16(e) * LW]
+// (the caller offsets buf by its lane), so LW lines can share one interleaved
+// buffer with consecutive threads of different lines hitting consecutive banks.
+template <typename C, int N, int DIR, int EPT, int LW, int S>
 SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw) {
     using Pl = FftPlan<N, EPT>;
     constexpr int E = Pl::E, T = Pl::T;
@@ -178,9 +204,9 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             // N/R is a multiple of 16 here, so pad16(i + r N/R) = pad16(i) + r (N/R)(17/16)
-            const C* src = buf + pad16(t + b * T);
+            const C* src = buf + pad16(t + b * T) * LW;
 #pragma unroll
-            for (int r = 0; r < R; ++r) u[b * R + r] = src[r * ((N / R) + (N / R) / 16)];
+            for (int r = 0; r < R; ++r) u[b * R + r] = src[r * ((N / R) + (N / R) / 16) * LW];
         }
         __syncthreads();
     }
@@ -189,12 +215,10 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
         const int i = t + b * T;
         if constexpr (!FIRST) {
             const int k = i & (P - 1);
-            const int step = k * (N / (P * R));      // W_{PR}^{r k} = tw[r * step]
+            C w[R];
+            twiddle_set<R, DIR>(tw, k * (N / (P * R)), w);   // W_{PR}^{r k} = tw[r * step]
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const C w = ld_tw(tw + r * step);
-                u[b * R + r] = DIR < 0 ? cmul(u[b * R + r], w) : cmulc(u[b * R + r], w);
-            }
+            for (int r = 1; r < R; ++r) u[b * R + r] = DIR < 0 ? cmul(u[b * R + r], w[r]) : cmulc(u[b * R + r], w[r]);
         }
         dft<R, DIR>(&u[b * R]);
     }
@@ -210,20 +234,20 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
             const int k = i & (P - 1);
             const int j = (i - k) * R + k;
             // P >= 16: pad16(j + r P) = pad16(j) + r P (17/16); P == 1: j = i R and r < R <= 16
-            C* dst = buf + pad16(j);
+            C* dst = buf + pad16(j) * LW;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[P >= 16 ? r * (P + P / 16) : r] = u[b * R + r];
+            for (int r = 0; r < R; ++r) dst[(P >= 16 ? r * (P + P / 16) : r) * LW] = u[b * R + r];
         }
         __syncthreads();
-        fft_stage<C, N, DIR, EPT, S + 1>(v, buf, t, tw);
+        fft_stage<C, N, DIR, EPT, LW, S + 1>(v, buf, t, tw);
     }
 }
 
 // Transform the team's line in place (registers v, distribution t + m*T).
 // Every thread of the block must call this the same number of times.
-template <typename C, int N, int DIR, int EPT = 16>
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1>
 SCINT_DEV void fft_line(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw) {
-    fft_stage<C, N, DIR, EPT, 0>(v, buf, t, tw);
+    fft_stage<C, N, DIR, EPT, LW, 0>(v, buf, t, tw);
 }
 
 }  // namespace scint

@@ -33,6 +33,7 @@ struct SynthArgs {
     uint32_t screen_id, key0, key1;
     double amp;          // sigma(k) = amp * (mx^2 + my^2)^(-beta/4), includes 1/sqrt(2)
     double neg_beta_4;   // -beta/4
+    float amp32, neg_beta_4_32;   // the same in FP32 for the high-frequency bins
     double out_scale;    // sqrt(2) / L^2
     const double2* tw;   // FP64 twiddles for n
     double2* work;       // n*n complex128, strip layout

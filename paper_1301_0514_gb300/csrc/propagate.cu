@@ -117,7 +117,7 @@ prop_cols_kernel(PropArgs a) {
     extern __shared__ float2 smem32[];
     const int w = threadIdx.x % W, t = threadIdx.x / W;
     const int x = blockIdx.x * W + w;
-    float2* buf = smem32 + w * Pl::BUF;
+    float2* buf = smem32 + w;     // W lines interleaved: element e of line w at pad16(e) * W + w
     // passband accumulator of this thread's pixels (own entries only)
     float* acc = reinterpret_cast<float*>(smem32 + W * Pl::BUF) + w * N + t;
 #pragma unroll
@@ -129,10 +129,10 @@ prop_cols_kernel(PropArgs a) {
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * W + w];
-        fft_line<float2, N, -1, kColEPT>(v, buf, t, a.tw);
+        fft_line<float2, N, -1, kColEPT, W>(v, buf, t, a.tw);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
-        fft_line<float2, N, +1, kColEPT>(v, buf, t, a.tw);
+        fft_line<float2, N, +1, kColEPT, W>(v, buf, t, a.tw);
         const float wl = a.lam.weight[l];
 #pragma unroll
         for (int m = 0; m < E; ++m) acc[m * T] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m * T]);

@@ -26,22 +26,22 @@ smooth_fwd_cols_kernel(SmoothArgs a) {
     extern __shared__ float2 smem32[];
     const int w = threadIdx.x % W, t = threadIdx.x / W;
     const int xa = (blockIdx.x * W + w) * 2;
-    float2* buf = smem32 + w * Pl::BUF;
+    float2* buf = smem32 + w;     // W lines interleaved
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m)
         v[m] = *reinterpret_cast<const float2*>(a.intensity + (size_t)(t + m * T) * N + xa);
-    fft_line<float2, N, -1>(v, buf, t, a.tw);
+    fft_line<float2, N, -1, 16, W>(v, buf, t, a.tw);
     // Z[N-k] lives in another thread: go through shared memory (natural order)
 #pragma unroll
-    for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = v[m];
+    for (int m = 0; m < E; ++m) buf[pad16(t + m * T) * W] = v[m];
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * T;
         if (k <= N / 2) {
             const float2 z = v[m];
-            const float2 zc = conjc(buf[pad16((N - k) & (N - 1))]);
+            const float2 zc = conjc(buf[pad16((N - k) & (N - 1)) * W]);
             // X_a = (Z + conj Z(-k))/2, X_b = (Z - conj Z(-k))/(2i)
             const float2 xa_ = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y + zc.y));
             const float2 xb_ = make_float2(0.5f * (z.y - zc.y), -0.5f * (z.x - zc.x));
@@ -104,7 +104,7 @@ smooth_inv_cols_kernel(SmoothArgs a) {
         const float2 Xb = lo ? make_float2(q.z, q.w) : make_float2(q.z, -q.w);
         v[m] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);   // Z = X_a + i X_b
     }
-    fft_line<float2, N, +1>(v, smem32 + w * Pl::BUF, t, a.tw);
+    fft_line<float2, N, +1, 16, W>(v, smem32 + w, t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m)
         *reinterpret_cast<float2*>(a.intensity + (size_t)(t + m * T) * N + xa) = v[m];

@@ -2,9 +2,11 @@
 
 Tolerances (fixed by the required accuracy of the FP32 path, not tuned):
   * Philox words: bit-exact.
-  * Shaped spectrum, phase screen (FP64 on both sides): 1e-12 relative to the
-    largest magnitude (a few ulp of FP64 rounding-order differences and of the
-    CUDA vs libm log / sincos / pow).
+  * Shaped spectrum: bins with |mx|, |my| <= 32 are FP64 on both sides (1e-13
+    relative); the other bins are drawn in FP32 on the GPU (2e-6 relative).
+  * Phase screen: 2e-6 rad absolute.  The screen's error is ~1e-7 of the rms
+    phase carried by the FP32 bins (a few rad at most); the intensity bound
+    needs the phase to ~4e-6 rad (2e-4 / (2 |A|_max * 5 sigma), |A|^2 <= 20).
   * Intensity, normalised to the unobstructed wave: 2e-4 max absolute.
   * Modulation index: 1e-4 relative.
   * Line FFT: 2e-6 (FP32) / 1e-13 (FP64) relative to the line's l2 norm.
@@ -24,6 +26,7 @@ pytestmark = pytest.mark.gpu
 
 I_TOL = 2e-4
 M_TOL = 1e-4
+PHI_TOL = 2e-6
 
 
 def _item(n=256, pixel_km=20.0, r_diff_km=100.0, **kw):
@@ -45,7 +48,12 @@ def test_noise_spectrum(beta):
     it = _item(n=128, pixel_km=15.0, r_diff_km=40.0, beta=beta, seed=99, screen_id=3)
     g = S.noise_spectrum(gpu_params(it)).cpu().numpy()
     o = O.noise_spectrum(oracle_params(it))
-    assert np.abs(g - o).max() <= 1e-12 * np.abs(o).max()
+    m = np.abs(np.fft.fftfreq(128, 1.0 / 128))
+    low = (m[:, None] <= 32) & (m[None, :] <= 32)
+    rel = np.abs(g - o) / np.maximum(np.abs(o), 1e-300)
+    assert rel[low].max() <= 1e-13
+    assert rel[~low].max() <= 2e-6
+    assert g[0, 0] == 0
 
 
 @pytest.mark.parametrize("n", [16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192])
@@ -80,7 +88,7 @@ def test_make_screen(n, pixel, rd, beta):
     it = _item(n=n, pixel_km=pixel, r_diff_km=rd, beta=beta, seed=W.SEED_BASE + n, screen_id=1)
     phi_g = S.make_screen(gpu_params(it)).cpu().numpy()
     phi_o = O.make_screen(oracle_params(it))
-    assert np.abs(phi_g - phi_o).max() <= 1e-12 * np.abs(phi_o).max()
+    assert np.abs(phi_g - phi_o).max() <= PHI_TOL
 
 
 def _intensity_case(it, lam=None):
@@ -214,7 +222,7 @@ def test_config2_full_size_one_screen():
     p_g, p_o = gpu_params(it), oracle_params(it)
     phi_g = S.make_screen(p_g)
     phi_o = O.make_screen(p_o)
-    assert (phi_g.cpu().numpy() - phi_o).__abs__().max() <= 1e-12 * np.abs(phi_o).max()
+    assert np.abs(phi_g.cpu().numpy() - phi_o).max() <= PHI_TOL
     I_g = S.propagate(p_g, phi_g)
     I_o = O.intensity_mono(phi_o, p_o)
     err = np.abs(I_g.cpu().numpy() - I_o).max()
@@ -227,6 +235,20 @@ def test_config2_full_size_one_screen():
     cm = S.curve_modulation(torch.from_numpy(c_g).cuda()).cpu().numpy()[:, 0]
     cm_o = np.array([O.modulation_index(c) for c in c_o])
     np.testing.assert_allclose(cm, cm_o, rtol=M_TOL)
+
+
+def test_largest_phase_screen_full_path():
+    """R_diff = 30 km (phase rms ~ 60 rad, peaks ~ 300 rad), 2048^2: screen, intensity, m vs oracle."""
+    it = W.config2(r_diffs=(30.0,), n=2048)[0]
+    p_g, p_o = gpu_params(it), oracle_params(it)
+    phi_g = S.make_screen(p_g)
+    phi_o = O.make_screen(p_o)
+    assert np.abs(phi_o).max() > 100.0
+    assert np.abs(phi_g.cpu().numpy() - phi_o).max() <= PHI_TOL
+    I_g = S.propagate(p_g, phi_g)
+    I_o = O.intensity_mono(phi_o, p_o)
+    assert np.abs(I_g.cpu().numpy() - I_o).max() <= I_TOL
+    assert S.modulation_index(p_g, I_g).cpu().numpy()[0] == pytest.approx(O.modulation_index_map(I_o, p_o), rel=M_TOL)
 
 
 def test_config3_like_screen_passband_and_disk():
