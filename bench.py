@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Throughput of the batched scintillation pipeline on GB300: one JSON line on rank 0.
+
+Workload (default "batched"): 48 seeded screens, 16 each of 1024^2, 2048^2 and
+4096^2 (10 km pixels, R_diff ~ U[30, 300] km at 550 nm, Kolmogorov), each
+propagated at 32 wavelengths in 400-700 nm (flat passband), smoothed by a
+projected stellar disk of U[0.1, 2] R_ref and sampled along 8 straight tracks,
+with the modulation index of the map and of every curve.  A step is one pass of
+the whole hot path over the batch: synthesis -> passband propagation ->
+smoothing -> light curves -> modulation indices, replayed as one CUDA graph.
+
+Metric: Fresnel-propagated pixels per second, sum over screens of N^2 x
+N_lambda per step / step time.  Timing: CUDA events on the launching stream,
+barrier + synchronize around exactly --steps replays after --warmup untimed
+ones, max over ranks.  Every per-screen field is 32-134 MB and a step moves
+hundreds of GB, so the inputs exceed the 129 MB L2 between steps.
+
+Multi-GPU: independent batches per rank (seeds offset by rank), no collective
+on the data path: weak scaling.  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Fresnel-propagated pixels/sec, batched FP32 vs plain, at <=2e-4 err; %HBM peak"
+UNIT = "pixel-wavelengths/s"
+PARAM_KEYS = ("n", "pixel_km", "r_diff_km", "beta", "lambda_nm", "lambda_ref_nm", "z_pc",
+              "source_radius_km", "seed", "screen_id", "margin_km")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+def _workload(name: str, rank: int):
+    from paper_1301_0514_gb300 import workloads as W
+    if name == "batched":
+        items = W.config3()
+        desc = ("batched: 48 screens (16 each of 1024^2, 2048^2, 4096^2, 10 km pixels, R_diff U[30,300] km) "
+                "x 32 wavelengths 400-700 nm, disk sources U[0.1,2] R_ref, 8 tracks/screen")
+    else:
+        items = W.config2(r_diffs=(100.0,))
+        items[0]["lambdas_nm"] = np.array([500.0])
+        desc = "single 4096^2 screen, 10 km pixels, R_diff 100 km, 500 nm, point source, 64 tracks"
+    for it in items:
+        it["seed"] += 100000 * rank
+    return items, desc
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1301_0514_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"scint_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_baseline(items, gpu_maps):
+    """FP64 oracle on one 1024^2 screen of the batch (all 32 wavelengths, disk, tracks), one core."""
+    import oracle as O
+    it = [x for x in items if x["n"] == 1024][0]
+    p = O.ScreenParams(**{k: it[k] for k in PARAM_KEYS})
+    t0 = time.perf_counter()
+    phi = O.make_screen(p)
+    I = O.sum_passband(phi, p, it["lambdas_nm"], it["weights"])
+    I = O.smooth_source(I, p.pixel_km, p.source_radius_km)
+    curves = O.lightcurves(I, it["tracks"], it["n_samples"])
+    m_map = O.modulation_index_map(I, p)
+    ms = [O.modulation_index(c) for c in curves]
+    dt = time.perf_counter() - t0
+    units = p.n * p.n * len(it["lambdas_nm"])
+    out = {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"one 1024^2 screen of the batch x {len(it['lambdas_nm'])} wavelengths + disk + "
+                     f"{len(it['tracks'])} tracks, {dt:.1f} s"}
+    err = None
+    if gpu_maps is not None and it["seed"] in gpu_maps:
+        g_I, g_m = gpu_maps[it["seed"]]
+        err = {"max_abs_intensity_err": float(np.abs(g_I - I).max()),
+               "m_rel_err": float(abs(g_m - m_map) / m_map)}
+        del ms
+    return out, err
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    items, desc = _workload(args.workload, 0)
+    import oracle as O
+    it = [x for x in items if x["n"] == min(x["n"] for x in items)][0]
+    p = O.ScreenParams(**{k: it[k] for k in PARAM_KEYS})
+    lams = it["lambdas_nm"][:4]        # bounded sample per step: 4 wavelengths of one screen
+
+    def step():
+        phi = O.make_screen(p)
+        I = O.sum_passband(phi, p, lams)
+        if p.source_radius_km > 0:
+            I = O.smooth_source(I, p.pixel_km, p.source_radius_km)
+        O.lightcurves(I, it["tracks"], it["n_samples"])
+        return I
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = p.n * p.n * len(lams) / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "sample": f"one {p.n}^2 screen x {len(lams)} wavelengths per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one {p.n}^2 screen x {len(lams)} wavelengths per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_1301_0514_gb300 as S
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    items, desc = _workload(args.workload, rank)
+    P = [S.params(**{k: it[k] for k in PARAM_KEYS}) for it in items]
+    sizes = sorted({p.n for p in P})
+    n_lam = max(len(it["lambdas_nm"]) for it in items)
+    ws = torch.empty(max(S.workspace_bytes(p, n_lam) for p in P), dtype=torch.uint8, device=dev)
+    phi = {n: torch.empty((n, n), dtype=torch.float64, device=dev) for n in sizes}
+    inten = {n: torch.empty((n, n), dtype=torch.float32, device=dev) for n in sizes}
+    curves = [torch.empty((len(it["tracks"]), it["n_samples"]), dtype=torch.float32, device=dev) for it in items]
+    m_map = torch.empty((len(items), 4), dtype=torch.float64, device=dev)
+    m_curve = [torch.empty((len(it["tracks"]), 3), dtype=torch.float64, device=dev) for it in items]
+    units = sum(p.n * p.n * len(it["lambdas_nm"]) for p, it in zip(P, items))
+    stream = torch.cuda.current_stream(dev)
+
+    def screen(i, p, it, plain=False):
+        S.make_screen(p, out=phi[p.n], workspace=ws)
+        if plain:
+            w = it["weights"] if it["weights"] is not None else np.full(len(it["lambdas_nm"]), 1.0 / len(it["lambdas_nm"]))
+            for j, lam in enumerate(it["lambdas_nm"]):
+                S.sum_passband(p, phi[p.n], [lam], [w[j]], out=inten[p.n], accumulate=j > 0, workspace=ws)
+        else:
+            S.sum_passband(p, phi[p.n], it["lambdas_nm"], it["weights"], out=inten[p.n], workspace=ws)
+        S.smooth_source(p, inten[p.n], workspace=ws)
+        S.lightcurve(p, inten[p.n], it["tracks"], it["n_samples"], out=curves[i])
+        S.modulation_index(p, inten[p.n], out=m_map[i], workspace=ws)
+        S.curve_modulation(curves[i], out=m_curve[i])
+
+    def step(plain=False):
+        for i, (p, it) in enumerate(zip(P, items)):
+            screen(i, p, it, plain)
+
+    # warm-up outside the graph (sets kernel attributes), then capture one graph of the step
+    step()
+    torch.cuda.synchronize(dev)
+    S.profile_enable(True)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    kstats = S.profile_read()           # per-kernel event times of the last timed replay
+    S.profile_enable(False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units * world / (ms * 1e-3)
+
+    # plain form: one screen and one wavelength per call, no graph, same kernels
+    torch.cuda.synchronize(dev)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    step(plain=True)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_plain = p0.elapsed_time(p1)
+
+    # end to end through the public API with host inputs and host results
+    pinned_curves = [torch.empty(c.shape, dtype=c.dtype, pin_memory=True) for c in curves]
+    pinned_m = torch.empty(m_map.shape, dtype=m_map.dtype, pin_memory=True)
+    h2d = sum(it["tracks"].nbytes + it["lambdas_nm"].nbytes + 96 for it in items)
+    d2h = sum(c.numel() * 4 for c in curves) + m_map.numel() * 8
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step()
+        for c, pc in zip(curves, pinned_curves):
+            pc.copy_(c, non_blocking=True)
+        pinned_m.copy_(m_map, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+
+    # roofline of the dominant kernel (largest share of the timed step)
+    hbm_peak, sm_max_mhz, peak_src = _peaks()
+    alu_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    dom_name, dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
+    per_launch_ms = dom["total_ms"] / dom["launches"]
+    gbs = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9
+    tflops = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12
+    ridge = alu_peak_tflops * 1e12 / (hbm_peak * 1e9)
+    intensity = dom["flops"] / dom["bytes"] if dom["bytes"] else 0.0
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        rec = tr.get(dom_name)
+        if rec and rec.get("source_hash") == _kernel_source_hash():
+            traffic = rec["bytes_per_launch"]
+    except Exception:
+        pass
+    if intensity > ridge:
+        roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak_tflops, "unit": "TFLOP/s",
+                "frac": tflops / alu_peak_tflops, "traffic": traffic}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": traffic}
+    roof.update({"kernel": dom_name, "launch_ms": per_launch_ms, "share": dom["total_ms"] / ms,
+                 "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+                 "fft_flops_per_launch": dom["flops"] / dom["launches"], "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                 "peak_source": f"hbm {peak_src} (MEASURED_PEAKS.json); alu = {SM_COUNT} SMs x "
+                                f"{FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz"})
+    launches = sum(v["launches"] for v in kstats.values())
+    kernels = {k: {"launches": v["launches"], "ms": v["total_ms"], "share": v["total_ms"] / ms,
+                   "GBps": v["bytes"] / max(v["total_ms"], 1e-9) / 1e6,
+                   "TFLOPs": v["flops"] / max(v["total_ms"], 1e-9) / 1e9} for k, v in kstats.items()}
+
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        it = [x for x in items if x["n"] == 1024][0]
+        i = items.index(it)
+        p = P[i]
+        screen(i, p, it)
+        torch.cuda.synchronize(dev)
+        gmap = {it["seed"]: (inten[1024].cpu().numpy().astype(np.float64), float(m_map[i, 0].item()))}
+        cpu, err = _cpu_baseline(items, gmap)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": desc, "form": "batched, one CUDA graph per step",
+                           "l2": "inputs larger than L2 (fields 32-134 MB per screen and wavelength)",
+                           "parallelism": f"independent batch per GPU x{world}"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": units * world / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+                "gpu_launches": launches * args.steps, "clocks": clk,
+                "plain": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                          "form": "one screen and one wavelength per call, no graph"},
+                "parity": err, "kernels": kernels}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "single4096"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -184,6 +184,29 @@ int scint_curve_modulation(const float* curves, int n_curves, int n_samples,
 /* Release the library's internal per-device workspace pools and tables. */
 void scint_release(void);
 
+/*
+ * Kernel profiler (instrumentation; the paper has no counterpart).  While
+ * enabled, every kernel launch is bracketed by two CUDA events recorded on the
+ * launching stream (event nodes when the stream is being captured into a
+ * graph), tagged with the launch's algorithmic DRAM bytes (each input read
+ * once, each output written once) and FFT flops (5 n log2 n per complex line
+ * transform of n points).
+ *   scint_profile_enable(on)  clears the records and turns recording on/off.
+ *   scint_profile_read        waits for the recorded events and sums them per
+ *                             kernel class into stats[0..max_stats); *n_stats
+ *                             receives the number of classes written.  For
+ *                             events inside a graph, the last replay counts.
+ */
+typedef struct scint_kernel_stat {
+    char    name[32];
+    int64_t launches;   /* kernel launches recorded */
+    double  total_ms;
+    double  bytes;
+    double  flops;
+} scint_kernel_stat;
+int scint_profile_enable(int on);
+int scint_profile_read(scint_kernel_stat* stats, int max_stats, int* n_stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,8 @@ from ._lib import (  # noqa: F401
     noise_spectrum,
     noise_words,
     params,
+    profile_enable,
+    profile_read,
     propagate,
     release,
     smooth_source,

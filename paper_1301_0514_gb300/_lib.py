@@ -65,6 +65,12 @@ def params(n: int, pixel_km: float, r_diff_km: float, beta: float = 11.0 / 3.0, 
                        seed=seed, screen_id=screen_id, reserved1=0)
 
 
+class KernelStat(ctypes.Structure):
+    """Mirror of struct scint_kernel_stat (include/scint.h)."""
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
 _lib = None
 _P = ctypes.POINTER(ScintParams)
 _vp = ctypes.c_void_p
@@ -96,6 +102,8 @@ def lib() -> ctypes.CDLL:
         "scint_noise_spectrum": ([_P, _vp, _vp], _i),
         "scint_fft_lines32": ([_i, _i, _vp, _i, _vp], _i),
         "scint_fft_lines64": ([_i, _i, _vp, _i, _vp], _i),
+        "scint_profile_enable": ([_i], _i),
+        "scint_profile_read": ([ctypes.POINTER(KernelStat), _i, ctypes.POINTER(_i)], _i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -238,3 +246,18 @@ def fft_lines(x: torch.Tensor, direction: int, stream=None) -> torch.Tensor:
 
 def release():
     lib().scint_release()
+
+
+def profile_enable(on: bool = True):
+    """Start (clearing old records) or stop the library's per-kernel event timing."""
+    _check(lib().scint_profile_enable(int(bool(on))))
+
+
+def profile_read():
+    """Per kernel class: dict(launches, total_ms, bytes, flops) of the recorded launches."""
+    arr = (KernelStat * 32)()
+    cnt = ctypes.c_int(0)
+    _check(lib().scint_profile_read(arr, 32, ctypes.byref(cnt)))
+    return {arr[i].name.decode(): dict(launches=int(arr[i].launches), total_ms=float(arr[i].total_ms),
+                                       bytes=float(arr[i].bytes), flops=float(arr[i].flops))
+            for i in range(cnt.value)}

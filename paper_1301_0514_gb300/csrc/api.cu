@@ -163,6 +163,73 @@ int resolve_ws(void* ws, size_t bytes, size_t need, cudaStream_t s, Carver* c) {
     return SCINT_OK;
 }
 
+// ---- kernel profiler -------------------------------------------------------------
+// When enabled, every kernel launch is bracketed by two CUDA events recorded on
+// its stream (they become event nodes when the stream is being captured), and
+// the algorithmic bytes and FFT flops of the launch are attached.
+enum KClass {
+    K_TWIDDLES, K_SYNTH_ROWS, K_SYNTH_COLS, K_PROP_TABLES, K_PROP_ROWS, K_PROP_COLS,
+    K_SMOOTH_FWD, K_SMOOTH_ROWS, K_SMOOTH_INV, K_LIGHTCURVE, K_MOMENTS, K_COUNT
+};
+const char* const kClassName[K_COUNT] = {
+    "twiddles", "synth_rows", "synth_cols", "prop_tables", "prop_rows", "prop_cols",
+    "smooth_fwd_cols", "smooth_rows", "smooth_inv_cols", "lightcurve", "moments"};
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes, flops;
+    int kernels;
+};
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<ProfRec> recs;
+};
+Profiler g_prof;
+
+double fft_flops(int n) { return 5.0 * n * std::log2((double)n); }   // per complex line of n points
+
+template <typename F>
+int launch_timed(KClass c, double bytes, double flops, cudaStream_t s, F&& launch, int kernels = 1) {
+    bool on;
+    {
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        on = g_prof.on;
+    }
+    ProfRec r{c, nullptr, nullptr, bytes, flops, kernels};
+    // while capturing, the records must be external event nodes to time graph replays
+    unsigned rec_flags = cudaEventRecordDefault;
+    if (on) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        SCINT_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
+        SCINT_CUDA(cudaEventCreate(&r.a));
+        SCINT_CUDA(cudaEventCreate(&r.b));
+        SCINT_CUDA(cudaEventRecordWithFlags(r.a, s, rec_flags));
+    }
+    SCINT_CUDA(launch());
+    if (on) {
+        SCINT_CUDA(cudaEventRecordWithFlags(r.b, s, rec_flags));
+        std::lock_guard<std::mutex> lk(g_prof.mu);
+        g_prof.recs.push_back(r);
+    }
+    return SCINT_OK;
+}
+#define SCINT_LAUNCH(cls, bytes, flops, stream, call)                                     \
+    do {                                                                                  \
+        const int rc_ = launch_timed(cls, bytes, flops, stream, [&] { return (call); }); \
+        if (rc_) return rc_;                                                              \
+    } while (0)
+
+void prof_clear_locked() {
+    for (auto& r : g_prof.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof.recs.clear();
+}
+
 // Propagate one wavelength group [l0, l0 + g) into the intensity map.
 int run_group(const scint_params* p, const double* phi, const double* lam, const double* wts,
               int l0, int g, float* intensity, int accumulate, Carver& c, const float2* tw,
@@ -193,9 +260,13 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
     pa.work = cg.take<float2>((size_t)g * n * n * 8);
     pa.intensity = intensity;
     pa.accumulate = accumulate;
-    SCINT_CUDA(launch_prop_tables(ta, s));
-    SCINT_CUDA(launch_prop_rows(pa, s));
-    SCINT_CUDA(launch_prop_cols(pa, s));
+    const double nn = (double)n * n;
+    SCINT_LAUNCH(K_PROP_TABLES, 12.0 * g * n, 0.0, s, launch_prop_tables(ta, s));
+    // rows: phi read once, one complex64 field written per wavelength; FFT_x + IFFT_x per row
+    SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * g * nn, 2.0 * g * n * fft_flops(n), s, launch_prop_rows(pa, s));
+    // columns: fields read, intensity written once (and read when accumulating)
+    SCINT_LAUNCH(K_PROP_COLS, 8.0 * g * nn + (accumulate ? 8.0 : 4.0) * nn, 2.0 * g * n * fft_flops(n), s,
+                 launch_prop_cols(pa, s));
     return SCINT_OK;
 }
 
@@ -227,7 +298,7 @@ int passband_impl(const scint_params* p, const double* phi, const double* lambda
     rc = resolve_ws(ws, ws_bytes, ws_prop(n, g), s, &c);
     if (rc) return rc;
     float2* tw = c.take<float2>((size_t)n * 8);
-    SCINT_CUDA(launch_twiddles32(tw, n, s));
+    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n, 0.0, s, launch_twiddles32(tw, n, s));
     for (int l0 = 0; l0 < n_lambda; l0 += g) {
         const int gg = std::min(g, n_lambda - l0);
         rc = run_group(p, phi, lambdas, w.data(), l0, gg, intensity, accumulate || l0 > 0, c, tw, s);
@@ -286,8 +357,11 @@ int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_
     a.tw = c.take<double2>((size_t)p->n * 16);
     a.work = c.take<double2>((size_t)p->n * p->n * 16);
     a.phi = phi;
-    SCINT_CUDA(launch_twiddles64(const_cast<double2*>(a.tw), p->n, s));
-    SCINT_CUDA(launch_synth(a, s));
+    const double nn = (double)p->n * p->n;
+    SCINT_LAUNCH(K_TWIDDLES, 16.0 * p->n, 0.0, s, launch_twiddles64(const_cast<double2*>(a.tw), p->n, s));
+    // rows: the noise is generated in registers, the half-transformed field is written
+    SCINT_LAUNCH(K_SYNTH_ROWS, 16.0 * nn, p->n * fft_flops(p->n), s, launch_synth_rows(a, s));
+    SCINT_LAUNCH(K_SYNTH_COLS, 16.0 * nn + 8.0 * nn, p->n * fft_flops(p->n), s, launch_synth_cols(a, s));
     return ok();
 }
 
@@ -323,8 +397,12 @@ int scint_smooth_source(const scint_params* p, float* intensity, void* workspace
     a.tw = tw;
     a.spec = c.take<float2>((size_t)(p->n / 2 + 1) * p->n * 8);
     a.intensity = intensity;
-    SCINT_CUDA(launch_twiddles32(tw, p->n, s));
-    SCINT_CUDA(launch_smooth(a, s));
+    const int n = p->n;
+    const double half = (double)(n / 2 + 1) * n * 8.0, nn = (double)n * n;
+    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n, 0.0, s, launch_twiddles32(tw, n, s));
+    SCINT_LAUNCH(K_SMOOTH_FWD, 4.0 * nn + half, (n / 2) * fft_flops(n), s, launch_smooth_pass(a, 0, s));
+    SCINT_LAUNCH(K_SMOOTH_ROWS, 2.0 * half, 2.0 * (n / 2 + 1) * fft_flops(n), s, launch_smooth_pass(a, 1, s));
+    SCINT_LAUNCH(K_SMOOTH_INV, half + 4.0 * nn, (n / 2) * fft_flops(n), s, launch_smooth_pass(a, 2, s));
     return ok();
 }
 
@@ -350,7 +428,7 @@ int scint_lightcurve(const scint_params* p, const float* intensity, const double
             const double* tr = tracks + 4 * (t0 + i);
             a.tr[i] = Track{tr[0], tr[1], std::cos(tr[2]), std::sin(tr[2]), tr[3]};
         }
-        SCINT_CUDA(launch_lightcurve(a, s));
+        SCINT_LAUNCH(K_LIGHTCURVE, 20.0 * a.n_tracks * (double)n_samples, 0.0, s, launch_lightcurve(a, s));
     }
     return ok();
 }
@@ -385,14 +463,49 @@ int scint_modulation_index(const scint_params* p, const float* intensity, double
         }
     }
     double* partial = c.take<double>((size_t)kMomentBlocks * 2 * sizeof(double));
-    SCINT_CUDA(launch_map_moments(intensity, n, i0, i1, i0, i1, partial, out, s));
+    // two kernels: per-block partial sums, then the final reduction
+    const int rc2 = launch_timed(K_MOMENTS, 4.0 * (double)(i1 - i0) * (i1 - i0), 0.0, s,
+                                 [&] { return launch_map_moments(intensity, n, i0, i1, i0, i1, partial, out, s); }, 2);
+    if (rc2) return rc2;
     return ok();
 }
 
 int scint_curve_modulation(const float* curves, int n_curves, int n_samples, double* out, void* stream) {
     if (n_curves < 0 || n_samples < 1) return fail(SCINT_EINVAL, "need n_curves >= 0 and n_samples >= 1");
     if (n_curves > 0 && (!curves || !out)) return fail(SCINT_EINVAL, "curves and out must be device pointers");
-    SCINT_CUDA(launch_curve_moments(curves, n_curves, n_samples, out, static_cast<cudaStream_t>(stream)));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SCINT_LAUNCH(K_MOMENTS, 4.0 * (double)n_curves * n_samples, 0.0, s,
+                 launch_curve_moments(curves, n_curves, n_samples, out, s));
+    return ok();
+}
+
+int scint_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    prof_clear_locked();
+    g_prof.on = on != 0;
+    return ok();
+}
+
+int scint_profile_read(scint_kernel_stat* stats, int max_stats, int* n_stats) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    scint_kernel_stat acc[K_COUNT];
+    memset(acc, 0, sizeof acc);
+    for (int c = 0; c < K_COUNT; ++c) snprintf(acc[c].name, sizeof acc[c].name, "%s", kClassName[c]);
+    for (auto& r : g_prof.recs) {
+        float ms = 0.0f;
+        const cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return fail(SCINT_ECUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+        const cudaError_t e2 = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e2 != cudaSuccess) return fail(SCINT_ECUDA, "cudaEventElapsedTime: %s", cudaGetErrorString(e2));
+        acc[r.cls].launches += r.kernels;
+        acc[r.cls].total_ms += ms;
+        acc[r.cls].bytes += r.bytes;
+        acc[r.cls].flops += r.flops;
+    }
+    int k = 0;
+    for (int c = 0; c < K_COUNT; ++c)
+        if (acc[c].launches && k < max_stats) stats[k++] = acc[c];
+    if (n_stats) *n_stats = k;
     return ok();
 }
 

@@ -39,7 +39,8 @@ struct SynthArgs {
     double2* work;       // n*n complex128, strip layout
     double* phi;         // n*n, row-major
 };
-cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s);
+cudaError_t launch_synth_rows(const SynthArgs& a, cudaStream_t s);
+cudaError_t launch_synth_cols(const SynthArgs& a, cudaStream_t s);
 
 // Test hooks: raw Philox words and the shaped spectrum F (row-major, FFT order).
 cudaError_t launch_noise_words(int n, uint32_t screen_id, uint32_t k0, uint32_t k1,
@@ -84,7 +85,8 @@ struct SmoothArgs {
     float2* spec;            // (n/2 + 1) x n complex64, row-major [ky][x]
     float* intensity;        // n*n in/out
 };
-cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t s);
+// which = 0: forward column pass, 1: row pass, 2: inverse column pass
+cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s);
 
 // -------- observables --------------------------------------------------------
 struct Track { double x0, y0, c, s, ds; };

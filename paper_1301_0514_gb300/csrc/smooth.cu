@@ -113,26 +113,28 @@ smooth_inv_cols_kernel(SmoothArgs a) {
 template <int N> constexpr size_t scol_smem() { return (size_t)scol_lines<N>() * FftPlan<N>::BUF * sizeof(float2); }
 template <int N> constexpr size_t srow_smem() { return (size_t)srow_lines<N>() * FftPlan<N>::BUF * sizeof(float2); }
 
-cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t s) {
+// which = 0: forward column pass, 1: row pass, 2: inverse column pass
+cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
         if constexpr (N < 32) {
             return cudaErrorNotSupported;
         } else {
             cudaError_t e;
-            if ((e = set_smem(smooth_fwd_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
-            if ((e = set_smem(smooth_rows_kernel<N>, srow_smem<N>())) != cudaSuccess) return e;
-            if ((e = set_smem(smooth_inv_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
             // every block of the column passes holds W line pairs = 2W real columns
             const int col_blocks = N / (2 * scol_lines<N>());
-            if (col_blocks < 1) return cudaErrorNotSupported;
-            smooth_fwd_cols_kernel<N><<<col_blocks, scol_threads<N>(), scol_smem<N>(), s>>>(a);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            const int rows = N / 2 + 1;
-            smooth_rows_kernel<N><<<(rows + srow_lines<N>() - 1) / srow_lines<N>(), srow_threads<N>(),
-                                    srow_smem<N>(), s>>>(a);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            smooth_inv_cols_kernel<N><<<col_blocks, scol_threads<N>(), scol_smem<N>(), s>>>(a);
+            if (which == 0) {
+                if ((e = set_smem(smooth_fwd_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
+                smooth_fwd_cols_kernel<N><<<col_blocks, scol_threads<N>(), scol_smem<N>(), s>>>(a);
+            } else if (which == 1) {
+                if ((e = set_smem(smooth_rows_kernel<N>, srow_smem<N>())) != cudaSuccess) return e;
+                const int rows = N / 2 + 1;
+                smooth_rows_kernel<N><<<(rows + srow_lines<N>() - 1) / srow_lines<N>(), srow_threads<N>(),
+                                        srow_smem<N>(), s>>>(a);
+            } else {
+                if ((e = set_smem(smooth_inv_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
+                smooth_inv_cols_kernel<N><<<col_blocks, scol_threads<N>(), scol_smem<N>(), s>>>(a);
+            }
             return cudaGetLastError();
         }
     });

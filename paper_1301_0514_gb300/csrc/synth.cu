@@ -125,7 +125,8 @@ synth_cols_kernel(SynthArgs a) {
     for (int m = 0; m < E; ++m) a.phi[(size_t)(t + m * T) * N + x] = a.out_scale * v[m].x;
 }
 
-cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s) {
+template <bool ROWS>
+cudaError_t launch_synth_pass(const SynthArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
         if constexpr (N > 8192) {
@@ -133,18 +134,16 @@ cudaError_t launch_synth(const SynthArgs& a, cudaStream_t s) {
         } else {
             constexpr int threads = synth_threads<N>();
             constexpr size_t smem = (size_t)synth_lines<N>() * FftPlan<N>::BUF * sizeof(double2);
-            cudaError_t e = set_smem(synth_rows_kernel<N>, smem);
+            auto k = ROWS ? synth_rows_kernel<N> : synth_cols_kernel<N>;
+            cudaError_t e = set_smem(k, smem);
             if (e != cudaSuccess) return e;
-            e = set_smem(synth_cols_kernel<N>, smem);
-            if (e != cudaSuccess) return e;
-            synth_rows_kernel<N><<<N / synth_lines<N>(), threads, smem, s>>>(a);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            synth_cols_kernel<N><<<N / synth_lines<N>(), threads, smem, s>>>(a);
+            k<<<N / synth_lines<N>(), threads, smem, s>>>(a);
             return cudaGetLastError();
         }
     });
 }
+cudaError_t launch_synth_rows(const SynthArgs& a, cudaStream_t s) { return launch_synth_pass<true>(a, s); }
+cudaError_t launch_synth_cols(const SynthArgs& a, cudaStream_t s) { return launch_synth_pass<false>(a, s); }
 
 // ---- test hooks --------------------------------------------------------------
 __global__ void noise_words_kernel(int n, uint32_t sid, uint32_t k0, uint32_t k1, uint32_t* out) {
