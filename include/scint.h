@@ -125,6 +125,26 @@ int scint_propagate(const scint_params* p, const double* phi, float* intensity,
                     void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * scint_propagate without any device allocation.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc and cannot pass
+ * a workspace either, e.g. hosts that forbid device allocation once running
+ * (fixed-budget real-time loops) or plugins inside a framework that owns all
+ * device memory.  The caller still passes phi and intensity exactly as for
+ * scint_propagate, and gets the same result.
+ *   - Scratch comes from one static device array of 8 MiB + 64 KiB inside the
+ *     library, so n is limited to 1024; larger n returns SCINT_EINVAL.  Every
+ *     GPU that loads the library holds the array until the process exits.
+ *   - The first call on each device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the array, and each call leaves its scratch contents
+ *     behind; nothing in it needs clearing between calls.  Calls whose
+ *     executions overlap on the GPU (different streams, or several host
+ *     threads) race on the array: serialise them.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ */
+int scint_propagate_noalloc(const scint_params* p, const double* phi, float* intensity, void* stream);
+
+/*
  * Passband co-addition (Sect. 3.2.4): intensity = sum_l w_l I(lambda_l) with
  * the same screen phase scaled by lambda_ref/lambda_l.
  *   lambdas_nm  host, n_lambda wavelengths (1..SCINT_MAX_LAMBDA).

@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         "scint_workspace_bytes": ([_P, _i], _sz),
         "scint_make_screen": ([_P, _vp, _vp, _sz, _vp], _i),
         "scint_propagate": ([_P, _vp, _vp, _vp, _sz, _vp], _i),
+        "scint_propagate_noalloc": ([_P, _vp, _vp, _vp], _i),
         "scint_sum_passband": ([_P, _vp, _vp, _vp, _i, _vp, _i, _vp, _sz, _vp], _i),
         "scint_smooth_source": ([_P, _vp, _vp, _sz, _vp], _i),
         "scint_lightcurve": ([_P, _vp, _vp, _i, _i, _vp, _vp], _i),

@@ -327,6 +327,41 @@ SynthArgs synth_args(const scint_params* p) {
 
 }  // namespace
 
+namespace {
+
+// ---- propagation from a static scratch array ------------------------------------
+// For callers that cannot allocate device memory themselves and cannot hand the
+// library a workspace (hosts that forbid device allocation once running, such
+// as fixed-budget real-time loops, or plugins inside a framework that owns all
+// device memory).  Scratch lives in this fixed array instead; every GPU that
+// loads the library keeps it for the life of the process.
+constexpr int kStaticMaxN = 1024;
+constexpr size_t kStaticScratchBytes = (size_t)8 * 1024 * 1024 + 64 * 1024;   // >= ws_prop(1024, 1)
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+std::vector<void*> g_static_addr;   // device address of g_static_scratch, per device
+
+// The array's name in host code is only a host-side handle: its device address
+// is looked up once per device, with that device current.
+int static_scratch_address(void** out) {
+    int dev = 0;
+    SCINT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if ((int)g_static_addr.size() <= dev) g_static_addr.resize(dev + 1, nullptr);
+    if (!g_static_addr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(SCINT_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+        g_static_addr[dev] = ptr;
+    }
+    *out = g_static_addr[dev];
+    return SCINT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int scint_version(void) { return 100; }
@@ -370,6 +405,23 @@ int scint_propagate(const scint_params* p, const double* phi, float* intensity, 
     if (!p) return fail(SCINT_EINVAL, "params is NULL");
     const double lam = p->lambda_nm, w = 1.0;
     return passband_impl(p, phi, &lam, &w, 1, intensity, 0, workspace, workspace_bytes,
+                         static_cast<cudaStream_t>(stream));
+}
+
+int scint_propagate_noalloc(const scint_params* p, const double* phi, float* intensity, void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->n > kStaticMaxN || ws_prop(p->n, 1) > kStaticScratchBytes)
+        return fail(SCINT_EINVAL, "n=%d exceeds the static scratch limit n <= %d (%zu bytes) of "
+                                  "scint_propagate_noalloc; use scint_propagate with a workspace",
+                    p->n, kStaticMaxN, kStaticScratchBytes);
+    void* scratch = nullptr;
+    rc = static_scratch_address(&scratch);
+    if (rc) return rc;
+    // Everything in the scratch (twiddles, tables, field) is written before it is
+    // read, so stale contents from the previous call need no clearing.
+    const double lam = p->lambda_nm, w = 1.0;
+    return passband_impl(p, phi, &lam, &w, 1, intensity, 0, scratch, kStaticScratchBytes,
                          static_cast<cudaStream_t>(stream));
 }
 
