@@ -23,6 +23,8 @@ LIB = os.path.join(PKG, "libscint.so")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# extra nvcc flags, e.g. build-time tuning choices such as -DSCINT_PROP_TWIDDLES=2
+FLAGS += os.environ.get("SCINT_NVCC_FLAGS", "").split()
 
 
 def _sources():

@@ -15,7 +15,9 @@
 // for each butterfly i in [0, N/R):  k = i mod P,
 //   u_r = x[i + r N/R] * W_{PR}^{r k},  y = DFT_R(u),  out[(i/P) P R + k + r P] = y_r.
 // DIR = -1 is the forward transform exp(-2 pi i k x / N); DIR = +1 the inverse
-// (unnormalised).  Twiddles come from a table tw[j] = exp(-2 pi i j / N).
+// (unnormalised).  Twiddles come either from the global table
+// tw[j] = exp(-2 pi i j / N) or from a per-block shared copy laid out [k][r]
+// per stage (conflict-free for consecutive k).
 #pragma once
 
 #include "common.cuh"
@@ -154,7 +156,26 @@ struct FftPlan {
     static constexpr int BUF = N + N / 16;               // padded buffer length
     __host__ __device__ static constexpr int radix(int s) { return s == 0 ? R0 : (s <= N16 ? 16 : (1 << TAIL)); }
     __host__ __device__ static constexpr int span(int s) { return s == 0 ? 1 : span(s - 1) * radix(s - 1); }
+    // shared twiddle table: for each stage s >= 1, entries [k][r - 1] = W_{PR}^{r k}
+    __host__ __device__ static constexpr int twoff(int s) {
+        return s <= 1 ? 0 : twoff(s - 1) + (radix(s - 1) - 1) * span(s - 1);
+    }
+    static constexpr int TWS = twoff(NSTAGE);            // table entries
 };
+
+// Fill a block's shared twiddle table from the global table tw[j] = exp(-2 pi i j / N).
+template <typename C, int N>
+SCINT_DEV void fill_twiddle_table(C* tws, const C* __restrict__ tw, int tid, int nthreads) {
+    using Pl = FftPlan<N>;
+#pragma unroll
+    for (int s = 1; s < Pl::NSTAGE; ++s) {
+        const int R = Pl::radix(s), P = Pl::span(s), base = Pl::twoff(s);
+        for (int e = tid; e < (R - 1) * P; e += nthreads) {
+            const int k = e / (R - 1), r = e % (R - 1) + 1;
+            tws[base + e] = __ldg(tw + r * k * (N / (P * R)));
+        }
+    }
+}
 
 SCINT_DEV int pad16(int a) { return a + (a >> 4); }
 
@@ -162,33 +183,60 @@ template <typename C>
 SCINT_DEV C ld_tw(const C* __restrict__ p) { return __ldg(p); }
 
 
-// Twiddles W_{PR}^{r k} = tw[r step], r = 1..R-1, from at most two table loads
-// (r = 1 and r = 4); the rest are products of depth <= 3 (a few ulp).
-template <int R, int DIR, typename C>
-SCINT_DEV void twiddle_set(const C* __restrict__ tw, int step, C (&w)[R]) {
-    if constexpr (R >= 2) w[1] = ld_tw(tw + step);
-    if constexpr (R >= 4) { w[2] = cmul(w[1], w[1]); w[3] = cmul(w[1], w[2]); }
+// LW: lane width of the buffer.  Element e of the line sits at buf[pad16(e) * LW]
+// (the caller offsets buf by its lane), so LW lines can share one interleaved
+// buffer with consecutive threads of different lines hitting consecutive banks.
+// Per-thread twiddle bases kept in registers across many transforms: for every
+// stage s >= 1 and butterfly b of thread t, W^k and W^{4k} (W = W_{PR},
+// k = (t + b T) mod P); the other powers are products of depth <= 3.
+template <typename C, int N, int EPT>
+struct TwiddleRegs {
+    using Pl = FftPlan<N, EPT>;
+    static constexpr int NS = Pl::NSTAGE > 1 ? Pl::NSTAGE : 2;
+    static constexpr int MAXNB = Pl::E;     // >= E / R for every stage
+    C w[NS][MAXNB][2];
+    SCINT_DEV void load(const C* __restrict__ tw, int t) {
+#pragma unroll
+        for (int s = 1; s < Pl::NSTAGE; ++s) {
+            const int R = Pl::radix(s), P = Pl::span(s);
+#pragma unroll
+            for (int b = 0; b < Pl::E / R; ++b) {
+                const int k = (t + b * Pl::T) & (P - 1);
+                const int step = k * (N / (P * R));
+                w[s][b][0] = __ldg(tw + step);
+                w[s][b][1] = R >= 8 ? __ldg(tw + 4 * step) : w[s][b][0];
+            }
+        }
+    }
+};
+
+// powers r = 1..R-1 of a base twiddle from (W^k, W^{4k})
+template <int R, typename C>
+SCINT_DEV void twiddle_powers(C w1, C w4, C (&w)[R]) {
+    if constexpr (R >= 2) w[1] = w1;
+    if constexpr (R >= 4) { w[2] = cmul(w1, w1); w[3] = cmul(w1, w[2]); }
     if constexpr (R >= 8) {
-        w[4] = ld_tw(tw + 4 * step);
-        w[5] = cmul(w[4], w[1]);
-        w[6] = cmul(w[4], w[2]);
-        w[7] = cmul(w[4], w[3]);
+        w[4] = w4;
+        w[5] = cmul(w4, w1);
+        w[6] = cmul(w4, w[2]);
+        w[7] = cmul(w4, w[3]);
     }
     if constexpr (R >= 16) {
-        w[8] = cmul(w[4], w[4]);
+        w[8] = cmul(w4, w4);
 #pragma unroll
         for (int r = 9; r < 12; ++r) w[r] = cmul(w[8], w[r - 8]);
-        w[12] = cmul(w[8], w[4]);
+        w[12] = cmul(w[8], w4);
 #pragma unroll
         for (int r = 13; r < 16; ++r) w[r] = cmul(w[12], w[r - 12]);
     }
 }
 
-// LW: lane width of the buffer.  Element e of the line sits at buf[pad16(e) * LW]
-// (the caller offsets buf by its lane), so LW lines can share one interleaved
-// buffer with consecutive threads of different lines hitting consecutive banks.
-template <typename C, int N, int DIR, int EPT, int LW, int S>
-SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw) {
+// Twiddle source TWM: 0 = global table tw[j] = exp(-2 pi i j / N); 1 = the
+// block's shared table (fill_twiddle_table; tw points to it); 2 = register
+// bases (tr).
+template <typename C, int N, int DIR, int EPT, int LW, int TWM, int S>
+SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw,
+                         const TwiddleRegs<C, N, EPT>* tr) {
     using Pl = FftPlan<N, EPT>;
     constexpr int E = Pl::E, T = Pl::T;
     constexpr int R = Pl::radix(S), P = Pl::span(S), NB = E / R;
@@ -215,10 +263,20 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
         const int i = t + b * T;
         if constexpr (!FIRST) {
             const int k = i & (P - 1);
-            C w[R];
-            twiddle_set<R, DIR>(tw, k * (N / (P * R)), w);   // W_{PR}^{r k} = tw[r * step]
+            if constexpr (TWM == 2) {
+                C w[R];
+                twiddle_powers<R>(tr->w[S][b][0], tr->w[S][b][1], w);
 #pragma unroll
-            for (int r = 1; r < R; ++r) u[b * R + r] = DIR < 0 ? cmul(u[b * R + r], w[r]) : cmulc(u[b * R + r], w[r]);
+                for (int r = 1; r < R; ++r) u[b * R + r] = DIR < 0 ? cmul(u[b * R + r], w[r]) : cmulc(u[b * R + r], w[r]);
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    // W_{PR}^{r k}: shared entry [k][r - 1] or global tw[r k N / (P R)]
+                    const C w = TWM == 1 ? tw[Pl::twoff(S) + k * (R - 1) + (r - 1)]
+                                         : ld_tw(tw + r * k * (N / (P * R)));
+                    u[b * R + r] = DIR < 0 ? cmul(u[b * R + r], w) : cmulc(u[b * R + r], w);
+                }
+            }
         }
         dft<R, DIR>(&u[b * R]);
     }
@@ -239,15 +297,21 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
             for (int r = 0; r < R; ++r) dst[(P >= 16 ? r * (P + P / 16) : r) * LW] = u[b * R + r];
         }
         __syncthreads();
-        fft_stage<C, N, DIR, EPT, LW, S + 1>(v, buf, t, tw);
+        fft_stage<C, N, DIR, EPT, LW, TWM, S + 1>(v, buf, t, tw, tr);
     }
 }
 
 // Transform the team's line in place (registers v, distribution t + m*T).
 // Every thread of the block must call this the same number of times.
-template <typename C, int N, int DIR, int EPT = 16, int LW = 1>
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0>
 SCINT_DEV void fft_line(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw) {
-    fft_stage<C, N, DIR, EPT, LW, 0>(v, buf, t, tw);
+    static_assert(TWM != 2, "register twiddles: use fft_line_tr");
+    fft_stage<C, N, DIR, EPT, LW, TWM, 0>(v, buf, t, tw, nullptr);
+}
+
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1>
+SCINT_DEV void fft_line_tr(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const TwiddleRegs<C, N, EPT>& tr) {
+    fft_stage<C, N, DIR, EPT, LW, 2, 0>(v, buf, t, nullptr, &tr);
 }
 
 }  // namespace scint

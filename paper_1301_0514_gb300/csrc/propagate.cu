@@ -20,7 +20,15 @@
 #include "fft.cuh"
 #include "kernels.cuh"
 
+// Twiddle source of the propagation FFTs (a build-time tuning choice):
+// 1 = per-block shared table, 2 = per-thread register bases + products.
+#ifndef SCINT_PROP_TWIDDLES
+#define SCINT_PROP_TWIDDLES 1
+#endif
+
 namespace scint {
+
+constexpr int kPropTw = SCINT_PROP_TWIDDLES;
 
 template <int N> __host__ __device__ constexpr int prow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N ? kTileRow32 / N : N); }
 template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T; }
@@ -75,9 +83,14 @@ prop_rows_kernel(PropArgs a) {
     // fixed-point phase of this thread's pixels, kept in shared memory across the
     // wavelength loop (each thread reads back only the entries it wrote)
     long long* P = reinterpret_cast<long long*>(smem32 + B * Pl::BUF) + team * N + t;
+    float2* tws = smem32 + B * Pl::BUF + B * N;   // shared twiddle table (after P, 8 B per entry)
+    TwiddleRegs<float2, N, 16> tr;
+    if constexpr (kPropTw == 2) tr.load(a.tw, t);
+    else fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
     const double to_fixed = 4294967296.0 / (2.0 * kPi);
 #pragma unroll
     for (int m = 0; m < E; ++m) P[m * T] = __double2ll_rn(a.phi[(size_t)y * N + t + m * T] * to_fixed);
+    __syncthreads();
 
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
@@ -89,16 +102,19 @@ prop_rows_kernel(PropArgs a) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const unsigned long long prod = (unsigned long long)P[m * T] * S;   // frac(phi s) * 2^64
-            const float tt = (float)(int)(prod >> 32) * 0x1.0p-32f;          // turns in [-1/2, 1/2)
+            // angle in [-pi, pi): the hardware sine/cosine (abs. error ~4e-7 there) suffices
+            const float ang = (float)(int)(prod >> 32) * (float)(2.0 * kPi * 0x1.0p-32);
             float sn, cs;
-            sincospif(2.0f * tt, &sn, &cs);
+            __sincosf(ang, &sn, &cs);
             const float amp = sfy * __ldg(sf + t + m * T);
             v[m] = make_float2(amp * cs, amp * sn);
         }
-        fft_line<float2, N, -1>(v, buf, t, a.tw);
+        if constexpr (kPropTw == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
+        else fft_line<float2, N, -1, 16, 1, 1>(v, buf, t, tws);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
-        fft_line<float2, N, +1>(v, buf, t, a.tw);
+        if constexpr (kPropTw == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
+        else fft_line<float2, N, +1, 16, 1, 1>(v, buf, t, tws);
         float2* dst = a.work + (size_t)l * N * N;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -120,8 +136,13 @@ prop_cols_kernel(PropArgs a) {
     float2* buf = smem32 + w;     // W lines interleaved: element e of line w at pad16(e) * W + w
     // passband accumulator of this thread's pixels (own entries only)
     float* acc = reinterpret_cast<float*>(smem32 + W * Pl::BUF) + w * N + t;
+    float2* tws = smem32 + W * Pl::BUF + (W * N) / 2;   // shared twiddle table (after acc)
+    TwiddleRegs<float2, N, kColEPT> tr;
+    if constexpr (kPropTw == 2) tr.load(a.tw, t);
+    else fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
     for (int m = 0; m < E; ++m) acc[m * T] = 0.0f;
+    __syncthreads();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         const float2* src = a.work + (size_t)l * N * N + (size_t)blockIdx.x * N * W;
@@ -129,10 +150,12 @@ prop_cols_kernel(PropArgs a) {
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * W + w];
-        fft_line<float2, N, -1, kColEPT, W>(v, buf, t, a.tw);
+        if constexpr (kPropTw == 2) fft_line_tr<float2, N, -1, kColEPT, W>(v, buf, t, tr);
+        else fft_line<float2, N, -1, kColEPT, W, 1>(v, buf, t, tws);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
-        fft_line<float2, N, +1, kColEPT, W>(v, buf, t, a.tw);
+        if constexpr (kPropTw == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
+        else fft_line<float2, N, +1, kColEPT, W, 1>(v, buf, t, tws);
         const float wl = a.lam.weight[l];
 #pragma unroll
         for (int m = 0; m < E; ++m) acc[m * T] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m * T]);
@@ -145,10 +168,12 @@ prop_cols_kernel(PropArgs a) {
 }
 
 template <int N> constexpr size_t prow_smem() {
-    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long));
+    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) +
+           (kPropTw == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0);
 }
 template <int N> constexpr size_t pcol_smem() {
-    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float));
+    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float)) +
+           (kPropTw == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0);
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
