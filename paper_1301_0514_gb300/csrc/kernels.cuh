@@ -18,9 +18,10 @@ constexpr int kTileCol32 = 8192;    // FP32 line passes over columns
 constexpr int kTile64 = 4096;       // FP64 synthesis passes
 
 // Intermediates between a row pass and a column pass use the "strip layout":
-// element (y, x) of an N x N field sits at (x / W) * N * W + y * W + x % W, W the
-// number of columns one column-pass block holds, so that block reads one
-// contiguous strip.
+// element (y, x) of an N x N field sits at (x / W) * N * W + y * W + x % W, so
+// that the column pass reads contiguous strips; W is at least the number of
+// columns one column-pass block holds, and for FP32 fields at least 4 (whole
+// 32-byte sectors per row written by the row pass).
 
 // -------- tables ------------------------------------------------------------
 // tw[j] = exp(-2 pi i j / n), j < n, rounded from FP64.

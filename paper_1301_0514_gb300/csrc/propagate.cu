@@ -33,6 +33,10 @@ constexpr int kPropTw = SCINT_PROP_TWIDDLES;
 template <int N> __host__ __device__ constexpr int prow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N ? kTileRow32 / N : N); }
 template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T; }
 template <int N> __host__ __device__ constexpr int pcol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N ? kTileCol32 / N : N); }
+// Strip width of the intermediate: at least 4 columns, so that every row of the
+// row pass writes whole 32-byte sectors; a column block then reads its
+// pcol_lines() columns out of one strip (sibling blocks share the sectors in L2).
+template <int N> __host__ __device__ constexpr int pstrip() { return pcol_lines<N>() >= 4 ? pcol_lines<N>() : (N >= 4 ? 4 : N); }
 constexpr int kColEPT = 16;   // values per thread in the column pass
 template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_lines<N>() * FftPlan<N, kColEPT>::T; }
 
@@ -75,7 +79,7 @@ template <int N>
 __global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
 prop_rows_kernel(PropArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), W = pcol_lines<N>();
+    constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), W = pstrip<N>();
     extern __shared__ float2 smem32[];
     const int team = threadIdx.x / T, t = threadIdx.x % T;
     const int y = blockIdx.x * B + team;
@@ -129,10 +133,11 @@ template <int N>
 __global__ void __launch_bounds__(pcol_threads<N>(), 1)
 prop_cols_kernel(PropArgs a) {
     using Pl = FftPlan<N, kColEPT>;
-    constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>();
+    constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
     extern __shared__ float2 smem32[];
     const int w = threadIdx.x % W, t = threadIdx.x / W;
     const int x = blockIdx.x * W + w;
+    const int x0 = blockIdx.x * W;    // first column of the block: strip x0 / WL, offset x0 % WL
     float2* buf = smem32 + w;     // W lines interleaved: element e of line w at pad16(e) * W + w
     // passband accumulator of this thread's pixels (own entries only)
     float* acc = reinterpret_cast<float*>(smem32 + W * Pl::BUF) + w * N + t;
@@ -145,11 +150,11 @@ prop_cols_kernel(PropArgs a) {
     __syncthreads();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
-        const float2* src = a.work + (size_t)l * N * N + (size_t)blockIdx.x * N * W;
+        const float2* src = a.work + (size_t)l * N * N + (size_t)(x0 / WL) * N * WL + (x0 % WL);
         const float2* h = a.h + (size_t)l * N;
         float2 v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * W + w];
+        for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * WL + w];
         if constexpr (kPropTw == 2) fft_line_tr<float2, N, -1, kColEPT, W>(v, buf, t, tr);
         else fft_line<float2, N, -1, kColEPT, W, 1>(v, buf, t, tws);
 #pragma unroll

@@ -88,12 +88,14 @@ SCINT_DEV double2 spectrum_bin(const SynthArgs& a, int kx, int ky) {
 
 template <int N> __host__ __device__ constexpr int synth_lines() { return N >= kTile64 ? 1 : (kTile64 / N < N ? kTile64 / N : N); }
 template <int N> __host__ __device__ constexpr int synth_threads() { return synth_lines<N>() * FftPlan<N>::T; }
+// strip width of the intermediate: at least 2 complex128 columns (whole 32-byte sectors per row)
+template <int N> __host__ __device__ constexpr int synth_strip() { return synth_lines<N>() >= 2 ? synth_lines<N>() : 2; }
 
 template <int N>
 __global__ void __launch_bounds__(synth_threads<N>())
 synth_rows_kernel(SynthArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int T = Pl::T, E = Pl::E, B = synth_lines<N>(), W = B;
+    constexpr int T = Pl::T, E = Pl::E, B = synth_lines<N>(), W = synth_strip<N>();
     extern __shared__ double2 smem64[];
     const int team = threadIdx.x / T, t = threadIdx.x % T;
     const int ky = blockIdx.x * B + team;
@@ -112,14 +114,15 @@ template <int N>
 __global__ void __launch_bounds__(synth_threads<N>())
 synth_cols_kernel(SynthArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int T = Pl::T, E = Pl::E, W = synth_lines<N>();
+    constexpr int T = Pl::T, E = Pl::E, W = synth_lines<N>(), WL = synth_strip<N>();
     extern __shared__ double2 smem64[];
     const int w = threadIdx.x % W, t = threadIdx.x / W;
     const int x = blockIdx.x * W + w;
-    const double2* src = a.work + (size_t)blockIdx.x * N * W;
+    const int x0 = blockIdx.x * W;
+    const double2* src = a.work + (size_t)(x0 / WL) * N * WL + (x0 % WL);
     double2 v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * W + w];
+    for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * WL + w];
     fft_line<double2, N, +1, 16, W>(v, smem64 + w, t, a.tw);     // W lines interleaved
 #pragma unroll
     for (int m = 0; m < E; ++m) a.phi[(size_t)(t + m * T) * N + x] = a.out_scale * v[m].x;
