@@ -201,6 +201,36 @@ int scint_modulation_index(const scint_params* p, const float* intensity, double
 int scint_curve_modulation(const float* curves, int n_curves, int n_samples,
                            double* out, void* stream);
 
+/*
+ * Gradient of a light-curve misfit with respect to the phase screen (reverse
+ * mode through Sect. 3.2-3.3; the paper states no gradient, this is the
+ * adjoint of the forward path of this library).  The forward map is
+ *   curves = lightcurve(smooth_source(sum_passband(phi)))
+ * with the same parameters; given grad_curves = dL/dcurves this computes
+ *   grad_phi = dL/dphi = sum_l s_l Im(conj(A_in,l) P_l^H (2 w_l g_I A_out,l)),
+ *   g_I = K B^T grad_curves  (B: bilinear sampling, K: disk filter, both as in
+ *   the forward calls), s_l = lambda_ref/lambda_l.
+ * The forward fields are recomputed (never stored).
+ *   lambdas_nm, weights, tracks  host, as in scint_sum_passband / scint_lightcurve.
+ *   grad_curves  device, n_tracks * n_samples floats.
+ *   grad_phi     device, N*N doubles, written (accumulate == 0) or added to.
+ * Workspace: scint_workspace_bytes(p, n_lambda) covers it.
+ */
+int scint_lightcurve_adjoint(const scint_params* p, const double* phi,
+                             const double* lambdas_nm, const double* weights, int n_lambda,
+                             const double* tracks, int n_tracks, int n_samples,
+                             const float* grad_curves, double* grad_phi, int accumulate,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * dL/dR_diff from dL/dphi: at a fixed seed the synthesised screen scales as
+ * R_diff^((2 - beta)/2) (Eq. spectre: sigma ~ R_diff^(1 - beta/2)), so
+ *   out[0] = ((2 - beta) / (2 R_diff)) sum_j phi_j grad_phi_j   (FP64).
+ *   out  device, 1 double.  Needs workspace (a few KB).
+ */
+int scint_rdiff_gradient(const scint_params* p, const double* phi, const double* grad_phi, double* out,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
 /* Release the library's internal per-device workspace pools and tables. */
 void scint_release(void);
 

@@ -11,6 +11,7 @@ from ._lib import (  # noqa: F401
     fft_lines,
     lib,
     lightcurve,
+    lightcurve_adjoint,
     make_screen,
     modulation_index,
     noise_spectrum,
@@ -19,10 +20,13 @@ from ._lib import (  # noqa: F401
     profile_enable,
     profile_read,
     propagate,
+    rdiff_gradient,
     release,
     smooth_source,
     sum_passband,
     workspace_bytes,
 )
+
+from .autograd import light_curves, screen  # noqa: F401,E402
 
 __version__ = "0.1.0"

@@ -103,6 +103,8 @@ def lib() -> ctypes.CDLL:
         "scint_noise_spectrum": ([_P, _vp, _vp], _i),
         "scint_fft_lines32": ([_i, _i, _vp, _i, _vp], _i),
         "scint_fft_lines64": ([_i, _i, _vp, _i, _vp], _i),
+        "scint_lightcurve_adjoint": ([_P, _vp, _vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, _sz, _vp], _i),
+        "scint_rdiff_gradient": ([_P, _vp, _vp, _vp, _vp, _sz, _vp], _i),
         "scint_profile_enable": ([_i], _i),
         "scint_profile_read": ([ctypes.POINTER(KernelStat), _i, ctypes.POINTER(_i)], _i),
     }
@@ -216,6 +218,36 @@ def curve_modulation(curves: torch.Tensor, out: Optional[torch.Tensor] = None, s
         out = torch.empty((nc, 3), dtype=torch.float64, device=curves.device)
     _check(lib().scint_curve_modulation(_dev(curves, torch.float32, nc * ns, "curves"), nc, ns,
                                         _dev(out, torch.float64, nc * 3, "out"), _stream(stream)))
+    return out
+
+
+def lightcurve_adjoint(p: ScintParams, phi: torch.Tensor, lambdas_nm, tracks, n_samples: int,
+                       grad_curves: torch.Tensor, weights=None, out: Optional[torch.Tensor] = None,
+                       accumulate: bool = False, workspace=None, stream=None) -> torch.Tensor:
+    """dL/dphi (N x N float64) for the forward curves = lightcurve(smooth(sum_passband(phi)))."""
+    lam = np.ascontiguousarray(lambdas_nm, dtype=np.float64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    tr = np.ascontiguousarray(tracks, dtype=np.float64).reshape(-1, 4)
+    if out is None:
+        out = torch.empty((p.n, p.n), dtype=torch.float64, device=phi.device)
+    ws, wp, wb = _workspace(p, len(lam), workspace, phi.device)
+    _check(lib().scint_lightcurve_adjoint(
+        ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"), lam.ctypes.data_as(ctypes.c_void_p),
+        None if w is None else w.ctypes.data_as(ctypes.c_void_p), len(lam),
+        tr.ctypes.data_as(ctypes.c_void_p), tr.shape[0], n_samples,
+        _dev(grad_curves, torch.float32, tr.shape[0] * n_samples, "grad_curves"),
+        _dev(out, torch.float64, p.n * p.n, "grad_phi"), int(bool(accumulate)), wp, wb, _stream(stream)))
+    return out
+
+
+def rdiff_gradient(p: ScintParams, phi: torch.Tensor, grad_phi: torch.Tensor, workspace=None,
+                   stream=None) -> torch.Tensor:
+    """dL/dR_diff (1-element float64 device tensor) from dL/dphi at a fixed seed."""
+    out = torch.empty(1, dtype=torch.float64, device=phi.device)
+    ws, wp, wb = _workspace(p, 1, workspace, phi.device)
+    _check(lib().scint_rdiff_gradient(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
+                                      _dev(grad_phi, torch.float64, p.n * p.n, "grad_phi"),
+                                      _dev(out, torch.float64, 1, "out"), wp, wb, _stream(stream)))
     return out
 
 

@@ -1,0 +1,215 @@
+// Reverse-mode gradient of a light-curve misfit with respect to the phase
+// screen: the adjoint of  phi -> A_in = SF exp(i s phi) -> A_out = P A_in ->
+// I = sum_l w_l |A_out|^2 -> (disk filter) -> bilinear light curves.
+//
+// Given g_c = dL/dcurves:
+//   g_I      = B^T g_c                   (bilinear scatter, this file)
+//   g_I     <- K g_I                     (disk filter is real and even: self-adjoint; smooth.cu)
+//   G_out    = 2 w_l g_I A_out           (complex gradient of |A|^2)
+//   G_in     = P^H G_out = IDFT(DFT(G_out) conj(H))
+//   g_phi   += s_l Im(conj(A_in) G_in)
+// P = P_y P_x is separable, so P^H = P_x^H P_y^H.  Per wavelength group:
+//   forward row pass (propagate.cu) -> field F in the strip layout;
+//   adjoint column pass: FFT_y H_y IFFT_y -> A_out; G_out; FFT_y conj(H_y)
+//                        IFFT_y, written back over F;
+//   adjoint row pass:    FFT_x conj(H_x) IFFT_x -> G_in; A_in recomputed from
+//                        the fixed-point phase; g_phi accumulated over the group.
+// The forward fields are recomputed, never stored.
+#include "dispatch.cuh"
+#include "propagate.cuh"
+
+namespace scint {
+
+// ---- bilinear scatter (transpose of lightcurve_kernel) ---------------------------
+__global__ void lightcurve_adjoint_kernel(CurveAdjArgs a) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (s >= a.n_samples || c >= a.n_tracks) return;
+    const Track tr = a.tr[c];
+    const double d = (double)s * tr.ds;
+    const double x = fma(d, tr.c, tr.x0);
+    const double y = fma(d, tr.s, tr.y0);
+    const double fx = floor(x), fy = floor(y);
+    const float tx = (float)(x - fx), ty = (float)(y - fy);
+    const int n = a.n;
+    long long ix = (long long)fx % n, iy = (long long)fy % n;
+    if (ix < 0) ix += n;
+    if (iy < 0) iy += n;
+    const int ix1 = (int)(ix + 1 == n ? 0 : ix + 1), iy1 = (int)(iy + 1 == n ? 0 : iy + 1);
+    const float g = a.grad_curves[(size_t)c * a.n_samples + s];
+    atomicAdd(a.grad_map + iy * n + ix, g * (1.0f - tx) * (1.0f - ty));
+    atomicAdd(a.grad_map + iy * n + ix1, g * tx * (1.0f - ty));
+    atomicAdd(a.grad_map + (size_t)iy1 * n + ix, g * (1.0f - tx) * ty);
+    atomicAdd(a.grad_map + (size_t)iy1 * n + ix1, g * tx * ty);
+}
+
+cudaError_t launch_lightcurve_adjoint(const CurveAdjArgs& a, cudaStream_t s) {
+    if (a.n_tracks <= 0 || a.n_samples <= 0) return cudaSuccess;
+    dim3 grid((a.n_samples + 255) / 256, a.n_tracks);
+    lightcurve_adjoint_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---- adjoint column pass ----------------------------------------------------------
+// buffers, the g_I columns (in place of the accumulator) and the twiddle table
+template <int N> constexpr size_t acol_smem() {
+    return (size_t)pcol_lines<N>() * (FftPlan<N, kColEPT>::BUF * sizeof(float2) + N * sizeof(float)) +
+           (size_t)FftPlan<N>::TWS * sizeof(float2);
+}
+
+template <int N>
+__global__ void __launch_bounds__(pcol_threads<N>(), 1)
+adj_cols_kernel(AdjArgs a) {
+    using Pl = FftPlan<N, kColEPT>;
+    constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
+    extern __shared__ float2 smem32[];
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int x = blockIdx.x * W + w;
+    const int x0 = blockIdx.x * W;
+    float2* buf = smem32 + w;
+    float* gi = reinterpret_cast<float*>(smem32 + W * Pl::BUF) + w * N + t;   // g_I of this column (own entries)
+    float2* tws = smem32 + W * Pl::BUF + (W * N) / 2;
+    fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+#pragma unroll
+    for (int m = 0; m < E; ++m) gi[m * T] = a.grad_map[(size_t)(t + m * T) * N + x];
+    __syncthreads();
+#pragma unroll 1
+    for (int l = 0; l < a.lam.count; ++l) {
+        float2* f = a.work + (size_t)l * N * N + (size_t)(x0 / WL) * N * WL + (x0 % WL);
+        const float2* h = a.h + (size_t)l * N;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = f[(size_t)(t + m * T) * WL + w];
+        fft_line<float2, N, -1, kColEPT, W, 1>(v, buf, t, tws);
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
+        fft_line<float2, N, +1, kColEPT, W, 1>(v, buf, t, tws);          // A_out of this column
+        const float c2w = 2.0f * a.lam.weight[l];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = v[m] * (c2w * gi[m * T]);     // G_out
+        fft_line<float2, N, -1, kColEPT, W, 1>(v, buf, t, tws);
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], __ldg(h + t + m * T));
+        fft_line<float2, N, +1, kColEPT, W, 1>(v, buf, t, tws);          // P_y^H G_out
+#pragma unroll
+        for (int m = 0; m < E; ++m) f[(size_t)(t + m * T) * WL + w] = v[m];
+    }
+}
+
+// ---- adjoint row pass --------------------------------------------------------------
+// buffers, fixed-point phases, twiddle table, g_phi accumulators
+template <int N> constexpr size_t arow_smem() {
+    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long) + N * sizeof(float)) +
+           (size_t)FftPlan<N>::TWS * sizeof(float2);
+}
+
+template <int N>
+__global__ void __launch_bounds__(prow_threads<N>(), 1)
+adj_rows_kernel(AdjArgs a) {
+    using Pl = FftPlan<N>;
+    constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), WL = pstrip<N>();
+    extern __shared__ float2 smem32[];
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const int y = blockIdx.x * B + team;
+    float2* buf = smem32 + team * Pl::BUF;
+    long long* P = reinterpret_cast<long long*>(smem32 + B * Pl::BUF) + team * N + t;
+    float2* tws = smem32 + B * Pl::BUF + B * N;
+    float* acc = reinterpret_cast<float*>(tws + Pl::TWS) + team * N + t;   // g_phi of this row (own entries)
+    fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        P[m * T] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
+        acc[m * T] = 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int l = 0; l < a.lam.count; ++l) {
+        const float2* f = a.work + (size_t)l * N * N;
+        const float2* h = a.h + (size_t)l * N;
+        const float* sf = a.sf + (size_t)l * N;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = f[strip_index<WL>(y, t + m * T, N)];
+        fft_line<float2, N, -1, 16, 1, 1>(v, buf, t, tws);
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], __ldg(h + t + m * T));
+        fft_line<float2, N, +1, 16, 1, 1>(v, buf, t, tws);              // G_in of this row
+        const unsigned long long S = a.lam.scale_fx[l];
+        const float s_l = a.lam.scale[l], sfy = sf[y];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const float2 A = unit_phasor(P[m * T], S) * (sfy * __ldg(sf + t + m * T));
+            // s Im(conj(A_in) G_in)
+            acc[m * T] = fmaf(s_l, A.x * v[m].y - A.y * v[m].x, acc[m * T]);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        double* o = a.grad_phi + (size_t)y * N + t + m * T;
+        *o = a.accumulate ? *o + (double)acc[m * T] : (double)acc[m * T];
+    }
+}
+
+cudaError_t launch_adj_cols(const AdjArgs& a, cudaStream_t s) {
+    return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
+        constexpr int N = decltype(nc)::value;
+        if constexpr (acol_smem<N>() > kMaxSmem || arow_smem<N>() > kMaxSmem) {
+            return cudaErrorNotSupported;
+        } else {
+            cudaError_t e = set_smem(adj_cols_kernel<N>, acol_smem<N>());
+            if (e != cudaSuccess) return e;
+            adj_cols_kernel<N><<<N / pcol_lines<N>(), pcol_threads<N>(), acol_smem<N>(), s>>>(a);
+            return cudaGetLastError();
+        }
+    });
+}
+
+cudaError_t launch_adj_rows(const AdjArgs& a, cudaStream_t s) {
+    return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
+        constexpr int N = decltype(nc)::value;
+        if constexpr (acol_smem<N>() > kMaxSmem || arow_smem<N>() > kMaxSmem) {
+            return cudaErrorNotSupported;
+        } else {
+            cudaError_t e = set_smem(adj_rows_kernel<N>, arow_smem<N>());
+            if (e != cudaSuccess) return e;
+            adj_rows_kernel<N><<<N / prow_lines<N>(), prow_threads<N>(), arow_smem<N>(), s>>>(a);
+            return cudaGetLastError();
+        }
+    });
+}
+
+// ---- dL/dR_diff = ((2 - beta) / (2 R_diff)) sum phi g_phi (FP64) ----------------------
+__global__ void __launch_bounds__(256) dot_partial_kernel(const double* a, const double* b, long long n,
+                                                          double* partial) {
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s = fma(a[i], b[i], s);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double sw[8];
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 8; ++i) t += sw[i];
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void dot_final_kernel(const double* partial, int nb, double scale, double* out) {
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < nb; ++i) t += partial[i];
+        out[0] = scale * t;
+    }
+}
+
+cudaError_t launch_scaled_dot(const double* a, const double* b, long long n, double scale, double* partial,
+                              double* out, cudaStream_t s) {
+    dot_partial_kernel<<<kMomentBlocks, 256, 0, s>>>(a, b, n, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dot_final_kernel<<<1, 32, 0, s>>>(partial, kMomentBlocks, scale, out);
+    return cudaGetLastError();
+}
+
+}  // namespace scint

@@ -96,6 +96,10 @@ size_t ws_prop(int n, int g) {
     return up((size_t)n * 8) + up((size_t)g * n * 8) + up((size_t)g * n * 4) + up((size_t)g * n * n * 8);
 }
 size_t ws_smooth(int n) { return up((size_t)n * 8) + up((size_t)(n / 2 + 1) * n * 8); }
+// adjoint: twiddles, g_I map, half spectrum for its disk filter, then the propagation group buffers
+size_t ws_adjoint(int n, int g) {
+    return up((size_t)n * n * 4) + up((size_t)(n / 2 + 1) * n * 8) + ws_prop(n, g);
+}
 size_t ws_moments() { return up((size_t)kMomentBlocks * 2 * sizeof(double)); }
 
 struct Carver {
@@ -169,11 +173,13 @@ int resolve_ws(void* ws, size_t bytes, size_t need, cudaStream_t s, Carver* c) {
 // the algorithmic bytes and FFT flops of the launch are attached.
 enum KClass {
     K_TWIDDLES, K_SYNTH_ROWS, K_SYNTH_COLS, K_PROP_TABLES, K_PROP_ROWS, K_PROP_COLS,
-    K_SMOOTH_FWD, K_SMOOTH_ROWS, K_SMOOTH_INV, K_LIGHTCURVE, K_MOMENTS, K_COUNT
+    K_SMOOTH_FWD, K_SMOOTH_ROWS, K_SMOOTH_INV, K_LIGHTCURVE, K_MOMENTS,
+    K_LC_ADJ, K_ADJ_COLS, K_ADJ_ROWS, K_DOT, K_COUNT
 };
 const char* const kClassName[K_COUNT] = {
     "twiddles", "synth_rows", "synth_cols", "prop_tables", "prop_rows", "prop_cols",
-    "smooth_fwd_cols", "smooth_rows", "smooth_inv_cols", "lightcurve", "moments"};
+    "smooth_fwd_cols", "smooth_rows", "smooth_inv_cols", "lightcurve", "moments",
+    "lightcurve_adjoint", "adj_cols", "adj_rows", "dot"};
 
 struct ProfRec {
     int cls;
@@ -251,6 +257,7 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
         ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
         pa.lam.scale_fx[i] = (uint64_t)std::llround(p->lambda_ref_nm / l * 4294967296.0);
         pa.lam.weight[i] = (float)wts[l0 + i];
+        pa.lam.scale[i] = (float)(p->lambda_ref_nm / l);
     }
     Carver cg = c;   // group buffers restart at the same offset for every group
     ta.h = cg.take<float2>((size_t)g * n * 8);
@@ -375,6 +382,7 @@ size_t scint_workspace_bytes(const scint_params* p, int n_lambda) {
     b = std::max(b, ws_prop(n, std::min(n_lambda, SCINT_MAX_LAMBDA)));
     b = std::max(b, ws_smooth(n));
     b = std::max(b, ws_moments());
+    b = std::max(b, ws_adjoint(n, std::min(n_lambda, SCINT_MAX_LAMBDA)));
     return b;
 }
 
@@ -528,6 +536,135 @@ int scint_curve_modulation(const float* curves, int n_curves, int n_samples, dou
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     SCINT_LAUNCH(K_MOMENTS, 4.0 * (double)n_curves * n_samples, 0.0, s,
                  launch_curve_moments(curves, n_curves, n_samples, out, s));
+    return ok();
+}
+
+int scint_lightcurve_adjoint(const scint_params* p, const double* phi, const double* lambdas_nm,
+                             const double* weights, int n_lambda, const double* tracks, int n_tracks,
+                             int n_samples, const float* grad_curves, double* grad_phi, int accumulate,
+                             void* workspace, size_t workspace_bytes, void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!phi || !grad_phi) return fail(SCINT_EINVAL, "phi and grad_phi must be device pointers");
+    if (!lambdas_nm || n_lambda < 1 || n_lambda > SCINT_MAX_LAMBDA)
+        return fail(SCINT_EINVAL, "n_lambda=%d must be in [1, %d]", n_lambda, SCINT_MAX_LAMBDA);
+    if (n_tracks < 0 || n_samples < 0) return fail(SCINT_EINVAL, "negative track or sample count");
+    if (n_tracks > 0 && n_samples > 0 && (!tracks || !grad_curves))
+        return fail(SCINT_EINVAL, "tracks (host) and grad_curves (device) are required");
+    for (int i = 0; i < 4 * n_tracks && n_samples > 0; ++i)
+        if (!std::isfinite(tracks[i])) return fail(SCINT_EINVAL, "track parameters must be finite");
+    std::vector<double> w(n_lambda, 1.0 / n_lambda);
+    for (int i = 0; i < n_lambda; ++i) {
+        if (!(lambdas_nm[i] > 0) || !std::isfinite(lambdas_nm[i])) return fail(SCINT_EINVAL, "lambda %d must be > 0", i);
+        if (weights) {
+            if (!std::isfinite(weights[i])) return fail(SCINT_EINVAL, "weight %d is not finite", i);
+            w[i] = weights[i];
+        }
+        if (taper_margin(p, lambdas_nm[i]) > 0.5 * screen_len(p))
+            return fail(SCINT_EINVAL, "taper margin exceeds half the screen");
+    }
+    const int n = p->n;
+    int g = n_lambda;
+    if (workspace) {
+        while (g > 1 && ws_adjoint(n, g) > workspace_bytes) --g;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Carver c{};
+    rc = resolve_ws(workspace, workspace_bytes, ws_adjoint(n, g), s, &c);
+    if (rc) return rc;
+    float* gmap = c.take<float>((size_t)n * n * 4);
+    float2* spec = c.take<float2>((size_t)(n / 2 + 1) * n * 8);
+    Carver cp = c;                       // propagation buffers: twiddles, then group tables and fields
+    float2* tw = cp.take<float2>((size_t)n * 8);
+    const double nn = (double)n * n;
+    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n, 0.0, s, launch_twiddles32(tw, n, s));
+    // g_I = B^T g_c
+    SCINT_CUDA(cudaMemsetAsync(gmap, 0, (size_t)n * n * 4, s));
+    for (int t0 = 0; t0 < n_tracks && n_samples > 0; t0 += kTracksPerLaunch) {
+        CurveAdjArgs a{};
+        a.n = n;
+        a.n_tracks = std::min(kTracksPerLaunch, n_tracks - t0);
+        a.n_samples = n_samples;
+        a.grad_curves = grad_curves + (size_t)t0 * n_samples;
+        a.grad_map = gmap;
+        for (int i = 0; i < a.n_tracks; ++i) {
+            const double* tr = tracks + 4 * (t0 + i);
+            a.tr[i] = Track{tr[0], tr[1], std::cos(tr[2]), std::sin(tr[2]), tr[3]};
+        }
+        SCINT_LAUNCH(K_LC_ADJ, 20.0 * a.n_tracks * (double)n_samples, 0.0, s, launch_lightcurve_adjoint(a, s));
+    }
+    // the disk filter is real and even, hence self-adjoint
+    if (p->source_radius_km > 0.0) {
+        SmoothArgs sa{};
+        sa.n = n;
+        sa.radius_over_L = p->source_radius_km / screen_len(p);
+        sa.tw = tw;
+        sa.spec = spec;
+        sa.intensity = gmap;
+        const double half = (double)(n / 2 + 1) * n * 8.0;
+        SCINT_LAUNCH(K_SMOOTH_FWD, 4.0 * nn + half, (n / 2) * fft_flops(n), s, launch_smooth_pass(sa, 0, s));
+        SCINT_LAUNCH(K_SMOOTH_ROWS, 2.0 * half, 2.0 * (n / 2 + 1) * fft_flops(n), s, launch_smooth_pass(sa, 1, s));
+        SCINT_LAUNCH(K_SMOOTH_INV, half + 4.0 * nn, (n / 2) * fft_flops(n), s, launch_smooth_pass(sa, 2, s));
+    }
+    for (int l0 = 0; l0 < n_lambda; l0 += g) {
+        const int gg = std::min(g, n_lambda - l0);
+        TableArgs ta{};
+        ta.n = n;
+        ta.count = gg;
+        PropArgs pa{};
+        pa.n = n;
+        pa.phi = phi;
+        pa.tw = tw;
+        pa.lam.count = gg;
+        const double L = screen_len(p);
+        for (int i = 0; i < gg; ++i) {
+            const double l = lambdas_nm[l0 + i];
+            ta.lz_over_2L2[i] = lz_km2(l, p->z_pc) / (2.0 * L * L);
+            ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
+            pa.lam.scale_fx[i] = (uint64_t)std::llround(p->lambda_ref_nm / l * 4294967296.0);
+            pa.lam.weight[i] = (float)w[l0 + i];
+            pa.lam.scale[i] = (float)(p->lambda_ref_nm / l);
+        }
+        Carver cg = cp;
+        ta.h = cg.take<float2>((size_t)gg * n * 8);
+        ta.sf = cg.take<float>((size_t)gg * n * 4);
+        pa.h = ta.h;
+        pa.sf = ta.sf;
+        pa.work = cg.take<float2>((size_t)gg * n * n * 8);
+        AdjArgs aa{};
+        aa.n = n;
+        aa.phi = phi;
+        aa.tw = tw;
+        aa.h = ta.h;
+        aa.sf = ta.sf;
+        aa.work = pa.work;
+        aa.grad_map = gmap;
+        aa.grad_phi = grad_phi;
+        aa.accumulate = accumulate || l0 > 0;
+        aa.lam = pa.lam;
+        SCINT_LAUNCH(K_PROP_TABLES, 12.0 * gg * n, 0.0, s, launch_prop_tables(ta, s));
+        SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * gg * nn, 2.0 * gg * n * fft_flops(n), s, launch_prop_rows(pa, s));
+        SCINT_LAUNCH(K_ADJ_COLS, 16.0 * gg * nn + 4.0 * nn, 4.0 * gg * n * fft_flops(n), s, launch_adj_cols(aa, s));
+        SCINT_LAUNCH(K_ADJ_ROWS, 8.0 * gg * nn + 8.0 * nn + (aa.accumulate ? 16.0 : 8.0) * nn,
+                     2.0 * gg * n * fft_flops(n), s, launch_adj_rows(aa, s));
+    }
+    return ok();
+}
+
+int scint_rdiff_gradient(const scint_params* p, const double* phi, const double* grad_phi, double* out,
+                         void* workspace, size_t workspace_bytes, void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!phi || !grad_phi || !out) return fail(SCINT_EINVAL, "phi, grad_phi and out must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Carver c{};
+    rc = resolve_ws(workspace, workspace_bytes, ws_moments(), s, &c);
+    if (rc) return rc;
+    double* partial = c.take<double>((size_t)kMomentBlocks * 2 * sizeof(double));
+    const long long nn = (long long)p->n * p->n;
+    // phi ~ R_diff^((2 - beta)/2) at a fixed seed
+    const double scale = (2.0 - p->beta) / (2.0 * p->r_diff_km);
+    SCINT_LAUNCH(K_DOT, 16.0 * (double)nn, 0.0, s, launch_scaled_dot(phi, grad_phi, nn, scale, partial, out, s));
     return ok();
 }
 

@@ -53,6 +53,7 @@ struct LambdaSet {
     int count;                       // wavelengths in this group
     uint64_t scale_fx[kMaxLambda];   // round(lambda_ref/lambda * 2^32)
     float weight[kMaxLambda];        // passband weight w_l
+    float scale[kMaxLambda];         // s = lambda_ref/lambda (the adjoint's d(phase)/d(phi))
 };
 
 struct PropArgs {
@@ -99,6 +100,33 @@ struct CurveArgs {
     Track tr[kTracksPerLaunch];
 };
 cudaError_t launch_lightcurve(const CurveArgs& a, cudaStream_t s);
+
+// -------- adjoint -------------------------------------------------------------
+struct CurveAdjArgs {
+    int n, n_tracks, n_samples;
+    const float* grad_curves;  // this launch's slice, n_tracks * n_samples
+    float* grad_map;           // n*n, accumulated with atomics
+    Track tr[kTracksPerLaunch];
+};
+cudaError_t launch_lightcurve_adjoint(const CurveAdjArgs& a, cudaStream_t s);
+
+struct AdjArgs {
+    int n;
+    const double* phi;
+    const float2* tw;
+    const float2* h;           // per lambda: H / n
+    const float* sf;           // per lambda: taper
+    float2* work;              // per lambda: forward row-pass field, overwritten by P_y^H G_out
+    const float* grad_map;     // dL/dI after the disk filter
+    double* grad_phi;          // n*n, written or accumulated
+    int accumulate;
+    LambdaSet lam;
+};
+cudaError_t launch_adj_cols(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adj_rows(const AdjArgs& a, cudaStream_t s);
+// out[0] = scale * sum_i a_i b_i (FP64); partial: kMomentBlocks doubles
+cudaError_t launch_scaled_dot(const double* a, const double* b, long long n, double scale, double* partial,
+                              double* out, cudaStream_t s);
 
 // FP64 moments of a rectangular region [r0, r1) x [c0, c1) of an n x n map;
 // out = {m, mean, sigma, count}.  partial: workspace of >= kMomentBlocks*2 doubles.

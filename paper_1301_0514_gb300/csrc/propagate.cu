@@ -17,30 +17,9 @@
 // arithmetic (error |phi s| 2^-33 / 2 pi turns from rounding s) and only the
 // reduced angle goes to the FP32 sine/cosine.
 #include "dispatch.cuh"
-#include "fft.cuh"
-#include "kernels.cuh"
-
-// Twiddle source of the propagation FFTs (a build-time tuning choice):
-// 1 = per-block shared table, 2 = per-thread register bases + products.
-#ifndef SCINT_PROP_TWIDDLES
-#define SCINT_PROP_TWIDDLES 1
-#endif
+#include "propagate.cuh"
 
 namespace scint {
-
-constexpr int kPropTw = SCINT_PROP_TWIDDLES;
-
-template <int N> __host__ __device__ constexpr int prow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N ? kTileRow32 / N : N); }
-template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T; }
-template <int N> __host__ __device__ constexpr int pcol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N ? kTileCol32 / N : N); }
-// Strip width of the intermediate: at least 4 columns, so that every row of the
-// row pass writes whole 32-byte sectors; a column block then reads its
-// pcol_lines() columns out of one strip (sibling blocks share the sectors in L2).
-template <int N> __host__ __device__ constexpr int pstrip() { return pcol_lines<N>() >= 4 ? pcol_lines<N>() : (N >= 4 ? 4 : N); }
-constexpr int kColEPT = 16;   // values per thread in the column pass
-template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_lines<N>() * FftPlan<N, kColEPT>::T; }
-
-SCINT_DEV int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
 
 // ---- tables -----------------------------------------------------------------
 __global__ void prop_tables_kernel(TableArgs a) {
@@ -91,9 +70,8 @@ prop_rows_kernel(PropArgs a) {
     TwiddleRegs<float2, N, 16> tr;
     if constexpr (kPropTw == 2) tr.load(a.tw, t);
     else fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
-    const double to_fixed = 4294967296.0 / (2.0 * kPi);
 #pragma unroll
-    for (int m = 0; m < E; ++m) P[m * T] = __double2ll_rn(a.phi[(size_t)y * N + t + m * T] * to_fixed);
+    for (int m = 0; m < E; ++m) P[m * T] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
     __syncthreads();
 
 #pragma unroll 1
@@ -104,15 +82,7 @@ prop_rows_kernel(PropArgs a) {
         const float sfy = sf[y];
         float2 v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const unsigned long long prod = (unsigned long long)P[m * T] * S;   // frac(phi s) * 2^64
-            // angle in [-pi, pi): the hardware sine/cosine (abs. error ~4e-7 there) suffices
-            const float ang = (float)(int)(prod >> 32) * (float)(2.0 * kPi * 0x1.0p-32);
-            float sn, cs;
-            __sincosf(ang, &sn, &cs);
-            const float amp = sfy * __ldg(sf + t + m * T);
-            v[m] = make_float2(amp * cs, amp * sn);
-        }
+        for (int m = 0; m < E; ++m) v[m] = unit_phasor(P[m * T], S) * (sfy * __ldg(sf + t + m * T));
         if constexpr (kPropTw == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
         else fft_line<float2, N, -1, 16, 1, 1>(v, buf, t, tws);
 #pragma unroll
@@ -121,10 +91,7 @@ prop_rows_kernel(PropArgs a) {
         else fft_line<float2, N, +1, 16, 1, 1>(v, buf, t, tws);
         float2* dst = a.work + (size_t)l * N * N;
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int x = t + m * T;
-            dst[(size_t)(x / W) * N * W + (size_t)y * W + (x % W)] = v[m];
-        }
+        for (int m = 0; m < E; ++m) dst[strip_index<W>(y, t + m * T, N)] = v[m];
     }
 }
 
@@ -171,17 +138,6 @@ prop_cols_kernel(PropArgs a) {
         *o = a.accumulate ? *o + acc[m * T] : acc[m * T];
     }
 }
-
-template <int N> constexpr size_t prow_smem() {
-    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) +
-           (kPropTw == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0);
-}
-template <int N> constexpr size_t pcol_smem() {
-    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float)) +
-           (kPropTw == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0);
-}
-
-constexpr size_t kMaxSmem = 227 * 1024;
 
 cudaError_t launch_prop_rows(const PropArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {

@@ -1,0 +1,61 @@
+// Block shapes and layouts shared by the propagation passes and their adjoints.
+#pragma once
+
+#include "fft.cuh"
+#include "kernels.cuh"
+
+// Twiddle source of the propagation FFTs (a build-time tuning choice):
+// 1 = per-block shared table, 2 = per-thread register bases + products.
+#ifndef SCINT_PROP_TWIDDLES
+#define SCINT_PROP_TWIDDLES 1
+#endif
+
+namespace scint {
+
+constexpr int kPropTw = SCINT_PROP_TWIDDLES;
+constexpr int kColEPT = 16;   // values per thread in the column passes
+constexpr size_t kMaxSmem = 227 * 1024;
+
+// rows per row-pass block, columns per column-pass block (all lines of a block
+// are transformed together)
+template <int N> __host__ __device__ constexpr int prow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N ? kTileRow32 / N : N); }
+template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T; }
+template <int N> __host__ __device__ constexpr int pcol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N ? kTileCol32 / N : N); }
+template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_lines<N>() * FftPlan<N, kColEPT>::T; }
+// Strip width of the intermediate: at least 4 columns, so that every row of the
+// row pass writes whole 32-byte sectors; a column block then reads its
+// pcol_lines() columns out of one strip (sibling blocks share the sectors in L2).
+template <int N> __host__ __device__ constexpr int pstrip() { return pcol_lines<N>() >= 4 ? pcol_lines<N>() : (N >= 4 ? 4 : N); }
+
+template <int N> constexpr size_t prow_smem() {
+    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) +
+           (kPropTw == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0);
+}
+template <int N> constexpr size_t pcol_smem() {
+    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float)) +
+           (kPropTw == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0);
+}
+
+// signed FFT frequency index of bin i
+SCINT_DEV int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// element (y, x) of a strip-layout field
+template <int WL> SCINT_DEV size_t strip_index(int y, int x, int n) {
+    return (size_t)(x / WL) * n * WL + (size_t)y * WL + (x % WL);
+}
+
+// phi (radians) -> 64-bit fixed-point turns, P = round(phi 2^32 / 2 pi)
+SCINT_DEV long long phase_fixed(double phi) { return __double2ll_rn(phi * (4294967296.0 / (2.0 * kPi))); }
+
+// exp(i phi s) from P and S = round(s 2^32): the low 64 bits of P S are the
+// fractional turns of phi s times 2^64 (exact reduction mod 2 pi); the angle
+// in [-pi, pi) goes to the hardware sine/cosine (abs. error ~4e-7 there).
+SCINT_DEV float2 unit_phasor(long long P, unsigned long long S) {
+    const unsigned long long prod = (unsigned long long)P * S;
+    const float ang = (float)(int)(prod >> 32) * (float)(2.0 * kPi * 0x1.0p-32);
+    float sn, cs;
+    __sincosf(ang, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+}  // namespace scint

@@ -1,0 +1,96 @@
+"""GPU gradient of a light-curve misfit vs the FP64 oracle's gradient (itself pinned by
+central finite differences in test_oracle_observables.py).
+
+Tolerance: 1e-4 of max |dL/dphi| elementwise (the FP32 forward fields enter the
+adjoint; their ~1e-6 relative error propagates linearly), and 1e-4 relative for
+dL/dR_diff.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1301_0514_gb300 as S
+from paper_1301_0514_gb300 import workloads as W
+from conftest import gpu_params, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+G_TOL = 1e-4
+
+
+def _case(n=128, rs=60.0, lams=(520.0, 580.0), beta=11.0 / 3.0):
+    it = W._item(n, 10.0, 25.0, beta=beta, lambda_nm=550.0, lambda_ref_nm=550.0, source_radius_km=rs,
+                 seed=W.SEED_BASE + 55, screen_id=2,
+                 tracks=[(1.5, 3.25, 0.4, 0.7), (20.0, 2.0, 2.2, 1.1), (-5.0, 77.0, 3.0, 0.37)], n_samples=300,
+                 lambdas_nm=np.array(lams))
+    return it
+
+
+def _oracle_gc(it, p_o, phi):
+    """dL/dc for L = mean (c - target)^2 with the oracle's forward curves."""
+    _, _, target = O.forward(p_o.with_(seed=p_o.seed + 500), it["lambdas_nm"], it["tracks"], it["n_samples"])
+    _, _, c = O.forward(p_o, it["lambdas_nm"], it["tracks"], it["n_samples"], phi=phi)
+    return 2.0 * (c - target) / c.size, target
+
+
+@pytest.mark.parametrize("n,rs,lams", [(128, 60.0, (520.0, 580.0)), (64, 0.0, (550.0,)),
+                                       (256, 300.0, (480.0, 530.0, 610.0, 690.0, 700.0))])
+def test_adjoint_matches_oracle(n, rs, lams):
+    it = _case(n, rs, lams)
+    p_g, p_o = gpu_params(it), oracle_params(it)
+    phi = O.make_screen(p_o)
+    gc, target = _oracle_gc(it, p_o, phi)
+    _, g_o, gr_o = O.misfit_gradient(p_o, phi, it["lambdas_nm"], it["tracks"], it["n_samples"], target)
+    phi_t = torch.from_numpy(phi).cuda()
+    g_g = S.lightcurve_adjoint(p_g, phi_t, it["lambdas_nm"], it["tracks"], it["n_samples"],
+                               torch.from_numpy(gc.astype(np.float32)).cuda())
+    scale = np.abs(g_o).max()
+    assert np.abs(g_g.cpu().numpy() - g_o).max() <= G_TOL * scale
+    gr = S.rdiff_gradient(p_g, phi_t, g_g).item()
+    assert gr == pytest.approx(gr_o, rel=1e-3, abs=1e-4 * abs(gr_o))
+
+
+def test_adjoint_with_small_workspace_groups_and_accumulate():
+    it = _case(128, 40.0, (500.0, 540.0, 580.0))
+    p_g, p_o = gpu_params(it), oracle_params(it)
+    phi = O.make_screen(p_o)
+    gc, target = _oracle_gc(it, p_o, phi)
+    _, g_o, _ = O.misfit_gradient(p_o, phi, it["lambdas_nm"], it["tracks"], it["n_samples"], target)
+    ws = torch.empty(S.workspace_bytes(p_g, 1), dtype=torch.uint8, device="cuda")   # one wavelength per group
+    out = torch.full((128, 128), 1.5, dtype=torch.float64, device="cuda")
+    S.lightcurve_adjoint(p_g, torch.from_numpy(phi).cuda(), it["lambdas_nm"], it["tracks"], it["n_samples"],
+                         torch.from_numpy(gc.astype(np.float32)).cuda(), out=out, accumulate=True, workspace=ws)
+    assert np.abs(out.cpu().numpy() - 1.5 - g_o).max() <= G_TOL * np.abs(g_o).max()
+
+
+def test_autograd_phi_and_rdiff():
+    """loss.backward() through screen(r_diff) -> light_curves -> misfit vs the oracle's gradient."""
+    it = _case(128, 60.0, (520.0, 580.0))
+    p_g, p_o = gpu_params(it), oracle_params(it)
+    _, _, target = O.forward(p_o.with_(seed=p_o.seed + 500), it["lambdas_nm"], it["tracks"], it["n_samples"])
+    r = torch.tensor(p_g.r_diff_km, dtype=torch.float64, requires_grad=True)
+    phi = S.screen(p_g, r)
+    phi.retain_grad()
+    curves = S.light_curves(phi, p_g, it["lambdas_nm"], it["tracks"], it["n_samples"])
+    loss = ((curves.double() - torch.from_numpy(target).cuda()) ** 2).mean()
+    loss.backward()
+    phi_o = O.make_screen(p_o)
+    l_o, g_o, gr_o = O.misfit_gradient(p_o, phi_o, it["lambdas_nm"], it["tracks"], it["n_samples"], target)
+    assert loss.item() == pytest.approx(l_o, rel=1e-4)
+    assert np.abs(phi.grad.cpu().numpy() - g_o).max() <= 1e-3 * np.abs(g_o).max()
+    assert r.grad.item() == pytest.approx(gr_o, rel=1e-3)
+
+
+def test_config5_gradient_full_size():
+    """2048^2, R_diff = 100 km, 500 nm, one track of 10^4 samples at 0.2 px: GPU vs oracle gradient."""
+    it = W.config5(batch=1)[0]
+    p_g, p_o = gpu_params(it), oracle_params(it)
+    phi = O.make_screen(p_o)
+    gc, target = _oracle_gc(it, p_o, phi)
+    _, g_o, gr_o = O.misfit_gradient(p_o, phi, it["lambdas_nm"], it["tracks"], it["n_samples"], target)
+    phi_t = torch.from_numpy(phi).cuda()
+    g_g = S.lightcurve_adjoint(p_g, phi_t, it["lambdas_nm"], it["tracks"], it["n_samples"],
+                               torch.from_numpy(gc.astype(np.float32)).cuda())
+    assert np.abs(g_g.cpu().numpy() - g_o).max() <= G_TOL * np.abs(g_o).max()
+    assert S.rdiff_gradient(p_g, phi_t, g_g).item() == pytest.approx(gr_o, rel=1e-3)
