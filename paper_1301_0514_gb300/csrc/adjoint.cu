@@ -53,26 +53,30 @@ cudaError_t launch_lightcurve_adjoint(const CurveAdjArgs& a, cudaStream_t s) {
 // ---- adjoint column pass ----------------------------------------------------------
 // buffers, the g_I columns (in place of the accumulator) and the twiddle table
 template <int N> constexpr size_t acol_smem() {
-    return (size_t)pcol_lines<N>() * (FftPlan<N, kColEPT>::BUF * sizeof(float2) + N * sizeof(float)) +
-           (size_t)FftPlan<N>::TWS * sizeof(float2);
+    return (size_t)pcol_lines<N>() * (FftPlan<N, kColEPT>::BUF * sizeof(float2) + N * sizeof(float)) / pcs<N>() +
+           (ptwm<N>() == 0 ? 0 : (size_t)FftPlan<N>::TWS * sizeof(float2));
 }
 
 template <int N>
 __global__ void __launch_bounds__(pcol_threads<N>(), 1)
 adj_cols_kernel(AdjArgs a) {
     using Pl = FftPlan<N, kColEPT>;
+    constexpr int CS = pcs<N>(), TWM = ptwm<N>() == 0 ? 0 : 1;
     constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
+    constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
     extern __shared__ float2 smem32[];
-    const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int x = blockIdx.x * W + w;
-    const int x0 = blockIdx.x * W;
+    const int w = threadIdx.x % W, tl = threadIdx.x / W;
+    const int t = line_rank<CS>() * TL + tl;
+    const int x0 = (blockIdx.x / CS) * W;
+    const int x = x0 + w;
     float2* buf = smem32 + w;
-    float* gi = reinterpret_cast<float*>(smem32 + W * Pl::BUF) + w * N + t;   // g_I of this column (own entries)
-    float2* tws = smem32 + W * Pl::BUF + (W * N) / 2;
-    fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+    float* gi = reinterpret_cast<float*>(smem32 + W * BUFL) + w * NL + tl;   // g_I of this column (own entries)
+    float2* tws = smem32 + W * BUFL + (W * NL) / 2;
+    const float2* twp = TWM == 1 ? tws : a.tw;
+    if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
-    for (int m = 0; m < E; ++m) gi[m * T] = a.grad_map[(size_t)(t + m * T) * N + x];
-    __syncthreads();
+    for (int m = 0; m < E; ++m) gi[m * TL] = a.grad_map[(size_t)(t + m * T) * N + x];
+    line_sync<CS>();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         float2* f = a.work + (size_t)l * N * N + (size_t)(x0 / WL) * N * WL + (x0 % WL);
@@ -80,48 +84,54 @@ adj_cols_kernel(AdjArgs a) {
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = f[(size_t)(t + m * T) * WL + w];
-        fft_line<float2, N, -1, kColEPT, W, 1>(v, buf, t, tws);
+        fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
-        fft_line<float2, N, +1, kColEPT, W, 1>(v, buf, t, tws);          // A_out of this column
+        fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);          // A_out of this column
         const float c2w = 2.0f * a.lam.weight[l];
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = v[m] * (c2w * gi[m * T]);     // G_out
-        fft_line<float2, N, -1, kColEPT, W, 1>(v, buf, t, tws);
+        for (int m = 0; m < E; ++m) v[m] = v[m] * (c2w * gi[m * TL]);     // G_out
+        fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], __ldg(h + t + m * T));
-        fft_line<float2, N, +1, kColEPT, W, 1>(v, buf, t, tws);          // P_y^H G_out
+        fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);          // P_y^H G_out
 #pragma unroll
         for (int m = 0; m < E; ++m) f[(size_t)(t + m * T) * WL + w] = v[m];
     }
+    if constexpr (CS == 2) line_sync<CS>();
 }
 
 // ---- adjoint row pass --------------------------------------------------------------
 // buffers, fixed-point phases, twiddle table, g_phi accumulators
 template <int N> constexpr size_t arow_smem() {
-    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long) + N * sizeof(float)) +
-           (size_t)FftPlan<N>::TWS * sizeof(float2);
+    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long) + N * sizeof(float)) / pcs<N>() +
+           (ptwm<N>() == 0 ? 0 : (size_t)FftPlan<N>::TWS * sizeof(float2));
 }
 
 template <int N>
 __global__ void __launch_bounds__(prow_threads<N>(), 1)
 adj_rows_kernel(AdjArgs a) {
     using Pl = FftPlan<N>;
+    constexpr int CS = pcs<N>(), TWM = ptwm<N>() == 0 ? 0 : 1;
     constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), WL = pstrip<N>();
+    constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
+    constexpr int TWSL = TWM == 1 ? Pl::TWS : 0;
     extern __shared__ float2 smem32[];
-    const int team = threadIdx.x / T, t = threadIdx.x % T;
-    const int y = blockIdx.x * B + team;
-    float2* buf = smem32 + team * Pl::BUF;
-    long long* P = reinterpret_cast<long long*>(smem32 + B * Pl::BUF) + team * N + t;
-    float2* tws = smem32 + B * Pl::BUF + B * N;
-    float* acc = reinterpret_cast<float*>(tws + Pl::TWS) + team * N + t;   // g_phi of this row (own entries)
-    fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+    const int team = threadIdx.x / TL, tl = threadIdx.x % TL;
+    const int t = line_rank<CS>() * TL + tl;
+    const int y = (blockIdx.x / CS) * B + team;
+    float2* buf = smem32 + team * BUFL;
+    long long* P = reinterpret_cast<long long*>(smem32 + B * BUFL) + team * NL + tl;
+    float2* tws = smem32 + B * BUFL + B * NL;
+    float* acc = reinterpret_cast<float*>(tws + TWSL) + team * NL + tl;   // g_phi of this row (own entries)
+    const float2* twp = TWM == 1 ? tws : a.tw;
+    if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-        P[m * T] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
-        acc[m * T] = 0.0f;
+        P[m * TL] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
+        acc[m * TL] = 0.0f;
     }
-    __syncthreads();
+    line_sync<CS>();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         const float2* f = a.work + (size_t)l * N * N;
@@ -130,24 +140,25 @@ adj_rows_kernel(AdjArgs a) {
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = f[strip_index<WL>(y, t + m * T, N)];
-        fft_line<float2, N, -1, 16, 1, 1>(v, buf, t, tws);
+        fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, twp);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], __ldg(h + t + m * T));
-        fft_line<float2, N, +1, 16, 1, 1>(v, buf, t, tws);              // G_in of this row
+        fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, twp);              // G_in of this row
         const unsigned long long S = a.lam.scale_fx[l];
         const float s_l = a.lam.scale[l], sfy = sf[y];
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            const float2 A = unit_phasor(P[m * T], S) * (sfy * __ldg(sf + t + m * T));
+            const float2 A = unit_phasor(P[m * TL], S) * (sfy * __ldg(sf + t + m * T));
             // s Im(conj(A_in) G_in)
-            acc[m * T] = fmaf(s_l, A.x * v[m].y - A.y * v[m].x, acc[m * T]);
+            acc[m * TL] = fmaf(s_l, A.x * v[m].y - A.y * v[m].x, acc[m * TL]);
         }
     }
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         double* o = a.grad_phi + (size_t)y * N + t + m * T;
-        *o = a.accumulate ? *o + (double)acc[m * T] : (double)acc[m * T];
+        *o = a.accumulate ? *o + (double)acc[m * TL] : (double)acc[m * TL];
     }
+    if constexpr (CS == 2) line_sync<CS>();
 }
 
 cudaError_t launch_adj_cols(const AdjArgs& a, cudaStream_t s) {
@@ -158,8 +169,8 @@ cudaError_t launch_adj_cols(const AdjArgs& a, cudaStream_t s) {
         } else {
             cudaError_t e = set_smem(adj_cols_kernel<N>, acol_smem<N>());
             if (e != cudaSuccess) return e;
-            adj_cols_kernel<N><<<N / pcol_lines<N>(), pcol_threads<N>(), acol_smem<N>(), s>>>(a);
-            return cudaGetLastError();
+            return launch_k(adj_cols_kernel<N>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
+                            dim3(pcol_threads<N>()), acol_smem<N>(), s, a);
         }
     });
 }
@@ -172,8 +183,8 @@ cudaError_t launch_adj_rows(const AdjArgs& a, cudaStream_t s) {
         } else {
             cudaError_t e = set_smem(adj_rows_kernel<N>, arow_smem<N>());
             if (e != cudaSuccess) return e;
-            adj_rows_kernel<N><<<N / prow_lines<N>(), prow_threads<N>(), arow_smem<N>(), s>>>(a);
-            return cudaGetLastError();
+            return launch_k(adj_rows_kernel<N>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
+                            dim3(prow_threads<N>()), arow_smem<N>(), s, a);
         }
     });
 }

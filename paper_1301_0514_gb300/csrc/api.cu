@@ -391,7 +391,6 @@ int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_
     int rc = check_params(p);
     if (rc) return rc;
     if (!phi) return fail(SCINT_EINVAL, "phi must be a device pointer");
-    if (p->n > 8192) return fail(SCINT_EUNSUPPORTED, "screen synthesis supports n <= 8192 in this build");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Carver c{};
     rc = resolve_ws(workspace, workspace_bytes, ws_synth(p->n), s, &c);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <type_traits>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -30,6 +31,29 @@ template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Launch k with clusters of cs blocks along x (cs == 1: ordinary launch).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*k)(KArgs...), int cs, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args&&... args) {
+    if (cs == 1) {
+        k<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
 }  // namespace scint

@@ -20,6 +20,8 @@
 // per stage (conflict-free for consecutive k).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace scint {
@@ -234,13 +236,32 @@ SCINT_DEV void twiddle_powers(C w1, C w4, C (&w)[R]) {
 // Twiddle source TWM: 0 = global table tw[j] = exp(-2 pi i j / N); 1 = the
 // block's shared table (fill_twiddle_table; tw points to it); 2 = register
 // bases (tr).
-template <typename C, int N, int DIR, int EPT, int LW, int TWM, int S>
+// CS = 1: the whole line sits in this block's shared buffer.  CS = 2: the line
+// is split over a cluster of two blocks; elements [0, N/2) live in rank 0's
+// buffer and [N/2, N) in rank 1's, each padded by pad16 of the local index, at
+// the same offset in both blocks; t is the thread's index in the line's team
+// across the cluster, and the stage barriers are cluster barriers.
+template <int CS> SCINT_DEV void line_sync() {
+    if constexpr (CS == 1) __syncthreads();
+    else cooperative_groups::this_cluster().sync();
+}
+
+template <typename C, int N, int DIR, int EPT, int LW, int TWM, int CS, int S>
 SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw,
                          const TwiddleRegs<C, N, EPT>* tr) {
     using Pl = FftPlan<N, EPT>;
     constexpr int E = Pl::E, T = Pl::T;
     constexpr int R = Pl::radix(S), P = Pl::span(S), NB = E / R;
     constexpr bool FIRST = (S == 0), LAST = (S == Pl::NSTAGE - 1);
+    constexpr int HALF = N / 2;
+    C* bufs[CS];
+    if constexpr (CS == 1) {
+        bufs[0] = buf;
+    } else {
+        auto cl = cooperative_groups::this_cluster();
+        bufs[0] = cl.map_shared_rank(buf, 0);
+        bufs[1] = cl.map_shared_rank(buf, 1);
+    }
     C u[E];
     if constexpr (FIRST) {
         // butterfly b takes positions t + b T + r N/R = t + (b + r NB) T
@@ -251,12 +272,16 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
     } else {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            // N/R is a multiple of 16 here, so pad16(i + r N/R) = pad16(i) + r (N/R)(17/16)
-            const C* src = buf + pad16(t + b * T) * LW;
+            // N/R is a multiple of 16 here, so pad16(i + r N/R) = pad16(i) + r (N/R)(17/16).
+            // Split line: i < N/R <= N/2, so element i + r N/R is in the upper half iff r >= R/2.
 #pragma unroll
-            for (int r = 0; r < R; ++r) u[b * R + r] = src[r * ((N / R) + (N / R) / 16) * LW];
+            for (int r = 0; r < R; ++r) {
+                const int o = (CS == 2 && r >= R / 2) ? 1 : 0;
+                const int rr = r - o * (R / 2);
+                u[b * R + r] = bufs[o][pad16(t + b * T) * LW + rr * ((N / R) + (N / R) / 16) * LW];
+            }
         }
-        __syncthreads();
+        line_sync<CS>();
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -291,27 +316,38 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
             const int i = t + b * T;
             const int k = i & (P - 1);
             const int j = (i - k) * R + k;
-            // P >= 16: pad16(j + r P) = pad16(j) + r P (17/16); P == 1: j = i R and r < R <= 16
-            C* dst = buf + pad16(j) * LW;
+            if constexpr (CS == 1) {
+                // P >= 16: pad16(j + r P) = pad16(j) + r P (17/16); P == 1: j = i R and r < R <= 16
+                C* dst = buf + pad16(j) * LW;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[(P >= 16 ? r * (P + P / 16) : r) * LW] = u[b * R + r];
+                for (int r = 0; r < R; ++r) dst[(P >= 16 ? r * (P + P / 16) : r) * LW] = u[b * R + r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int e = j + r * P;
+                    const int o = e >= HALF ? 1 : 0;
+                    bufs[o][pad16(e - o * HALF) * LW] = u[b * R + r];
+                }
+            }
         }
-        __syncthreads();
-        fft_stage<C, N, DIR, EPT, LW, TWM, S + 1>(v, buf, t, tw, tr);
+        line_sync<CS>();
+        fft_stage<C, N, DIR, EPT, LW, TWM, CS, S + 1>(v, buf, t, tw, tr);
     }
 }
 
 // Transform the team's line in place (registers v, distribution t + m*T).
-// Every thread of the block must call this the same number of times.
-template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0>
+// Every thread of the block (of the cluster, for CS = 2) must call this the
+// same number of times.
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0, int CS = 1>
 SCINT_DEV void fft_line(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw) {
     static_assert(TWM != 2, "register twiddles: use fft_line_tr");
-    fft_stage<C, N, DIR, EPT, LW, TWM, 0>(v, buf, t, tw, nullptr);
+    static_assert(CS == 1 || (CS == 2 && FftPlan<N, EPT>::NSTAGE > 1 && N >= 512), "split lines need N >= 512");
+    fft_stage<C, N, DIR, EPT, LW, TWM, CS, 0>(v, buf, t, tw, nullptr);
 }
 
 template <typename C, int N, int DIR, int EPT = 16, int LW = 1>
 SCINT_DEV void fft_line_tr(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const TwiddleRegs<C, N, EPT>& tr) {
-    fft_stage<C, N, DIR, EPT, LW, 2, 0>(v, buf, t, nullptr, &tr);
+    fft_stage<C, N, DIR, EPT, LW, 2, 1, 0>(v, buf, t, nullptr, &tr);
 }
 
 }  // namespace scint

@@ -58,21 +58,25 @@ template <int N>
 __global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
 prop_rows_kernel(PropArgs a) {
     using Pl = FftPlan<N>;
+    constexpr int CS = pcs<N>(), TWM = ptwm<N>();
     constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), W = pstrip<N>();
+    constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
     extern __shared__ float2 smem32[];
-    const int team = threadIdx.x / T, t = threadIdx.x % T;
-    const int y = blockIdx.x * B + team;
-    float2* buf = smem32 + team * Pl::BUF;
+    const int team = threadIdx.x / TL, tl = threadIdx.x % TL;
+    const int t = line_rank<CS>() * TL + tl;     // index in the line's team
+    const int y = (blockIdx.x / CS) * B + team;
+    float2* buf = smem32 + team * BUFL;
     // fixed-point phase of this thread's pixels, kept in shared memory across the
     // wavelength loop (each thread reads back only the entries it wrote)
-    long long* P = reinterpret_cast<long long*>(smem32 + B * Pl::BUF) + team * N + t;
-    float2* tws = smem32 + B * Pl::BUF + B * N;   // shared twiddle table (after P, 8 B per entry)
+    long long* P = reinterpret_cast<long long*>(smem32 + B * BUFL) + team * NL + tl;
+    float2* tws = smem32 + B * BUFL + B * NL;   // shared twiddle table (after P, 8 B per entry)
+    const float2* twp = TWM == 1 ? tws : a.tw;
     TwiddleRegs<float2, N, 16> tr;
-    if constexpr (kPropTw == 2) tr.load(a.tw, t);
-    else fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+    if constexpr (TWM == 2) tr.load(a.tw, t);
+    else if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
-    for (int m = 0; m < E; ++m) P[m * T] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
-    __syncthreads();
+    for (int m = 0; m < E; ++m) P[m * TL] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
+    line_sync<CS>();
 
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
@@ -82,17 +86,18 @@ prop_rows_kernel(PropArgs a) {
         const float sfy = sf[y];
         float2 v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = unit_phasor(P[m * T], S) * (sfy * __ldg(sf + t + m * T));
-        if constexpr (kPropTw == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
-        else fft_line<float2, N, -1, 16, 1, 1>(v, buf, t, tws);
+        for (int m = 0; m < E; ++m) v[m] = unit_phasor(P[m * TL], S) * (sfy * __ldg(sf + t + m * T));
+        if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
+        else fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, twp);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
-        if constexpr (kPropTw == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
-        else fft_line<float2, N, +1, 16, 1, 1>(v, buf, t, tws);
+        if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
+        else fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, twp);
         float2* dst = a.work + (size_t)l * N * N;
 #pragma unroll
         for (int m = 0; m < E; ++m) dst[strip_index<W>(y, t + m * T, N)] = v[m];
     }
+    if constexpr (CS == 2) line_sync<CS>();   // no block leaves while its partner may still read its buffer
 }
 
 // ---- column pass ---------------------------------------------------------------
@@ -100,21 +105,25 @@ template <int N>
 __global__ void __launch_bounds__(pcol_threads<N>(), 1)
 prop_cols_kernel(PropArgs a) {
     using Pl = FftPlan<N, kColEPT>;
+    constexpr int CS = pcs<N>(), TWM = ptwm<N>();
     constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
+    constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
     extern __shared__ float2 smem32[];
-    const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int x = blockIdx.x * W + w;
-    const int x0 = blockIdx.x * W;    // first column of the block: strip x0 / WL, offset x0 % WL
+    const int w = threadIdx.x % W, tl = threadIdx.x / W;
+    const int t = line_rank<CS>() * TL + tl;
+    const int x0 = (blockIdx.x / CS) * W;    // first column of the block: strip x0 / WL, offset x0 % WL
+    const int x = x0 + w;
     float2* buf = smem32 + w;     // W lines interleaved: element e of line w at pad16(e) * W + w
     // passband accumulator of this thread's pixels (own entries only)
-    float* acc = reinterpret_cast<float*>(smem32 + W * Pl::BUF) + w * N + t;
-    float2* tws = smem32 + W * Pl::BUF + (W * N) / 2;   // shared twiddle table (after acc)
+    float* acc = reinterpret_cast<float*>(smem32 + W * BUFL) + w * NL + tl;
+    float2* tws = smem32 + W * BUFL + (W * NL) / 2;   // shared twiddle table (after acc)
+    const float2* twp = TWM == 1 ? tws : a.tw;
     TwiddleRegs<float2, N, kColEPT> tr;
-    if constexpr (kPropTw == 2) tr.load(a.tw, t);
-    else fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+    if constexpr (TWM == 2) tr.load(a.tw, t);
+    else if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
-    for (int m = 0; m < E; ++m) acc[m * T] = 0.0f;
-    __syncthreads();
+    for (int m = 0; m < E; ++m) acc[m * TL] = 0.0f;
+    line_sync<CS>();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         const float2* src = a.work + (size_t)l * N * N + (size_t)(x0 / WL) * N * WL + (x0 % WL);
@@ -122,42 +131,49 @@ prop_cols_kernel(PropArgs a) {
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * WL + w];
-        if constexpr (kPropTw == 2) fft_line_tr<float2, N, -1, kColEPT, W>(v, buf, t, tr);
-        else fft_line<float2, N, -1, kColEPT, W, 1>(v, buf, t, tws);
+        if constexpr (TWM == 2) fft_line_tr<float2, N, -1, kColEPT, W>(v, buf, t, tr);
+        else fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
-        if constexpr (kPropTw == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
-        else fft_line<float2, N, +1, kColEPT, W, 1>(v, buf, t, tws);
+        if constexpr (TWM == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
+        else fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);
         const float wl = a.lam.weight[l];
 #pragma unroll
-        for (int m = 0; m < E; ++m) acc[m * T] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m * T]);
+        for (int m = 0; m < E; ++m) acc[m * TL] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m * TL]);
     }
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float* o = a.intensity + (size_t)(t + m * T) * N + x;
-        *o = a.accumulate ? *o + acc[m * T] : acc[m * T];
+        *o = a.accumulate ? *o + acc[m * TL] : acc[m * TL];
     }
+    if constexpr (CS == 2) line_sync<CS>();
 }
 
 cudaError_t launch_prop_rows(const PropArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
-        if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) return cudaErrorNotSupported;
-        cudaError_t e = set_smem(prop_rows_kernel<N>, prow_smem<N>());
-        if (e != cudaSuccess) return e;
-        prop_rows_kernel<N><<<N / prow_lines<N>(), prow_threads<N>(), prow_smem<N>(), s>>>(a);
-        return cudaGetLastError();
+        if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
+            return cudaErrorNotSupported;
+        } else {
+            cudaError_t e = set_smem(prop_rows_kernel<N>, prow_smem<N>());
+            if (e != cudaSuccess) return e;
+            return launch_k(prop_rows_kernel<N>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
+                            dim3(prow_threads<N>()), prow_smem<N>(), s, a);
+        }
     });
 }
 
 cudaError_t launch_prop_cols(const PropArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
-        if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) return cudaErrorNotSupported;
-        cudaError_t e = set_smem(prop_cols_kernel<N>, pcol_smem<N>());
-        if (e != cudaSuccess) return e;
-        prop_cols_kernel<N><<<N / pcol_lines<N>(), pcol_threads<N>(), pcol_smem<N>(), s>>>(a);
-        return cudaGetLastError();
+        if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
+            return cudaErrorNotSupported;
+        } else {
+            cudaError_t e = set_smem(prop_cols_kernel<N>, pcol_smem<N>());
+            if (e != cudaSuccess) return e;
+            return launch_k(prop_cols_kernel<N>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
+                            dim3(pcol_threads<N>()), pcol_smem<N>(), s, a);
+        }
     });
 }
 

@@ -16,24 +16,36 @@ constexpr int kPropTw = SCINT_PROP_TWIDDLES;
 constexpr int kColEPT = 16;   // values per thread in the column passes
 constexpr size_t kMaxSmem = 227 * 1024;
 
+// Lines longer than one block's shared memory (N = 16384) are split over a
+// cluster of two blocks (fft.cuh, CS = 2); they read twiddles from the global
+// table.  Own-entry arrays (fixed-point phases, accumulators) hold the N/CS
+// entries of the line that the block's threads own.
+template <int N> __host__ __device__ constexpr int pcs() { return N >= 16384 ? 2 : 1; }
+template <int N> __host__ __device__ constexpr int ptwm() { return pcs<N>() == 2 ? 0 : kPropTw; }
+
 // rows per row-pass block, columns per column-pass block (all lines of a block
-// are transformed together)
+// are transformed together); threads are per block
 template <int N> __host__ __device__ constexpr int prow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N ? kTileRow32 / N : N); }
-template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T; }
+template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T / pcs<N>(); }
 template <int N> __host__ __device__ constexpr int pcol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N ? kTileCol32 / N : N); }
-template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_lines<N>() * FftPlan<N, kColEPT>::T; }
+template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_lines<N>() * FftPlan<N, kColEPT>::T / pcs<N>(); }
 // Strip width of the intermediate: at least 4 columns, so that every row of the
 // row pass writes whole 32-byte sectors; a column block then reads its
 // pcol_lines() columns out of one strip (sibling blocks share the sectors in L2).
 template <int N> __host__ __device__ constexpr int pstrip() { return pcol_lines<N>() >= 4 ? pcol_lines<N>() : (N >= 4 ? 4 : N); }
 
+template <int N> constexpr size_t ptws_bytes() { return ptwm<N>() == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0; }
 template <int N> constexpr size_t prow_smem() {
-    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) +
-           (kPropTw == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0);
+    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) / pcs<N>() + ptws_bytes<N>();
 }
 template <int N> constexpr size_t pcol_smem() {
-    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float)) +
-           (kPropTw == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0);
+    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float)) / pcs<N>() + ptws_bytes<N>();
+}
+
+// rank of this block in its line's cluster (0 when lines are not split)
+template <int CS> SCINT_DEV int line_rank() {
+    if constexpr (CS == 1) return 0;
+    else return (int)cooperative_groups::this_cluster().block_rank();
 }
 
 // signed FFT frequency index of bin i

@@ -12,43 +12,64 @@
 
 namespace scint {
 
+// N = 16384 lines are split over a cluster of two blocks (fft.cuh, CS = 2)
+template <int N> __host__ __device__ constexpr int scs() { return N >= 16384 ? 2 : 1; }
 template <int N> __host__ __device__ constexpr int scol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N / 2 ? kTileCol32 / N : N / 2); }
-template <int N> __host__ __device__ constexpr int scol_threads() { return scol_lines<N>() * FftPlan<N>::T; }
+template <int N> __host__ __device__ constexpr int scol_threads() { return scol_lines<N>() * FftPlan<N>::T / scs<N>(); }
 template <int N> __host__ __device__ constexpr int srow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N / 2 ? kTileRow32 / N : N / 2); }
-template <int N> __host__ __device__ constexpr int srow_threads() { return srow_lines<N>() * FftPlan<N>::T; }
+template <int N> __host__ __device__ constexpr int srow_threads() { return srow_lines<N>() * FftPlan<N>::T / scs<N>(); }
+
+template <int CS> SCINT_DEV int srank() {
+    if constexpr (CS == 1) return 0;
+    else return (int)cooperative_groups::this_cluster().block_rank();
+}
 
 // forward: two real columns (xa, xa+1) -> half spectra rows 0..N/2 of spec
 template <int N>
 __global__ void __launch_bounds__(scol_threads<N>(), 1)
 smooth_fwd_cols_kernel(SmoothArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int T = Pl::T, E = Pl::E, W = scol_lines<N>();
+    constexpr int CS = scs<N>();
+    constexpr int T = Pl::T, E = Pl::E, W = scol_lines<N>(), TL = T / CS, HALF = N / 2;
     extern __shared__ float2 smem32[];
-    const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int xa = (blockIdx.x * W + w) * 2;
+    const int w = threadIdx.x % W;
+    const int t = srank<CS>() * TL + threadIdx.x / W;
+    const int xa = ((blockIdx.x / CS) * W + w) * 2;
     float2* buf = smem32 + w;     // W lines interleaved
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m)
         v[m] = *reinterpret_cast<const float2*>(a.intensity + (size_t)(t + m * T) * N + xa);
-    fft_line<float2, N, -1, 16, W>(v, buf, t, a.tw);
+    if constexpr (CS == 2) line_sync<CS>();
+    fft_line<float2, N, -1, 16, W, 0, CS>(v, buf, t, a.tw);
     // Z[N-k] lives in another thread: go through shared memory (natural order)
+    float2* bufs[CS];
+    if constexpr (CS == 1) {
+        bufs[0] = buf;
+    } else {
+        bufs[0] = cooperative_groups::this_cluster().map_shared_rank(buf, 0);
+        bufs[1] = cooperative_groups::this_cluster().map_shared_rank(buf, 1);
+    }
 #pragma unroll
-    for (int m = 0; m < E; ++m) buf[pad16(t + m * T) * W] = v[m];
-    __syncthreads();
+    for (int m = 0; m < E; ++m) {
+        const int e = t + m * T, o = CS == 2 && e >= HALF ? 1 : 0;
+        bufs[o][pad16(e - o * HALF) * W] = v[m];
+    }
+    line_sync<CS>();
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int k = t + m * T;
         if (k <= N / 2) {
+            const int e = (N - k) & (N - 1), o = CS == 2 && e >= HALF ? 1 : 0;
             const float2 z = v[m];
-            const float2 zc = conjc(buf[pad16((N - k) & (N - 1)) * W]);
+            const float2 zc = conjc(bufs[o][pad16(e - o * HALF) * W]);
             // X_a = (Z + conj Z(-k))/2, X_b = (Z - conj Z(-k))/(2i)
             const float2 xa_ = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y + zc.y));
             const float2 xb_ = make_float2(0.5f * (z.y - zc.y), -0.5f * (z.x - zc.x));
             *reinterpret_cast<float4*>(a.spec + (size_t)k * N + xa) = make_float4(xa_.x, xa_.y, xb_.x, xb_.y);
         }
     }
-    __syncthreads();
+    line_sync<CS>();
 }
 
 // rows of the half spectrum: FFT_x, times K/N^2, IFFT_x
@@ -56,16 +77,19 @@ template <int N>
 __global__ void __launch_bounds__(srow_threads<N>(), 1)
 smooth_rows_kernel(SmoothArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int T = Pl::T, E = Pl::E, B = srow_lines<N>();
+    constexpr int CS = scs<N>();
+    constexpr int T = Pl::T, E = Pl::E, B = srow_lines<N>(), TL = T / CS;
     extern __shared__ float2 smem32[];
-    const int team = threadIdx.x / T, t = threadIdx.x % T;
-    const int ky = blockIdx.x * B + team;
+    const int team = threadIdx.x / TL;
+    const int t = srank<CS>() * TL + threadIdx.x % TL;
+    const int ky = (blockIdx.x / CS) * B + team;
     const bool live = ky <= N / 2;
     float2* row = a.spec + (size_t)(live ? ky : 0) * N;
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = live ? row[t + m * T] : make_float2(0.f, 0.f);
-    fft_line<float2, N, -1>(v, smem32 + team * Pl::BUF, t, a.tw);
+    if constexpr (CS == 2) line_sync<CS>();
+    fft_line<float2, N, -1, 16, 1, 0, CS>(v, smem32 + team * (Pl::BUF / CS), t, a.tw);
     // mx^2 + my^2 <= N^2/2 is exact in FP32 for N <= 4096 and within one rounding above
     const float inv = 1.0f / ((float)N * (float)N);
     const float twopi_r = (float)(2.0 * kPi * a.radius_over_L);
@@ -77,11 +101,12 @@ smooth_rows_kernel(SmoothArgs a) {
         const float K = u > 0.0f ? 2.0f * j1f(u) / u : 1.0f;
         v[m] = v[m] * (K * inv);
     }
-    fft_line<float2, N, +1>(v, smem32 + team * Pl::BUF, t, a.tw);
+    fft_line<float2, N, +1, 16, 1, 0, CS>(v, smem32 + team * (Pl::BUF / CS), t, a.tw);
     if (live) {
 #pragma unroll
         for (int m = 0; m < E; ++m) row[t + m * T] = v[m];
     }
+    if constexpr (CS == 2) line_sync<CS>();
 }
 
 // inverse: half spectra -> two real columns
@@ -89,10 +114,12 @@ template <int N>
 __global__ void __launch_bounds__(scol_threads<N>(), 1)
 smooth_inv_cols_kernel(SmoothArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int T = Pl::T, E = Pl::E, W = scol_lines<N>();
+    constexpr int CS = scs<N>();
+    constexpr int T = Pl::T, E = Pl::E, W = scol_lines<N>(), TL = T / CS;
     extern __shared__ float2 smem32[];
-    const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int xa = (blockIdx.x * W + w) * 2;
+    const int w = threadIdx.x % W;
+    const int t = srank<CS>() * TL + threadIdx.x / W;
+    const int xa = ((blockIdx.x / CS) * W + w) * 2;
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -104,14 +131,16 @@ smooth_inv_cols_kernel(SmoothArgs a) {
         const float2 Xb = lo ? make_float2(q.z, q.w) : make_float2(q.z, -q.w);
         v[m] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);   // Z = X_a + i X_b
     }
-    fft_line<float2, N, +1, 16, W>(v, smem32 + w, t, a.tw);
+    if constexpr (CS == 2) line_sync<CS>();
+    fft_line<float2, N, +1, 16, W, 0, CS>(v, smem32 + w, t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m)
         *reinterpret_cast<float2*>(a.intensity + (size_t)(t + m * T) * N + xa) = v[m];
+    if constexpr (CS == 2) line_sync<CS>();
 }
 
-template <int N> constexpr size_t scol_smem() { return (size_t)scol_lines<N>() * FftPlan<N>::BUF * sizeof(float2); }
-template <int N> constexpr size_t srow_smem() { return (size_t)srow_lines<N>() * FftPlan<N>::BUF * sizeof(float2); }
+template <int N> constexpr size_t scol_smem() { return (size_t)scol_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>(); }
+template <int N> constexpr size_t srow_smem() { return (size_t)srow_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>(); }
 
 // which = 0: forward column pass, 1: row pass, 2: inverse column pass
 cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {
@@ -120,22 +149,22 @@ cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {
         if constexpr (N < 32) {
             return cudaErrorNotSupported;
         } else {
+            constexpr int CS = scs<N>();
             cudaError_t e;
-            // every block of the column passes holds W line pairs = 2W real columns
-            const int col_blocks = N / (2 * scol_lines<N>());
+            // every block (cluster) of the column passes holds W line pairs = 2W real columns
+            const int col_blocks = N / (2 * scol_lines<N>()) * CS;
             if (which == 0) {
                 if ((e = set_smem(smooth_fwd_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
-                smooth_fwd_cols_kernel<N><<<col_blocks, scol_threads<N>(), scol_smem<N>(), s>>>(a);
+                return launch_k(smooth_fwd_cols_kernel<N>, CS, dim3(col_blocks), dim3(scol_threads<N>()), scol_smem<N>(), s, a);
             } else if (which == 1) {
                 if ((e = set_smem(smooth_rows_kernel<N>, srow_smem<N>())) != cudaSuccess) return e;
                 const int rows = N / 2 + 1;
-                smooth_rows_kernel<N><<<(rows + srow_lines<N>() - 1) / srow_lines<N>(), srow_threads<N>(),
-                                        srow_smem<N>(), s>>>(a);
+                return launch_k(smooth_rows_kernel<N>, CS, dim3((rows + srow_lines<N>() - 1) / srow_lines<N>() * CS),
+                                dim3(srow_threads<N>()), srow_smem<N>(), s, a);
             } else {
                 if ((e = set_smem(smooth_inv_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
-                smooth_inv_cols_kernel<N><<<col_blocks, scol_threads<N>(), scol_smem<N>(), s>>>(a);
+                return launch_k(smooth_inv_cols_kernel<N>, CS, dim3(col_blocks), dim3(scol_threads<N>()), scol_smem<N>(), s, a);
             }
-            return cudaGetLastError();
         }
     });
 }

@@ -86,62 +86,77 @@ SCINT_DEV double2 spectrum_bin(const SynthArgs& a, int kx, int ky) {
     return make_double2((double)(sig * r * cs), (double)(sig * r * sn));
 }
 
+// Lines per block (all transformed together); N = 16384 lines (256 KB in FP64)
+// are split over a cluster of two blocks (fft.cuh, CS = 2).
+template <int N> __host__ __device__ constexpr int synth_cs() { return N >= 16384 ? 2 : 1; }
 template <int N> __host__ __device__ constexpr int synth_lines() { return N >= kTile64 ? 1 : (kTile64 / N < N ? kTile64 / N : N); }
-template <int N> __host__ __device__ constexpr int synth_threads() { return synth_lines<N>() * FftPlan<N>::T; }
+template <int N> __host__ __device__ constexpr int synth_threads() { return synth_lines<N>() * FftPlan<N>::T / synth_cs<N>(); }
 // strip width of the intermediate: at least 2 complex128 columns (whole 32-byte sectors per row)
 template <int N> __host__ __device__ constexpr int synth_strip() { return synth_lines<N>() >= 2 ? synth_lines<N>() : 2; }
+template <int N> constexpr size_t synth_smem() { return (size_t)synth_lines<N>() * FftPlan<N>::BUF * sizeof(double2) / synth_cs<N>(); }
+
+template <int CS> SCINT_DEV int synth_rank() {
+    if constexpr (CS == 1) return 0;
+    else return (int)cooperative_groups::this_cluster().block_rank();
+}
 
 template <int N>
 __global__ void __launch_bounds__(synth_threads<N>())
 synth_rows_kernel(SynthArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int T = Pl::T, E = Pl::E, B = synth_lines<N>(), W = synth_strip<N>();
+    constexpr int CS = synth_cs<N>();
+    constexpr int T = Pl::T, E = Pl::E, B = synth_lines<N>(), W = synth_strip<N>(), TL = T / CS;
     extern __shared__ double2 smem64[];
-    const int team = threadIdx.x / T, t = threadIdx.x % T;
-    const int ky = blockIdx.x * B + team;
+    const int team = threadIdx.x / TL;
+    const int t = synth_rank<CS>() * TL + threadIdx.x % TL;
+    const int ky = (blockIdx.x / CS) * B + team;
     double2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = spectrum_bin(a, t + m * T, ky);
-    fft_line<double2, N, +1>(v, smem64 + team * Pl::BUF, t, a.tw);
+    if constexpr (CS == 2) line_sync<CS>();       // the partner block is running before its buffer is touched
+    fft_line<double2, N, +1, 16, 1, 0, CS>(v, smem64 + team * (Pl::BUF / CS), t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int x = t + m * T;
         a.work[(size_t)(x / W) * N * W + (size_t)ky * W + (x % W)] = v[m];
     }
+    if constexpr (CS == 2) line_sync<CS>();
 }
 
 template <int N>
 __global__ void __launch_bounds__(synth_threads<N>())
 synth_cols_kernel(SynthArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int T = Pl::T, E = Pl::E, W = synth_lines<N>(), WL = synth_strip<N>();
+    constexpr int CS = synth_cs<N>();
+    constexpr int T = Pl::T, E = Pl::E, W = synth_lines<N>(), WL = synth_strip<N>(), TL = T / CS;
     extern __shared__ double2 smem64[];
-    const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int x = blockIdx.x * W + w;
-    const int x0 = blockIdx.x * W;
+    const int w = threadIdx.x % W;
+    const int t = synth_rank<CS>() * TL + threadIdx.x / W;
+    const int x0 = (blockIdx.x / CS) * W;
+    const int x = x0 + w;
     const double2* src = a.work + (size_t)(x0 / WL) * N * WL + (x0 % WL);
     double2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * WL + w];
-    fft_line<double2, N, +1, 16, W>(v, smem64 + w, t, a.tw);     // W lines interleaved
+    if constexpr (CS == 2) line_sync<CS>();
+    fft_line<double2, N, +1, 16, W, 0, CS>(v, smem64 + w, t, a.tw);     // W lines interleaved
 #pragma unroll
     for (int m = 0; m < E; ++m) a.phi[(size_t)(t + m * T) * N + x] = a.out_scale * v[m].x;
+    if constexpr (CS == 2) line_sync<CS>();
 }
 
 template <bool ROWS>
 cudaError_t launch_synth_pass(const SynthArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
-        if constexpr (N > 8192) {
+        if constexpr (synth_smem<N>() > 227 * 1024) {
             return cudaErrorNotSupported;
         } else {
-            constexpr int threads = synth_threads<N>();
-            constexpr size_t smem = (size_t)synth_lines<N>() * FftPlan<N>::BUF * sizeof(double2);
             auto k = ROWS ? synth_rows_kernel<N> : synth_cols_kernel<N>;
-            cudaError_t e = set_smem(k, smem);
+            cudaError_t e = set_smem(k, synth_smem<N>());
             if (e != cudaSuccess) return e;
-            k<<<N / synth_lines<N>(), threads, smem, s>>>(a);
-            return cudaGetLastError();
+            return launch_k(k, synth_cs<N>(), dim3(N / synth_lines<N>() * synth_cs<N>()), dim3(synth_threads<N>()),
+                            synth_smem<N>(), s, a);
         }
     });
 }
