@@ -64,6 +64,11 @@ def _workload(name: str, rank: int):
         items = W.config3()
         desc = ("batched: 48 screens (16 each of 1024^2, 2048^2, 4096^2, 10 km pixels, R_diff U[30,300] km) "
                 "x 32 wavelengths 400-700 nm, disk sources U[0.1,2] R_ref, 8 tracks/screen")
+    elif name == "profile":
+        items = [x for x in W.config3() if x["n"] == 4096][:1]
+        items[0]["lambdas_nm"] = items[0]["lambdas_nm"][::4]
+        desc = ("profiling case: one 4096^2 screen of the batched workload x 8 wavelengths "
+                "(~1.2 GB on the device, above the L2 size)")
     else:
         items = W.config2(r_diffs=(100.0,))
         items[0]["lambdas_nm"] = np.array([500.0])
@@ -329,7 +334,7 @@ def run_ours(args):
 
     cpu = None
     err = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and any(x["n"] == 1024 for x in items):
         it = [x for x in items if x["n"] == 1024][0]
         i = items.index(it)
         p = P[i]
@@ -364,7 +369,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "single4096"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

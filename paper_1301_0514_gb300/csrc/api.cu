@@ -91,7 +91,7 @@ double f_beta(double beta) {
 constexpr size_t kAlign = 256;
 size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
-size_t ws_synth(int n) { return up((size_t)n * 16) + up((size_t)n * n * 16); }
+size_t ws_synth(int n) { return up((size_t)n * 16) + up((size_t)(n / 2 + 1) * n * 16); }
 size_t ws_prop(int n, int g) {
     return up((size_t)n * 8) + up((size_t)g * n * 8) + up((size_t)g * n * 4) + up((size_t)g * n * n * 8);
 }
@@ -397,13 +397,16 @@ int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_
     if (rc) return rc;
     SynthArgs a = synth_args(p);
     a.tw = c.take<double2>((size_t)p->n * 16);
-    a.work = c.take<double2>((size_t)p->n * p->n * 16);
+    a.work = c.take<double2>((size_t)(p->n / 2 + 1) * p->n * 16);
     a.phi = phi;
     const double nn = (double)p->n * p->n;
     SCINT_LAUNCH(K_TWIDDLES, 16.0 * p->n, 0.0, s, launch_twiddles64(const_cast<double2*>(a.tw), p->n, s));
     // rows: the noise is generated in registers, the half-transformed field is written
-    SCINT_LAUNCH(K_SYNTH_ROWS, 16.0 * nn, p->n * fft_flops(p->n), s, launch_synth_rows(a, s));
-    SCINT_LAUNCH(K_SYNTH_COLS, 16.0 * nn + 8.0 * nn, p->n * fft_flops(p->n), s, launch_synth_cols(a, s));
+    const double half = (double)(p->n / 2 + 1) * p->n * 16.0;
+    // rows: the noise is generated in registers, rows 0..n/2 of the x-transformed field are written
+    SCINT_LAUNCH(K_SYNTH_ROWS, half, (p->n / 2 + 1) * fft_flops(p->n), s, launch_synth_rows(a, s));
+    // columns: two real columns per complex transform
+    SCINT_LAUNCH(K_SYNTH_COLS, half + 8.0 * nn, (p->n / 2) * fft_flops(p->n), s, launch_synth_cols(a, s));
     return ok();
 }
 

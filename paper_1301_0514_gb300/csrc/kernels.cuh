@@ -37,7 +37,7 @@ struct SynthArgs {
     float amp32, neg_beta_4_32;   // the same in FP32 for the high-frequency bins
     double out_scale;    // sqrt(2) / L^2
     const double2* tw;   // FP64 twiddles for n
-    double2* work;       // n*n complex128, strip layout
+    double2* work;       // (n/2 + 1) x n complex128, row-major: rows ky = 0..n/2 after the x transform
     double* phi;         // n*n, row-major
 };
 cudaError_t launch_synth_rows(const SynthArgs& a, cudaStream_t s);

@@ -19,6 +19,10 @@ template <int N> __host__ __device__ constexpr int scol_threads() { return scol_
 template <int N> __host__ __device__ constexpr int srow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N / 2 ? kTileRow32 / N : N / 2); }
 template <int N> __host__ __device__ constexpr int srow_threads() { return srow_lines<N>() * FftPlan<N>::T / scs<N>(); }
 
+// shared twiddle table below the split size (after the line buffers)
+template <int N> __host__ __device__ constexpr int stwm() { return scs<N>() == 1 ? 1 : 0; }
+template <int N> constexpr size_t stws_bytes() { return stwm<N>() == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0; }
+
 template <int CS> SCINT_DEV int srank() {
     if constexpr (CS == 1) return 0;
     else return (int)cooperative_groups::this_cluster().block_rank();
@@ -36,12 +40,16 @@ smooth_fwd_cols_kernel(SmoothArgs a) {
     const int t = srank<CS>() * TL + threadIdx.x / W;
     const int xa = ((blockIdx.x / CS) * W + w) * 2;
     float2* buf = smem32 + w;     // W lines interleaved
+    constexpr int TWM = stwm<N>();
+    float2* tws = smem32 + W * (Pl::BUF / CS);
+    if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+    const float2* twp = TWM == 1 ? tws : a.tw;
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m)
         v[m] = *reinterpret_cast<const float2*>(a.intensity + (size_t)(t + m * T) * N + xa);
-    if constexpr (CS == 2) line_sync<CS>();
-    fft_line<float2, N, -1, 16, W, 0, CS>(v, buf, t, a.tw);
+    line_sync<CS>();
+    fft_line<float2, N, -1, 16, W, TWM, CS>(v, buf, t, twp);
     // Z[N-k] lives in another thread: go through shared memory (natural order)
     float2* bufs[CS];
     if constexpr (CS == 1) {
@@ -85,11 +93,15 @@ smooth_rows_kernel(SmoothArgs a) {
     const int ky = (blockIdx.x / CS) * B + team;
     const bool live = ky <= N / 2;
     float2* row = a.spec + (size_t)(live ? ky : 0) * N;
+    constexpr int TWM = stwm<N>();
+    float2* tws = smem32 + B * (Pl::BUF / CS);
+    if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+    const float2* twp = TWM == 1 ? tws : a.tw;
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = live ? row[t + m * T] : make_float2(0.f, 0.f);
-    if constexpr (CS == 2) line_sync<CS>();
-    fft_line<float2, N, -1, 16, 1, 0, CS>(v, smem32 + team * (Pl::BUF / CS), t, a.tw);
+    line_sync<CS>();
+    fft_line<float2, N, -1, 16, 1, TWM, CS>(v, smem32 + team * (Pl::BUF / CS), t, twp);
     // mx^2 + my^2 <= N^2/2 is exact in FP32 for N <= 4096 and within one rounding above
     const float inv = 1.0f / ((float)N * (float)N);
     const float twopi_r = (float)(2.0 * kPi * a.radius_over_L);
@@ -101,7 +113,7 @@ smooth_rows_kernel(SmoothArgs a) {
         const float K = u > 0.0f ? 2.0f * j1f(u) / u : 1.0f;
         v[m] = v[m] * (K * inv);
     }
-    fft_line<float2, N, +1, 16, 1, 0, CS>(v, smem32 + team * (Pl::BUF / CS), t, a.tw);
+    fft_line<float2, N, +1, 16, 1, TWM, CS>(v, smem32 + team * (Pl::BUF / CS), t, twp);
     if (live) {
 #pragma unroll
         for (int m = 0; m < E; ++m) row[t + m * T] = v[m];
@@ -131,16 +143,20 @@ smooth_inv_cols_kernel(SmoothArgs a) {
         const float2 Xb = lo ? make_float2(q.z, q.w) : make_float2(q.z, -q.w);
         v[m] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);   // Z = X_a + i X_b
     }
-    if constexpr (CS == 2) line_sync<CS>();
-    fft_line<float2, N, +1, 16, W, 0, CS>(v, smem32 + w, t, a.tw);
+    constexpr int TWM = stwm<N>();
+    float2* tws = smem32 + W * (Pl::BUF / CS);
+    if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+    const float2* twp = TWM == 1 ? tws : a.tw;
+    line_sync<CS>();
+    fft_line<float2, N, +1, 16, W, TWM, CS>(v, smem32 + w, t, twp);
 #pragma unroll
     for (int m = 0; m < E; ++m)
         *reinterpret_cast<float2*>(a.intensity + (size_t)(t + m * T) * N + xa) = v[m];
     if constexpr (CS == 2) line_sync<CS>();
 }
 
-template <int N> constexpr size_t scol_smem() { return (size_t)scol_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>(); }
-template <int N> constexpr size_t srow_smem() { return (size_t)srow_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>(); }
+template <int N> constexpr size_t scol_smem() { return (size_t)scol_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>() + stws_bytes<N>(); }
+template <int N> constexpr size_t srow_smem() { return (size_t)srow_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>() + stws_bytes<N>(); }
 
 // which = 0: forward column pass, 1: row pass, 2: inverse column pass
 cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {

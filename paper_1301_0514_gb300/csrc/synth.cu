@@ -1,11 +1,18 @@
 // FP64 phase-screen synthesis (Sect. 3.1, Eq. spectre, Eq. densite).
 //
-// Pass 1 (rows of the spectrum): each team generates the shaped Gaussian noise
-// F[ky][kx] of one spectral row in registers (Philox4x32-10 + Box-Muller,
-// amplitude sqrt(L^2 S_phi(q))), inverse-transforms it along x and writes the
-// half-transformed row into the strip-layout intermediate.  The noise is never
-// stored.
-// Pass 2 (columns): inverse transform along y and write phi = sqrt(2)/L^2 Re(.).
+// phi = sqrt(2)/L^2 Re sum_k F_k e^{+2 pi i k.x}; the real part of the inverse
+// transform of F equals the inverse transform of its Hermitian part
+// F_h(k) = (F(k) + conj F(-k)) / 2, whose transform is real.  So:
+// Row pass (spectral rows ky = 0..N/2 only): each team generates F_h of one
+//   row in registers (for every bin the noise of (ky, kx) and of the mirror
+//   bin (-ky, -kx), Philox4x32-10 + Box-Muller, amplitude sqrt(L^2 S(q))),
+//   inverse-transforms it along x and writes the row G(ky, x); rows N/2+1..N-1
+//   are conj G(N-ky, x) and are never formed.
+// Column pass: two real columns per complex transform: Z(ky) = G_a(ky) + i
+//   G_b(ky) over all ky (Hermitian extension), inverse transform along y, and
+//   phi_a = sqrt(2)/L^2 Re, phi_b = sqrt(2)/L^2 Im.
+// This halves the FP64 transform work and the intermediate (row-major,
+// (N/2+1) x N complex128).  The noise is never stored.
 #include "dispatch.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
@@ -91,13 +98,23 @@ SCINT_DEV double2 spectrum_bin(const SynthArgs& a, int kx, int ky) {
 template <int N> __host__ __device__ constexpr int synth_cs() { return N >= 16384 ? 2 : 1; }
 template <int N> __host__ __device__ constexpr int synth_lines() { return N >= kTile64 ? 1 : (kTile64 / N < N ? kTile64 / N : N); }
 template <int N> __host__ __device__ constexpr int synth_threads() { return synth_lines<N>() * FftPlan<N>::T / synth_cs<N>(); }
-// strip width of the intermediate: at least 2 complex128 columns (whole 32-byte sectors per row)
-template <int N> __host__ __device__ constexpr int synth_strip() { return synth_lines<N>() >= 2 ? synth_lines<N>() : 2; }
+// column pass: complex lines (each two real output columns) per block, at most N/2
+template <int N> __host__ __device__ constexpr int synth_col_lines() { return synth_lines<N>() < N / 2 ? synth_lines<N>() : N / 2; }
+template <int N> __host__ __device__ constexpr int synth_col_threads() { return synth_col_lines<N>() * FftPlan<N>::T / synth_cs<N>(); }
 template <int N> constexpr size_t synth_smem() { return (size_t)synth_lines<N>() * FftPlan<N>::BUF * sizeof(double2) / synth_cs<N>(); }
+template <int N> constexpr size_t synth_col_smem() { return (size_t)synth_col_lines<N>() * FftPlan<N>::BUF * sizeof(double2) / synth_cs<N>(); }
 
 template <int CS> SCINT_DEV int synth_rank() {
     if constexpr (CS == 1) return 0;
     else return (int)cooperative_groups::this_cluster().block_rank();
+}
+
+// F_h(ky, kx) = (F(ky, kx) + conj F(-ky, -kx)) / 2
+SCINT_DEV double2 hermitian_bin(const SynthArgs& a, int kx, int ky) {
+    const int n = a.n;
+    const double2 f = spectrum_bin(a, kx, ky);
+    const double2 g = spectrum_bin(a, (n - kx) & (n - 1), (n - ky) & (n - 1));
+    return make_double2(0.5 * (f.x + g.x), 0.5 * (f.y - g.y));
 }
 
 template <int N>
@@ -105,43 +122,54 @@ __global__ void __launch_bounds__(synth_threads<N>())
 synth_rows_kernel(SynthArgs a) {
     using Pl = FftPlan<N>;
     constexpr int CS = synth_cs<N>();
-    constexpr int T = Pl::T, E = Pl::E, B = synth_lines<N>(), W = synth_strip<N>(), TL = T / CS;
+    constexpr int T = Pl::T, E = Pl::E, B = synth_lines<N>(), TL = T / CS;
     extern __shared__ double2 smem64[];
     const int team = threadIdx.x / TL;
     const int t = synth_rank<CS>() * TL + threadIdx.x % TL;
     const int ky = (blockIdx.x / CS) * B + team;
+    const bool live = ky <= N / 2;                 // rows above N/2 are the conjugates of rows below
     double2 v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = spectrum_bin(a, t + m * T, ky);
-    if constexpr (CS == 2) line_sync<CS>();       // the partner block is running before its buffer is touched
+    for (int m = 0; m < E; ++m) v[m] = live ? hermitian_bin(a, t + m * T, ky) : make_double2(0.0, 0.0);
+    line_sync<CS>();
     fft_line<double2, N, +1, 16, 1, 0, CS>(v, smem64 + team * (Pl::BUF / CS), t, a.tw);
+    if (live) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        const int x = t + m * T;
-        a.work[(size_t)(x / W) * N * W + (size_t)ky * W + (x % W)] = v[m];
+        for (int m = 0; m < E; ++m) a.work[(size_t)ky * N + t + m * T] = v[m];
     }
     if constexpr (CS == 2) line_sync<CS>();
 }
 
+// two real output columns (xa, xa + 1) per complex line
 template <int N>
-__global__ void __launch_bounds__(synth_threads<N>())
+__global__ void __launch_bounds__(synth_col_threads<N>())
 synth_cols_kernel(SynthArgs a) {
     using Pl = FftPlan<N>;
     constexpr int CS = synth_cs<N>();
-    constexpr int T = Pl::T, E = Pl::E, W = synth_lines<N>(), WL = synth_strip<N>(), TL = T / CS;
+    constexpr int T = Pl::T, E = Pl::E, W = synth_col_lines<N>(), TL = T / CS;
     extern __shared__ double2 smem64[];
     const int w = threadIdx.x % W;
     const int t = synth_rank<CS>() * TL + threadIdx.x / W;
-    const int x0 = (blockIdx.x / CS) * W;
-    const int x = x0 + w;
-    const double2* src = a.work + (size_t)(x0 / WL) * N * WL + (x0 % WL);
+    const int xa = ((blockIdx.x / CS) * W + w) * 2;
     double2 v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * WL + w];
-    if constexpr (CS == 2) line_sync<CS>();
+    for (int m = 0; m < E; ++m) {
+        const int ky = t + m * T;
+        const bool lo = ky <= N / 2;
+        const double2* g = a.work + (size_t)(lo ? ky : N - ky) * N + xa;
+        const double2 ga = g[0], gb = g[1];
+        // G(ky) = conj G(N - ky) above N/2; Z = G_a + i G_b
+        const double2 za = lo ? ga : conjc(ga), zb = lo ? gb : conjc(gb);
+        v[m] = make_double2(za.x - zb.y, za.y + zb.x);
+    }
+    line_sync<CS>();
     fft_line<double2, N, +1, 16, W, 0, CS>(v, smem64 + w, t, a.tw);     // W lines interleaved
 #pragma unroll
-    for (int m = 0; m < E; ++m) a.phi[(size_t)(t + m * T) * N + x] = a.out_scale * v[m].x;
+    for (int m = 0; m < E; ++m) {
+        double* o = a.phi + (size_t)(t + m * T) * N + xa;
+        o[0] = a.out_scale * v[m].x;
+        o[1] = a.out_scale * v[m].y;
+    }
     if constexpr (CS == 2) line_sync<CS>();
 }
 
@@ -152,11 +180,18 @@ cudaError_t launch_synth_pass(const SynthArgs& a, cudaStream_t s) {
         if constexpr (synth_smem<N>() > 227 * 1024) {
             return cudaErrorNotSupported;
         } else {
-            auto k = ROWS ? synth_rows_kernel<N> : synth_cols_kernel<N>;
-            cudaError_t e = set_smem(k, synth_smem<N>());
-            if (e != cudaSuccess) return e;
-            return launch_k(k, synth_cs<N>(), dim3(N / synth_lines<N>() * synth_cs<N>()), dim3(synth_threads<N>()),
-                            synth_smem<N>(), s, a);
+            constexpr int CS = synth_cs<N>();
+            cudaError_t e;
+            if (ROWS) {
+                if ((e = set_smem(synth_rows_kernel<N>, synth_smem<N>())) != cudaSuccess) return e;
+                const int rows = N / 2 + 1;
+                return launch_k(synth_rows_kernel<N>, CS, dim3((rows + synth_lines<N>() - 1) / synth_lines<N>() * CS),
+                                dim3(synth_threads<N>()), synth_smem<N>(), s, a);
+            } else {
+                if ((e = set_smem(synth_cols_kernel<N>, synth_col_smem<N>())) != cudaSuccess) return e;
+                return launch_k(synth_cols_kernel<N>, CS, dim3(N / (2 * synth_col_lines<N>()) * CS),
+                                dim3(synth_col_threads<N>()), synth_col_smem<N>(), s, a);
+            }
         }
     });
 }
