@@ -78,12 +78,12 @@ def _workload(name: str, rank: int):
     return items, desc
 
 
-def _kernel_source_hash():
+def _kernel_source_hash(files):
+    """Hash of the CUDA sources a kernel is built from (a traffic record is void once they change)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1301_0514_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -312,8 +312,10 @@ def run_ours(args):
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         rec = tr.get(dom_name)
-        if rec and rec.get("source_hash") == _kernel_source_hash():
-            traffic = rec["bytes_per_launch"]
+        if rec and rec.get("source_hash") == _kernel_source_hash(rec["sources"]):
+            # DRAM bytes of one captured launch scale with the lines it processes:
+            # the captured dram/algorithmic ratio times this launch's algorithmic bytes
+            traffic = rec["dram_over_algorithmic"] * dom["bytes"] / dom["launches"]
     except Exception:
         pass
     if intensity > ridge:

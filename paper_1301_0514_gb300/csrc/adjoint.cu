@@ -54,14 +54,14 @@ cudaError_t launch_lightcurve_adjoint(const CurveAdjArgs& a, cudaStream_t s) {
 // buffers, the g_I columns (in place of the accumulator) and the twiddle table
 template <int N> constexpr size_t acol_smem() {
     return (size_t)pcol_lines<N>() * (FftPlan<N, kColEPT>::BUF * sizeof(float2) + N * sizeof(float)) / pcs<N>() +
-           (ptwm<N>() == 0 ? 0 : (size_t)FftPlan<N>::TWS * sizeof(float2));
+           (pcs<N>() == 2 ? 0 : (size_t)FftPlan<N>::TWS * sizeof(float2));
 }
 
 template <int N>
 __global__ void __launch_bounds__(pcol_threads<N>(), 1)
 adj_cols_kernel(AdjArgs a) {
     using Pl = FftPlan<N, kColEPT>;
-    constexpr int CS = pcs<N>(), TWM = ptwm<N>() == 0 ? 0 : 1;
+    constexpr int CS = pcs<N>(), TWM = pcs<N>() == 2 ? 0 : 1;   // shared twiddle table unless split
     constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
     constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
     extern __shared__ float2 smem32[];
@@ -105,14 +105,14 @@ adj_cols_kernel(AdjArgs a) {
 // buffers, fixed-point phases, twiddle table, g_phi accumulators
 template <int N> constexpr size_t arow_smem() {
     return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long) + N * sizeof(float)) / pcs<N>() +
-           (ptwm<N>() == 0 ? 0 : (size_t)FftPlan<N>::TWS * sizeof(float2));
+           (pcs<N>() == 2 ? 0 : (size_t)FftPlan<N>::TWS * sizeof(float2));
 }
 
 template <int N>
 __global__ void __launch_bounds__(prow_threads<N>(), 1)
 adj_rows_kernel(AdjArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int CS = pcs<N>(), TWM = ptwm<N>() == 0 ? 0 : 1;
+    constexpr int CS = pcs<N>(), TWM = pcs<N>() == 2 ? 0 : 1;   // shared twiddle table unless split
     constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), WL = pstrip<N>();
     constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
     constexpr int TWSL = TWM == 1 ? Pl::TWS : 0;

@@ -58,7 +58,7 @@ template <int N>
 __global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
 prop_rows_kernel(PropArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int CS = pcs<N>(), TWM = ptwm<N>();
+    constexpr int CS = pcs<N>(), TWM = prow_twm<N>();
     constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), W = pstrip<N>();
     constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
     extern __shared__ float2 smem32[];
@@ -105,7 +105,7 @@ template <int N>
 __global__ void __launch_bounds__(pcol_threads<N>(), 1)
 prop_cols_kernel(PropArgs a) {
     using Pl = FftPlan<N, kColEPT>;
-    constexpr int CS = pcs<N>(), TWM = ptwm<N>();
+    constexpr int CS = pcs<N>(), TWM = pcol_twm<N>();
     constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
     constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
     extern __shared__ float2 smem32[];

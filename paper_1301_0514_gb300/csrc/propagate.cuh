@@ -4,15 +4,22 @@
 #include "fft.cuh"
 #include "kernels.cuh"
 
-// Twiddle source of the propagation FFTs (a build-time tuning choice):
-// 1 = per-block shared table, 2 = per-thread register bases + products.
-#ifndef SCINT_PROP_TWIDDLES
-#define SCINT_PROP_TWIDDLES 1
+// Twiddle source of the propagation FFTs (build-time tuning choices, measured on
+// GB300 at 1024^2-4096^2 x 32 wavelengths): 1 = per-block shared table,
+// 2 = per-thread register bases + products.  The row pass is faster with
+// register bases (its 2 blocks/SM keep the shared-memory pipe busy), the column
+// pass with the shared table (its single block/SM has registers to spare).
+#ifndef SCINT_ROW_TWIDDLES
+#define SCINT_ROW_TWIDDLES 2
+#endif
+#ifndef SCINT_COL_TWIDDLES
+#define SCINT_COL_TWIDDLES 1
 #endif
 
 namespace scint {
 
-constexpr int kPropTw = SCINT_PROP_TWIDDLES;
+constexpr int kRowTw = SCINT_ROW_TWIDDLES;
+constexpr int kColTw = SCINT_COL_TWIDDLES;
 constexpr int kColEPT = 16;   // values per thread in the column passes
 constexpr size_t kMaxSmem = 227 * 1024;
 
@@ -21,7 +28,8 @@ constexpr size_t kMaxSmem = 227 * 1024;
 // table.  Own-entry arrays (fixed-point phases, accumulators) hold the N/CS
 // entries of the line that the block's threads own.
 template <int N> __host__ __device__ constexpr int pcs() { return N >= 16384 ? 2 : 1; }
-template <int N> __host__ __device__ constexpr int ptwm() { return pcs<N>() == 2 ? 0 : kPropTw; }
+template <int N> __host__ __device__ constexpr int prow_twm() { return pcs<N>() == 2 ? 0 : kRowTw; }
+template <int N> __host__ __device__ constexpr int pcol_twm();   // below: depends on the shared-memory budget
 
 // rows per row-pass block, columns per column-pass block (all lines of a block
 // are transformed together); threads are per block
@@ -34,13 +42,20 @@ template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_
 // pcol_lines() columns out of one strip (sibling blocks share the sectors in L2).
 template <int N> __host__ __device__ constexpr int pstrip() { return pcol_lines<N>() >= 4 ? pcol_lines<N>() : (N >= 4 ? 4 : N); }
 
-template <int N> constexpr size_t ptws_bytes() { return ptwm<N>() == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0; }
+template <int N> constexpr size_t ptws_bytes(int twm) { return twm == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0; }
 template <int N> constexpr size_t prow_smem() {
-    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) / pcs<N>() + ptws_bytes<N>();
+    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) / pcs<N>() +
+           ptws_bytes<N>(prow_twm<N>());
 }
-template <int N> constexpr size_t pcol_smem() {
-    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float)) / pcs<N>() + ptws_bytes<N>();
+// column pass: line buffers, accumulators and (when it fits) the twiddle table
+template <int N> __host__ __device__ constexpr size_t pcol_base_bytes() {
+    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float)) / pcs<N>();
 }
+template <int N> __host__ __device__ constexpr int pcol_twm() {
+    return pcs<N>() == 2 ? 0
+         : (kColTw == 1 && pcol_base_bytes<N>() + (size_t)FftPlan<N>::TWS * sizeof(float2) > kMaxSmem ? 2 : kColTw);
+}
+template <int N> constexpr size_t pcol_smem() { return pcol_base_bytes<N>() + ptws_bytes<N>(pcol_twm<N>()); }
 
 // rank of this block in its line's cluster (0 when lines are not split)
 template <int CS> SCINT_DEV int line_rank() {
