@@ -7,7 +7,8 @@ propagated at 32 wavelengths in 400-700 nm (flat passband), smoothed by a
 projected stellar disk of U[0.1, 2] R_ref and sampled along 8 straight tracks,
 with the modulation index of the map and of every curve.  A step is one pass of
 the whole hot path over the batch: synthesis -> passband propagation ->
-smoothing -> light curves -> modulation indices, replayed as one CUDA graph.
+smoothing -> light curves -> modulation indices, issued by scint_run_batch on
+four internal streams and replayed as one CUDA graph.
 
 Metric: Fresnel-propagated pixels per second, sum over screens of N^2 x
 N_lambda per step / step time.  Timing: CUDA events on the launching stream,
@@ -207,37 +208,47 @@ def run_ours(args):
     items, desc = _workload(args.workload, rank)
     P = [S.params(**{k: it[k] for k in PARAM_KEYS}) for it in items]
     sizes = sorted({p.n for p in P})
-    n_lam = max(len(it["lambdas_nm"]) for it in items)
-    ws = torch.empty(max(S.workspace_bytes(p, n_lam) for p in P), dtype=torch.uint8, device=dev)
-    phi = {n: torch.empty((n, n), dtype=torch.float64, device=dev) for n in sizes}
-    inten = {n: torch.empty((n, n), dtype=torch.float32, device=dev) for n in sizes}
+    lams, wts = items[0]["lambdas_nm"], items[0]["weights"]
+    assert all(np.array_equal(it["lambdas_nm"], lams) for it in items), "one passband per batch"
+    n_lam = len(lams)
     curves = [torch.empty((len(it["tracks"]), it["n_samples"]), dtype=torch.float32, device=dev) for it in items]
     m_map = torch.empty((len(items), 4), dtype=torch.float64, device=dev)
     m_curve = [torch.empty((len(it["tracks"]), 3), dtype=torch.float64, device=dev) for it in items]
+    # the screen checked against the oracle keeps its intensity map; the others live in lane scratch
+    par_i = next((i for i, p in enumerate(P) if p.n == 1024), None)
+    par_I = torch.empty((1024, 1024), dtype=torch.float32, device=dev) if par_i is not None else None
+    entries = [dict(params=p, tracks=it["tracks"], n_samples=it["n_samples"], curves=curves[i],
+                    m_map=m_map[i], m_curves=m_curve[i], intensity=par_I if i == par_i else None)
+               for i, (p, it) in enumerate(zip(P, items))]
+    batch = S.batch_items(entries)
+    ws = torch.empty(max(S.batch_workspace_bytes(batch, n_lam, args.lanes),
+                         max(S.workspace_bytes(p, 1) for p in P)), dtype=torch.uint8, device=dev)
+    # plain form: its own maps, one per grid size
+    phi = {n: torch.empty((n, n), dtype=torch.float64, device=dev) for n in sizes}
+    inten = {n: torch.empty((n, n), dtype=torch.float32, device=dev) for n in sizes}
     units = sum(p.n * p.n * len(it["lambdas_nm"]) for p, it in zip(P, items))
     stream = torch.cuda.current_stream(dev)
 
-    def screen(i, p, it, plain=False):
+    def plain_screen(i, p, it):
         S.make_screen(p, out=phi[p.n], workspace=ws)
-        if plain:
-            w = it["weights"] if it["weights"] is not None else np.full(len(it["lambdas_nm"]), 1.0 / len(it["lambdas_nm"]))
-            for j, lam in enumerate(it["lambdas_nm"]):
-                S.sum_passband(p, phi[p.n], [lam], [w[j]], out=inten[p.n], accumulate=j > 0, workspace=ws)
-        else:
-            S.sum_passband(p, phi[p.n], it["lambdas_nm"], it["weights"], out=inten[p.n], workspace=ws)
+        w = wts if wts is not None else np.full(n_lam, 1.0 / n_lam)
+        for j, lam in enumerate(lams):
+            S.sum_passband(p, phi[p.n], [lam], [w[j]], out=inten[p.n], accumulate=j > 0, workspace=ws)
         S.smooth_source(p, inten[p.n], workspace=ws)
         S.lightcurve(p, inten[p.n], it["tracks"], it["n_samples"], out=curves[i])
         S.modulation_index(p, inten[p.n], out=m_map[i], workspace=ws)
         S.curve_modulation(curves[i], out=m_curve[i])
 
     def step(plain=False):
-        for i, (p, it) in enumerate(zip(P, items)):
-            screen(i, p, it, plain)
+        if plain:
+            for i, (p, it) in enumerate(zip(P, items)):
+                plain_screen(i, p, it)
+        else:
+            S.run_batch(batch, lams, wts, n_lanes=args.lanes, workspace=ws)
 
     # warm-up outside the graph (sets kernel attributes), then capture one graph of the step
     step()
     torch.cuda.synchronize(dev)
-    S.profile_enable(True)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, capture_error_mode="relaxed"):
         step()
@@ -265,14 +276,30 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    kstats = S.profile_read()           # per-kernel event times of the last timed replay
-    S.profile_enable(False)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = units * world / (ms * 1e-3)
+
+    # Per-kernel times: concurrent lanes share the SMs, so an event pair around a
+    # launch would also count other lanes' kernels.  The kernels are timed in a
+    # serial replay of the same step (one lane, event pairs as graph nodes).
+    S.profile_enable(True)
+    pgraph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(pgraph, capture_error_mode="relaxed"):
+        S.run_batch(batch, lams, wts, n_lanes=1, workspace=ws)
+    torch.cuda.synchronize(dev)
+    pgraph.replay()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    pgraph.replay()
+    q1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_serial = q0.elapsed_time(q1)
+    kstats = S.profile_read()           # per-kernel event times of the last serial replay
+    S.profile_enable(False)
 
     # plain form: one screen and one wavelength per call, no graph, same kernels
     torch.cuda.synchronize(dev)
@@ -303,7 +330,7 @@ def run_ours(args):
     hbm_peak, sm_max_mhz, peak_src = _peaks()
     alu_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     dom_name, dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
-    per_launch_ms = dom["total_ms"] / dom["launches"]
+    per_launch_ms = dom["total_ms"] / dom["launches"]   # from the serial replay
     gbs = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9
     tflops = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12
     ridge = alu_peak_tflops * 1e12 / (hbm_peak * 1e9)
@@ -324,38 +351,39 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": traffic}
-    roof.update({"kernel": dom_name, "launch_ms": per_launch_ms, "share": dom["total_ms"] / ms,
+    roof.update({"kernel": dom_name, "launch_ms": per_launch_ms, "share": dom["total_ms"] / ms_serial,
+                 "timing": f"serial one-lane replay of the step ({ms_serial:.1f} ms), CUDA events per launch",
                  "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
                  "fft_flops_per_launch": dom["flops"] / dom["launches"], "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
                  "peak_source": f"hbm {peak_src} (MEASURED_PEAKS.json); alu = {SM_COUNT} SMs x "
                                 f"{FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz"})
     launches = sum(v["launches"] for v in kstats.values())
-    kernels = {k: {"launches": v["launches"], "ms": v["total_ms"], "share": v["total_ms"] / ms,
+    kernels = {k: {"launches": v["launches"], "ms": v["total_ms"], "share": v["total_ms"] / ms_serial,
                    "GBps": v["bytes"] / max(v["total_ms"], 1e-9) / 1e6,
                    "TFLOPs": v["flops"] / max(v["total_ms"], 1e-9) / 1e9} for k, v in kstats.items()}
 
     cpu = None
     err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and any(x["n"] == 1024 for x in items):
-        it = [x for x in items if x["n"] == 1024][0]
-        i = items.index(it)
-        p = P[i]
-        screen(i, p, it)
+        it = items[par_i]
+        step()
         torch.cuda.synchronize(dev)
-        gmap = {it["seed"]: (inten[1024].cpu().numpy().astype(np.float64), float(m_map[i, 0].item()))}
+        gmap = {it["seed"]: (par_I.cpu().numpy().astype(np.float64), float(m_map[par_i, 0].item()))}
         cpu, err = _cpu_baseline(items, gmap)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": desc, "form": "batched, one CUDA graph per step",
+                "config": {"workload": desc, "form": f"scint_run_batch on {args.lanes} lane(s), one CUDA graph per step",
                            "l2": "inputs larger than L2 (fields 32-134 MB per screen and wavelength)",
                            "parallelism": f"independent batch per GPU x{world}"},
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": units * world / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
                 "gpu_launches": launches * args.steps, "clocks": clk,
+                "serial": {"value": units / (ms_serial * 1e-3), "ms_per_step": ms_serial,
+                           "form": "the same batch on one lane (kernels in sequence), with per-launch events"},
                 "plain": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                           "form": "one screen and one wavelength per call, no graph"},
                 "parity": err, "kernels": kernels}
@@ -372,6 +400,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile"])
+    ap.add_argument("--lanes", type=int, default=4, help="streams the batch is scheduled on (1..8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

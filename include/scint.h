@@ -202,6 +202,73 @@ int scint_curve_modulation(const float* curves, int n_curves, int n_samples,
                            double* out, void* stream);
 
 /*
+ * Batch of independent screens, each run through the whole forward path of the
+ * paper's polychromatic extended-source simulation (Sect. 3.1 synthesis,
+ * Sect. 3.2 propagation with taper, Sect. 3.2.4 passband co-addition,
+ * Sect. 3.2.3 disk smoothing, Sect. 3.3 light curves, Sect. 4 modulation
+ * index), as in the paper's sweeps over R_diff, source radius and spectral
+ * index.  For item i, with its own params:
+ *   phi  = make_screen(params)                                  (if phi != NULL, kept)
+ *   I    = smooth_source(sum_passband(phi, lambdas, weights))   (if intensity != NULL, kept)
+ *   curves   = lightcurve(I, tracks)                             (if n_tracks, n_samples > 0)
+ *   m_map    = modulation_index(I)                               (if m_map != NULL)
+ *   m_curves = curve_modulation(curves)                          (if m_curves != NULL)
+ * Each result equals that of the single-screen calls above.  Fields:
+ *   params      the screen (its lambda_nm only selects the fiducial zone of m_map)
+ *   phi         device, N*N doubles written, or NULL (the screen lives in scratch)
+ *   intensity   device, N*N floats written, or NULL (scratch)
+ *   tracks      host, 4 * n_tracks doubles as in scint_lightcurve (read before
+ *               the call returns)
+ *   curves      device, n_tracks * n_samples floats written; may be NULL only
+ *               when n_tracks or n_samples is 0
+ *   m_map       device, 4 doubles (m, mean, sigma, count) or NULL
+ *   m_curves    device, 3 * n_tracks doubles or NULL; needs curves
+ */
+typedef struct scint_batch_item {
+    scint_params  params;
+    double*       phi;
+    float*        intensity;
+    const double* tracks;
+    int32_t       n_tracks;
+    int32_t       n_samples;
+    float*        curves;
+    double*       m_map;
+    double*       m_curves;
+} scint_batch_item;
+
+#define SCINT_MAX_LANES 8
+
+/*
+ * Workspace for scint_run_batch with n_lanes lanes when each screen's passband
+ * of n_lambda wavelengths runs in one group: n_lanes equal slices, each the
+ * forward workspace of the largest screen plus, when any item leaves phi or
+ * intensity NULL, scratch maps of that size.  0 on invalid arguments.
+ */
+size_t scint_batch_workspace_bytes(const scint_batch_item* items, int n_items, int n_lambda, int n_lanes);
+
+/*
+ * Run a batch (see scint_batch_item).  The library schedules the items on
+ * n_lanes internal CUDA streams (1..SCINT_MAX_LANES; <= 0 selects 2), the
+ * costliest first, each to the lane with the least work queued
+ * (longest-processing-time rule with cost N^2 log2 N (n_lambda + 8)), so that
+ * kernels of small screens fill the tail waves of large ones.  The lanes start
+ * after the work already queued on `stream` and `stream` waits for all of
+ * them, so the call is ordered on `stream` like every other entry point and can
+ * be captured into a CUDA graph (the lanes join the capture).
+ *   items        host array of n_items records (n_items >= 0).
+ *   lambdas_nm   host, n_lambda wavelengths shared by every item; weights host
+ *                or NULL (1/n_lambda), as in scint_sum_passband.
+ *   workspace    device, >= n_lanes * (the minimum slice for one wavelength
+ *                group); a slice smaller than the one-group size makes the
+ *                passbands run in groups.  NULL: the per-device pool.
+ * Every item is checked on the host before anything is launched.  Concurrent
+ * calls from several host threads are serialised while they enqueue.
+ */
+int scint_run_batch(const scint_batch_item* items, int n_items,
+                    const double* lambdas_nm, const double* weights, int n_lambda,
+                    int n_lanes, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Gradient of a light-curve misfit with respect to the phase screen (reverse
  * mode through Sect. 3.2-3.3; the paper states no gradient, this is the
  * adjoint of the forward path of this library).  The forward map is

@@ -5,6 +5,10 @@ C ABI of include/scint.h; this package only marshals arguments to it.
 """
 from ._lib import (  # noqa: F401
     MAX_LAMBDA,
+    MAX_LANES,
+    BatchItem,
+    batch_items,
+    batch_workspace_bytes,
     ScintError,
     ScintParams,
     curve_modulation,
@@ -22,6 +26,7 @@ from ._lib import (  # noqa: F401
     propagate,
     rdiff_gradient,
     release,
+    run_batch,
     smooth_source,
     sum_passband,
     workspace_bytes,

@@ -65,6 +65,24 @@ def params(n: int, pixel_km: float, r_diff_km: float, beta: float = 11.0 / 3.0, 
                        seed=seed, screen_id=screen_id, reserved1=0)
 
 
+class BatchItem(ctypes.Structure):
+    """Mirror of struct scint_batch_item (include/scint.h)."""
+    _fields_ = [
+        ("params", ScintParams),
+        ("phi", ctypes.c_void_p),
+        ("intensity", ctypes.c_void_p),
+        ("tracks", ctypes.c_void_p),
+        ("n_tracks", ctypes.c_int32),
+        ("n_samples", ctypes.c_int32),
+        ("curves", ctypes.c_void_p),
+        ("m_map", ctypes.c_void_p),
+        ("m_curves", ctypes.c_void_p),
+    ]
+
+
+MAX_LANES = 8
+
+
 class KernelStat(ctypes.Structure):
     """Mirror of struct scint_kernel_stat (include/scint.h)."""
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
@@ -105,6 +123,8 @@ def lib() -> ctypes.CDLL:
         "scint_fft_lines64": ([_i, _i, _vp, _i, _vp], _i),
         "scint_lightcurve_adjoint": ([_P, _vp, _vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, _sz, _vp], _i),
         "scint_rdiff_gradient": ([_P, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+        "scint_batch_workspace_bytes": ([ctypes.POINTER(BatchItem), _i, _i, _i], _sz),
+        "scint_run_batch": ([ctypes.POINTER(BatchItem), _i, _vp, _vp, _i, _i, _vp, _sz, _vp], _i),
         "scint_profile_enable": ([_i], _i),
         "scint_profile_read": ([ctypes.POINTER(KernelStat), _i, ctypes.POINTER(_i)], _i),
     }
@@ -249,6 +269,59 @@ def rdiff_gradient(p: ScintParams, phi: torch.Tensor, grad_phi: torch.Tensor, wo
                                       _dev(grad_phi, torch.float64, p.n * p.n, "grad_phi"),
                                       _dev(out, torch.float64, 1, "out"), wp, wb, _stream(stream)))
     return out
+
+
+def _opt_dev(t: Optional[torch.Tensor], dtype, numel: int, name: str):
+    return None if t is None else _dev(t, dtype, numel, name)
+
+
+def batch_items(entries) -> "ctypes.Array":
+    """ctypes array of scint_batch_item from dicts with keys params and, optionally,
+    phi, intensity, tracks (n x 4 host array), n_samples, curves, m_map, m_curves
+    (device tensors or None).  The track arrays are kept alive on the result."""
+    arr = (BatchItem * len(entries))()
+    keep = []
+    for i, e in enumerate(entries):
+        p = e["params"]
+        nn = p.n * p.n
+        tr = np.ascontiguousarray(e.get("tracks", np.zeros((0, 4))), dtype=np.float64).reshape(-1, 4)
+        keep.append(tr)
+        ns = int(e.get("n_samples", 0))
+        arr[i].params = p
+        arr[i].phi = _opt_dev(e.get("phi"), torch.float64, nn, "phi")
+        arr[i].intensity = _opt_dev(e.get("intensity"), torch.float32, nn, "intensity")
+        arr[i].tracks = tr.ctypes.data if tr.shape[0] else None
+        arr[i].n_tracks = tr.shape[0]
+        arr[i].n_samples = ns
+        arr[i].curves = _opt_dev(e.get("curves"), torch.float32, tr.shape[0] * ns, "curves")
+        arr[i].m_map = _opt_dev(e.get("m_map"), torch.float64, 4, "m_map")
+        arr[i].m_curves = _opt_dev(e.get("m_curves"), torch.float64, 3 * tr.shape[0], "m_curves")
+    arr._keep = keep
+    return arr
+
+
+def batch_workspace_bytes(items, n_lambda: int, n_lanes: int = 0) -> int:
+    arr = items if isinstance(items, ctypes.Array) else batch_items(items)
+    return int(lib().scint_batch_workspace_bytes(arr, len(arr), n_lambda, n_lanes))
+
+
+def run_batch(items, lambdas_nm, weights=None, n_lanes: int = 0, workspace: Optional[torch.Tensor] = None,
+              stream=None):
+    """Forward path of every item (see scint_run_batch); outputs are written into the
+    items' tensors.  `items` is a list of dicts (batch_items) or its ctypes array."""
+    arr = items if isinstance(items, ctypes.Array) else batch_items(items)
+    lam = np.ascontiguousarray(lambdas_nm, dtype=np.float64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    if workspace is None:
+        wp, wb = None, 0
+    else:
+        if not (workspace.is_cuda and workspace.is_contiguous()):
+            raise ValueError("workspace must be a contiguous CUDA tensor")
+        wp, wb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+    _check(lib().scint_run_batch(arr, len(arr), lam.ctypes.data_as(ctypes.c_void_p),
+                                 None if w is None else w.ctypes.data_as(ctypes.c_void_p), len(lam),
+                                 int(n_lanes), wp, wb, _stream(stream)))
+    return arr
 
 
 def noise_words(p: ScintParams, stream=None, device="cuda") -> torch.Tensor:

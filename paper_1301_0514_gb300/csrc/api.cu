@@ -1,6 +1,7 @@
 // C-ABI entry points: host-side parameter checks, derived physical scalars,
 // workspace carving and kernel sequencing.  Declarations and the contract of
 // every function are in include/scint.h and include/scint_testing.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -11,6 +12,7 @@
 
 #include "../../include/scint.h"
 #include "../../include/scint_testing.h"
+#include "api_internal.h"
 #include "kernels.cuh"
 
 namespace scint {
@@ -236,6 +238,20 @@ void prof_clear_locked() {
     g_prof.recs.clear();
 }
 
+int check_passband(const scint_params* p, const double* lambdas, const double* weights, int n_lambda) {
+    const int rc = check_params(p);
+    if (rc) return rc;
+    if (!lambdas || n_lambda < 1 || n_lambda > SCINT_MAX_LAMBDA)
+        return fail(SCINT_EINVAL, "n_lambda=%d must be in [1, %d]", n_lambda, SCINT_MAX_LAMBDA);
+    for (int i = 0; i < n_lambda; ++i) {
+        if (!(lambdas[i] > 0) || !std::isfinite(lambdas[i])) return fail(SCINT_EINVAL, "lambda %d must be > 0", i);
+        if (weights && !std::isfinite(weights[i])) return fail(SCINT_EINVAL, "weight %d is not finite", i);
+        if (taper_margin(p, lambdas[i]) > 0.5 * screen_len(p))
+            return fail(SCINT_EINVAL, "taper margin exceeds half the screen");
+    }
+    return SCINT_OK;
+}
+
 // Propagate one wavelength group [l0, l0 + g) into the intensity map.
 int run_group(const scint_params* p, const double* phi, const double* lam, const double* wts,
               int l0, int g, float* intensity, int accumulate, Carver& c, const float2* tw,
@@ -280,21 +296,11 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
 int passband_impl(const scint_params* p, const double* phi, const double* lambdas, const double* weights,
                   int n_lambda, float* intensity, int accumulate, void* ws, size_t ws_bytes,
                   cudaStream_t s) {
-    int rc = check_params(p);
+    int rc = check_passband(p, lambdas, weights, n_lambda);
     if (rc) return rc;
     if (!phi || !intensity) return fail(SCINT_EINVAL, "phi and intensity must be device pointers");
-    if (!lambdas || n_lambda < 1 || n_lambda > SCINT_MAX_LAMBDA)
-        return fail(SCINT_EINVAL, "n_lambda=%d must be in [1, %d]", n_lambda, SCINT_MAX_LAMBDA);
     std::vector<double> w(n_lambda, 1.0 / n_lambda);
-    for (int i = 0; i < n_lambda; ++i) {
-        if (!(lambdas[i] > 0) || !std::isfinite(lambdas[i])) return fail(SCINT_EINVAL, "lambda %d must be > 0", i);
-        if (weights) {
-            if (!std::isfinite(weights[i])) return fail(SCINT_EINVAL, "weight %d is not finite", i);
-            w[i] = weights[i];
-        }
-        if (taper_margin(p, lambdas[i]) > 0.5 * screen_len(p))
-            return fail(SCINT_EINVAL, "taper margin exceeds half the screen");
-    }
+    if (weights) w.assign(weights, weights + n_lambda);
     const int n = p->n;
     // group size: all wavelengths if the workspace allows, else the largest that fits
     int g = n_lambda;
@@ -333,6 +339,22 @@ SynthArgs synth_args(const scint_params* p) {
 }
 
 }  // namespace
+
+// ---- helpers shared with the batch executor (csrc/batch.cu) ----------------------
+namespace scint {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+int clear_error() { return ok(); }
+const char* last_error() { return g_error.c_str(); }
+int validate_params(const scint_params* p) { return check_params(p); }
+int validate_passband(const scint_params* p, const double* lambdas, const double* weights, int n_lambda) {
+    return check_passband(p, lambdas, weights, n_lambda);
+}
+size_t aligned_bytes(size_t b) { return up(b); }
+size_t forward_workspace_bytes(int n, int g) {
+    return std::max(std::max(ws_synth(n), ws_prop(n, g)), std::max(ws_smooth(n), ws_moments()));
+}
+int pool_workspace(size_t bytes, cudaStream_t s, void** out) { return pool_get(bytes, s, out); }
+}  // namespace scint
 
 namespace {
 
@@ -701,6 +723,7 @@ int scint_profile_read(scint_kernel_stat* stats, int max_stats, int* n_stats) {
 }
 
 void scint_release(void) {
+    scint::release_lanes();
     std::lock_guard<std::mutex> lk(g_pool.mu);
     int cur = 0;
     cudaGetDevice(&cur);

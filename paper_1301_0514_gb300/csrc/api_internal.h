@@ -1,0 +1,35 @@
+// Host-side helpers of csrc/api.cu used by the other host translation units
+// (the batch executor): error reporting, parameter checks, workspace sizing and
+// the per-device workspace pool.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "../../include/scint.h"
+
+namespace scint {
+
+// Set the calling thread's last-error message; returns code.
+int set_error(int code, const char* msg);
+// Clear the calling thread's last-error message; returns SCINT_OK.
+int clear_error();
+const char* last_error();
+
+// Host checks of one screen's parameters, and of a passband for it (the same
+// checks, with the same messages, as the single-screen entry points).
+int validate_params(const scint_params* p);
+int validate_passband(const scint_params* p, const double* lambdas, const double* weights, int n_lambda);
+
+// Bytes rounded up to the library's workspace alignment (256).
+size_t aligned_bytes(size_t b);
+// Workspace of the forward path of one N x N screen (synthesis, a passband
+// group of g wavelengths, smoothing, moments): the maximum over its calls.
+size_t forward_workspace_bytes(int n, int g);
+// The per-device pool: at least `bytes`, grown outside stream capture only.
+int pool_workspace(size_t bytes, cudaStream_t s, void** out);
+// Destroy the batch executor's streams and events (csrc/batch.cu).
+void release_lanes();
+
+}  // namespace scint

@@ -1,6 +1,8 @@
 // Runtime grid size -> compile-time template argument.
 #pragma once
 
+#include <map>
+#include <mutex>
 #include <type_traits>
 #include <utility>
 
@@ -26,11 +28,23 @@ cudaError_t dispatch_n(int n, F&& f) {
     }
 }
 
-// Opt a kernel into more than 48 KB of dynamic shared memory, once per process.
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per kernel
+// and device (later calls, e.g. inside a stream capture, make no CUDA call).
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_pair(dev, reinterpret_cast<const void*>(kernel));
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done[key] = bytes;
+    return e;
 }
 
 // Launch k with clusters of cs blocks along x (cs == 1: ordinary launch).

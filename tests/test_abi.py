@@ -111,3 +111,62 @@ def test_workloads_are_seeded_and_shaped():
     assert all(a["seed"] == b["seed"] and a["r_diff_km"] == b["r_diff_km"] for a, b in zip(c3, again))
     c2 = W.config2()
     assert [it["r_diff_km"] for it in c2] == [30.0, 100.0, 300.0] and c2[0]["tracks"].shape == (64, 4)
+
+
+def _c_layout(struct, fields):
+    """offsetof/sizeof of a struct of include/scint.h, compiled with the host C compiler."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    body = "".join(f'printf("%zu ", offsetof({struct}, {f}));' for f in fields)
+    src = f'#include <stdio.h>\n#include <stddef.h>\n#include "scint.h"\nint main(void){{{body}printf("%zu", sizeof({struct}));return 0;}}\n'
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "p.c"), os.path.join(d, "p")
+        open(c, "w").write(src)
+        subprocess.run([cc, "-I", INCLUDE, c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return [int(x) for x in out]
+
+
+def test_struct_layouts_match_the_c_compiler():
+    for struct, cls in (("scint_params", _lib.ScintParams), ("scint_batch_item", _lib.BatchItem),
+                        ("scint_kernel_stat", _lib.KernelStat)):
+        fields = [f for f, _ in cls._fields_]
+        got = _c_layout(struct, fields)
+        assert got[:-1] == [getattr(cls, f).offset for f in fields], struct
+        assert got[-1] == ctypes.sizeof(cls), struct
+
+
+def _batch_entry(n=256, **kw):
+    return dict(params=S.params(n=n, pixel_km=20.0, r_diff_km=100.0, **kw))
+
+
+def test_batch_rejected_on_host(lib):
+    good = _batch_entry()
+    lam = [500.0, 600.0]
+    cases = [
+        ([good, _batch_entry(n=100)], {}, "item 1: n=100"),
+        ([good], dict(n_lanes=S.MAX_LANES + 1), "n_lanes"),
+        ([dict(good, tracks=np.array([[0.0, 1.0, float("nan"), 1.0]]), n_samples=4)], {}, "item 0"),
+        ([dict(good, tracks=np.array([[0.0, 1.0, 0.5, 1.0]]), n_samples=4)], {}, "tracks and curves"),
+    ]
+    for items, kw, msg in cases:
+        with pytest.raises(S.ScintError) as e:
+            S.run_batch(items, lam, stream=0, **kw)
+        assert e.value.code == 1 and msg in str(e.value), (msg, str(e.value))
+    with pytest.raises(S.ScintError):
+        S.run_batch([good], [], stream=0)
+
+
+def test_batch_workspace_bytes(lib):
+    items = [_batch_entry(n=256), _batch_entry(n=1024), _batch_entry(n=512)]
+    one = S.batch_workspace_bytes(items, 4, 1)
+    assert one > 0
+    # lanes split the workspace into equal slices sized for the largest screen
+    assert S.batch_workspace_bytes(items, 4, 3) == 3 * one
+    assert S.batch_workspace_bytes(items, 4, 5) == 3 * one       # never more lanes than items
+    assert S.batch_workspace_bytes(items, 8, 1) > one            # a larger wavelength group
+    assert S.batch_workspace_bytes([_batch_entry(n=100)], 4, 1) == 0
