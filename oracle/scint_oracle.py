@@ -210,6 +210,86 @@ def structure_function_discrete(n: int, pixel_km: float, r_diff_km: float, beta:
 
 
 # ---------------------------------------------------------------------------
+# Screen check of Sect. 3.1.1: spectrum and structure function recomputed from
+# the generated F_phi (Eq. crec), and R_diff^rec from D_rec(R_diff^rec) = 1.
+# ---------------------------------------------------------------------------
+def annulus_index(mx, my):
+    """Annulus of the integer wave vector (mx, my): the nearest integer to |m|.
+
+    The paper averages |F|^2 over the circle of radius q without a bin width;
+    here (Reading R15) annulus j collects the FFT bins with j - 1/2 <= |m| < j + 1/2,
+    i.e. width dq = 1/L centred on q_j = j/L.  |m| is never a half-integer for
+    integer mx, my, so the assignment is unambiguous.
+    """
+    mx = np.asarray(mx, dtype=np.int64)
+    my = np.asarray(my, dtype=np.int64)
+    return np.floor(np.sqrt((mx * mx + my * my).astype(np.float64)) + 0.5).astype(np.int64)
+
+
+def max_annulus(n: int) -> int:
+    """Largest annulus index of an n x n grid (its corner, |m| = sqrt(2) n/2)."""
+    return int(annulus_index(n // 2, n // 2))
+
+
+def spectrum_rec(p: ScreenParams, j_max=None):
+    """S_rec(q_j) = <|F_phi|^2>_{annulus j} / (L_x L_y) for j = 0..j_max (Sect. 3.1.1),
+    from the generated F_phi of noise_spectrum, and the number of bins per annulus.
+
+    Only spectral rows with |m_y| <= j_max can reach annuli j <= j_max, so a
+    small j_max touches few rows.  Annuli without bins get S_rec = 0.
+    """
+    n = p.n
+    L = n * p.pixel_km
+    top = max_annulus(n)
+    j_max = top if j_max is None else min(int(j_max), top)
+    m = np.rint(np.fft.fftfreq(n) * n).astype(np.int64)          # signed integer frequencies
+    rows = np.nonzero(np.abs(m) <= j_max)[0]
+    F = noise_spectrum(p, rows)
+    j = annulus_index(m[None, :], m[rows][:, None])
+    keep = j <= j_max
+    power = np.abs(F[keep]) ** 2
+    sums = np.bincount(j[keep], weights=power, minlength=j_max + 1)
+    counts = np.bincount(j[keep], minlength=j_max + 1)
+    s = np.zeros(j_max + 1)
+    nz = counts > 0
+    s[nz] = sums[nz] / counts[nz] / (L * L)
+    return s, counts
+
+
+def structure_function_rec(s_rec, n: int, pixel_km: float, r_km):
+    """D_rec(r) = 2 (xi_rec(0) - xi_rec(r)) with Eq. crec,
+        xi_rec(r) = int_{q_min}^{q_max} 2 pi q S_rec(q) J0(2 pi q r) dq,
+    evaluated on the annuli: q_j = j dq, dq = 1/L, j = 1..J with q_min = 1/L and
+    q_max = 1/(2 Delta_1), the paper's 1D limits (J = n/2, or fewer if s_rec is
+    shorter), each annulus weighted by its width dq (midpoint rule, Reading R15).
+    """
+    s_rec = np.asarray(s_rec, dtype=np.float64)
+    L = n * pixel_km
+    dq = 1.0 / L
+    J = min(len(s_rec) - 1, n // 2)
+    q = np.arange(1, J + 1) * dq
+    S = s_rec[1:J + 1]
+    r = np.atleast_1d(np.asarray(r_km, dtype=np.float64))
+    arg = 2.0 * np.pi * q[None, :] * r[:, None]
+    return 2.0 * (2.0 * np.pi * q[None, :] * S[None, :] * (1.0 - special.j0(arg))).sum(axis=1) * dq
+
+
+def rdiff_rec(s_rec, n: int, pixel_km: float, iterations: int = 64) -> float:
+    """R_diff^rec: the root of D_rec(R) = 1 on (0, L/2], by bisection from that
+    bracket (nan when D_rec(L/2) < 1, i.e. the screen never decorrelates by 1 rad^2)."""
+    lo, hi = 0.0, 0.5 * n * pixel_km
+    if structure_function_rec(s_rec, n, pixel_km, hi)[0] < 1.0:
+        return float("nan")
+    for _ in range(iterations):
+        mid = 0.5 * (lo + hi)
+        if structure_function_rec(s_rec, n, pixel_km, mid)[0] < 1.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+# ---------------------------------------------------------------------------
 # Illumination pattern (Sect. 2 Eq. hxy, Sect. 3.2)
 # ---------------------------------------------------------------------------
 def fresnel_radius_km(lambda_nm: float, z_pc: float) -> float:
