@@ -393,17 +393,140 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_screen_check(args):
+    """Sect. 3.1.1 screen check at the paper's size: S_rec over all annuli of one
+    N x N realisation, D_rec at 256 lags and R_diff^rec.  Metric: spectral bins/s."""
+    import torch
+    import paper_1301_0514_gb300 as S
+    from paper_1301_0514_gb300 import workloads as W
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    n, pix, rd = args.check_n, 28.85, 500.0
+    p = S.params(n=n, pixel_km=pix, r_diff_km=rd, seed=W.SEED_BASE + 9100 + 100000 * rank)
+    n_bins = S.max_annulus(n) + 1
+    s = torch.empty(n_bins, dtype=torch.float64, device=dev)
+    c = torch.empty(n_bins, dtype=torch.int64, device=dev)
+    lags = torch.linspace(10.0, 0.25 * n * pix, 256, dtype=torch.float64, device=dev)
+    d = torch.empty(256, dtype=torch.float64, device=dev)
+    root = torch.empty(1, dtype=torch.float64, device=dev)
+    ws = torch.empty(4096, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        S.spectrum_rec(p, out=(s, c))
+        S.structure_function_rec(p, s, lags, workspace=ws, out=(d, root))
+
+    step()
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    units = float(n) * n
+    value = units * world / (ms * 1e-3)
+
+    # per-kernel times from one profiled eager step
+    S.profile_enable(True)
+    step()
+    torch.cuda.synchronize(dev)
+    kstats = S.profile_read()
+    S.profile_enable(False)
+    launches = sum(v["launches"] for v in kstats.values())
+    dom_name, dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
+    _, sm_max_mhz, _ = _peaks()
+    # Philox4x32-10 bound: 10 rounds x 2 32x32->64-bit multiplies per bin, each a
+    # multiply-add pair on the integer pipe (64 lanes per SM per clock)
+    imad_per_bin = 40.0
+    peak = SM_COUNT * 64 * sm_max_mhz * 1e6 / imad_per_bin
+    achieved = units / (kstats["radial_spectrum"]["total_ms"] * 1e-3)
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gbins/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "radial_spectrum",
+            "peak_source": f"Philox4x32-10 integer multiplies: {SM_COUNT} SMs x 64 lanes x {sm_max_mhz:.0f} MHz "
+                           f"/ {imad_per_bin:.0f} per bin",
+            "timing": "one profiled eager step, CUDA events per launch"}
+
+    # end to end: the same calls with the results read back to pinned host memory
+    hs = torch.empty(n_bins, dtype=torch.float64, pin_memory=True)
+    hd = torch.empty(256 + 1, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        step()
+        hs.copy_(s, non_blocking=True)
+        hd[:256].copy_(d, non_blocking=True)
+        hd[256:].copy_(root, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / 3
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        po = O.ScreenParams(n=n, pixel_km=pix, r_diff_km=rd, seed=p.seed)
+        j_max = 1500          # about 4e7 of the 2e8 bins: several seconds of oracle time
+        t0 = time.perf_counter()
+        s_o, _ = O.spectrum_rec(po, j_max=j_max)
+        dt = time.perf_counter() - t0
+        rows = 2 * j_max + 1
+        cpu = {"value": rows * n / dt, "unit": "bins/s", "cores": 1, "kind": "oracle",
+               "sample": f"annulus sums over the {rows} spectral rows |m_y| <= {j_max} of the {n}^2 grid, {dt:.1f} s"}
+        err = float(np.max(np.abs(s[:j_max + 1].cpu().numpy() - s_o) / np.maximum(np.abs(s_o), 1e-300)))
+    if rank == 0:
+        line = {"metric": f"screen-check spectral bins/s (Sect. 3.1.1, N={n})", "value": value, "unit": "bins/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+                "data": "synthetic",
+                "config": {"workload": f"screen check: one {n}^2 realisation, 28.85 km pixels, R_diff 500 km, "
+                                       f"{n_bins} annuli, D_rec at 256 lags, R_diff^rec by 64 bisection steps",
+                           "l2": "no input: the noise is regenerated per bin"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": units * world / (e2e_ms * 1e-3), "unit": "bins/s", "h2d_bytes_per_step": 96,
+                        "d2h_bytes_per_step": int(8 * (n_bins + 257)), "ms_per_step": e2e_ms},
+                "gpu_launches": launches * args.steps, "clocks": clk,
+                "r_diff_rec_km": float(root.item()),
+                "parity": None if cpu is None else {"max_rel_err_low_annuli": err},
+                "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in kstats.items()}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "screen_check"])
+    ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
     ap.add_argument("--lanes", type=int, default=4, help="streams the batch is scheduled on (1..8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.workload == "screen_check" and args.impl != "reference":
+        run_screen_check(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -12,7 +12,8 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- *  - Grids are square, N x N, N a power of two; arrays are row-major with the
+ *  - Grids are square, N x N, N a power of two (the screen check of Sect.
+ *    3.1.1 takes any even N); arrays are row-major with the
  *    row index y: element (y, x) sits at [y * N + x].  Pixel (ix, iy) has its
  *    centre at ((ix + 1/2) Delta, (iy + 1/2) Delta) on the screen.
  *  - Lengths are in km, wavelengths in nm, distances in pc.
@@ -54,6 +55,7 @@ extern "C" {
 #define SCINT_MAX_LAMBDA   128 /* wavelengths per passband call */
 #define SCINT_MIN_N        16
 #define SCINT_MAX_N        16384
+#define SCINT_MAX_CHECK_N  32768 /* grid size limit of the screen check (any even N) */
 
 /*
  * Parameters of one screen and observation.
@@ -110,6 +112,47 @@ size_t scint_workspace_bytes(const scint_params* p, int n_lambda);
  */
 int scint_make_screen(const scint_params* p, double* phi,
                       void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Screen check of Sect. 3.1.1, part 1: the spectral density recomputed from the
+ * generated F_phi (the same F as scint_make_screen draws),
+ *   S_rec(q_j) = sum_{annulus j} |F_k|^2 / (count_j L_x L_y),  q_j = j / L,
+ * where annulus j holds the FFT bins whose integer wave vector m (k = m / L)
+ * has j - 1/2 <= |m| < j + 1/2 (the paper averages over the circle |k| = q
+ * without naming a width; annuli of width 1/L are this library's reading).
+ * The noise is regenerated bin by bin, never stored.  p->n may be any even
+ * number in [SCINT_MIN_N, SCINT_MAX_CHECK_N] (the paper's check uses N ~ 14000);
+ * only n, pixel_km, r_diff_km, beta, seed and screen_id are used.
+ *   s_rec    device, n_bins doubles written: S_rec(q_j) for j < n_bins (0 for
+ *            annuli without bins: j = 0 holds only the DC bin, where F = 0, and
+ *            j > sqrt(2) N/2 lies outside the grid).
+ *   counts   device, n_bins uint64 written: bins per annulus.
+ * The annulus sums are 64-bit fixed point with a per-annulus scale (each bin
+ * truncated to 2^-36 of the annulus' expected bin power), so they are exact
+ * and the result is the same bit for bit on every run.
+ */
+int scint_spectrum_rec(const scint_params* p, double* s_rec, uint64_t* counts, int n_bins, void* stream);
+
+/*
+ * Screen check of Sect. 3.1.1, part 2 (Eq. crec): the structure function
+ *   D_rec(r) = 2 (xi_rec(0) - xi_rec(r))
+ *            = 2 sum_{j=1}^{J} 2 pi q_j S_rec(q_j) (1 - J0(2 pi q_j r)) dq,
+ * dq = 1/L, J = min(n_bins - 1, N/2): the integral of Eq. crec between the
+ * paper's q_min = 1/L and q_max = 1/(2 Delta_1) by the midpoint rule on the
+ * annuli, with J0 from the CUDA math library; and R_diff^rec, the root of
+ * D_rec(R) = 1, by 64 bisection steps on (0, L/2] (NaN if D_rec(L/2) < 1).
+ * s_rec may be scint_spectrum_rec's output or any spectrum sampled at q_j
+ * (e.g. the theoretical S_phi, as in the paper's comparison).
+ *   s_rec   device, n_bins >= 2 doubles, read.
+ *   r_km    device, n_r lags (km), read; d_rec device, n_r doubles written
+ *           (both may be NULL when n_r == 0).
+ *   r_rec   device, 1 double written, or NULL to skip the root.
+ * Each D_rec value is summed in a fixed order (reproducible bit for bit).
+ * Needs workspace (< 1 KB) when r_rec != NULL.
+ */
+int scint_structure_function_rec(const scint_params* p, const double* s_rec, int n_bins,
+                                 const double* r_km, int n_r, double* d_rec, double* r_rec,
+                                 void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * Monochromatic point-source intensity at p->lambda_nm (Eq. hxy, Sect. 3.2.1):

@@ -4,6 +4,7 @@ The computation runs in libscint.so (hand-written CUDA for sm_103a) behind the
 C ABI of include/scint.h; this package only marshals arguments to it.
 """
 from ._lib import (  # noqa: F401
+    MAX_CHECK_N,
     MAX_LAMBDA,
     MAX_LANES,
     BatchItem,
@@ -17,6 +18,7 @@ from ._lib import (  # noqa: F401
     lightcurve,
     lightcurve_adjoint,
     make_screen,
+    max_annulus,
     modulation_index,
     noise_spectrum,
     noise_words,
@@ -28,6 +30,8 @@ from ._lib import (  # noqa: F401
     release,
     run_batch,
     smooth_source,
+    spectrum_rec,
+    structure_function_rec,
     sum_passband,
     workspace_bytes,
 )

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libscint.so")
 SCINT_OK = 0
 ERRORS = {1: "SCINT_EINVAL", 2: "SCINT_ENOMEM", 3: "SCINT_ECUDA", 4: "SCINT_ETIMEOUT", 5: "SCINT_EUNSUPPORTED"}
 MAX_LAMBDA = 128
+MAX_CHECK_N = 32768
 
 
 class ScintError(RuntimeError):
@@ -125,6 +126,8 @@ def lib() -> ctypes.CDLL:
         "scint_rdiff_gradient": ([_P, _vp, _vp, _vp, _vp, _sz, _vp], _i),
         "scint_batch_workspace_bytes": ([ctypes.POINTER(BatchItem), _i, _i, _i], _sz),
         "scint_run_batch": ([ctypes.POINTER(BatchItem), _i, _vp, _vp, _i, _i, _vp, _sz, _vp], _i),
+        "scint_spectrum_rec": ([_P, _vp, _vp, _i, _vp], _i),
+        "scint_structure_function_rec": ([_P, _vp, _i, _vp, _i, _vp, _vp, _vp, _sz, _vp], _i),
         "scint_profile_enable": ([_i], _i),
         "scint_profile_read": ([ctypes.POINTER(KernelStat), _i, ctypes.POINTER(_i)], _i),
     }
@@ -322,6 +325,54 @@ def run_batch(items, lambdas_nm, weights=None, n_lanes: int = 0, workspace: Opti
                                  None if w is None else w.ctypes.data_as(ctypes.c_void_p), len(lam),
                                  int(n_lanes), wp, wb, _stream(stream)))
     return arr
+
+
+def max_annulus(n: int) -> int:
+    """Largest annulus index of an n x n grid (its corner, |m| = sqrt(2) n/2)."""
+    return int(np.floor(np.sqrt(2.0 * (n // 2) ** 2) + 0.5))
+
+
+def spectrum_rec(p: ScintParams, n_bins: Optional[int] = None, out=None, stream=None, device="cuda"):
+    """(S_rec, counts) over annuli j = 0..n_bins-1 (Sect. 3.1.1); all annuli by default.
+    `out` = (float64, int64) device tensors of n_bins elements to write into."""
+    if out is not None:
+        s, c = out
+        n_bins = s.numel()
+        _dev(s, torch.float64, n_bins, "s_rec"), _dev(c, torch.int64, n_bins, "counts")
+    else:
+        n_bins = max_annulus(p.n) + 1 if n_bins is None else int(n_bins)
+        s = torch.empty(n_bins, dtype=torch.float64, device=device)
+        c = torch.empty(n_bins, dtype=torch.int64, device=device)
+    _check(lib().scint_spectrum_rec(ctypes.byref(p), ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                    n_bins, _stream(stream)))
+    return s, c
+
+
+def structure_function_rec(p: ScintParams, s_rec: torch.Tensor, r_km=None, root: bool = True, workspace=None,
+                           out=None, stream=None):
+    """(D_rec at r_km, R_diff^rec) by Eq. crec from a spectrum on the annuli (Sect. 3.1.1).
+    r_km: lags (host array or float64 device tensor); `out` = (d, root) device tensors."""
+    dev = s_rec.device
+    if isinstance(r_km, torch.Tensor):
+        r = r_km
+    else:
+        r = torch.as_tensor(np.zeros(0) if r_km is None else np.asarray(r_km, dtype=np.float64), device=dev)
+    r = r.to(torch.float64).contiguous()
+    if out is not None:
+        d, out = out
+    else:
+        d = torch.empty(r.numel(), dtype=torch.float64, device=dev)
+        out = torch.empty(1, dtype=torch.float64, device=dev) if root else None
+    if workspace is None:
+        wp, wb = None, 0
+    else:
+        wp, wb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+    _check(lib().scint_structure_function_rec(
+        ctypes.byref(p), _dev(s_rec, torch.float64, s_rec.numel(), "s_rec"), s_rec.numel(),
+        ctypes.c_void_p(r.data_ptr()) if r.numel() else None, r.numel(),
+        ctypes.c_void_p(d.data_ptr()) if r.numel() else None,
+        None if out is None else ctypes.c_void_p(out.data_ptr()), wp, wb, _stream(stream)))
+    return d, out
 
 
 def noise_words(p: ScintParams, stream=None, device="cuda") -> torch.Tensor:

@@ -91,6 +91,7 @@ double f_beta(double beta) {
 
 // ---- workspace ------------------------------------------------------------------
 constexpr size_t kAlign = 256;
+constexpr int kRdiffRecIterations = 64;   // bisection steps for R_diff^rec (resolution L 2^-65)
 size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
 size_t ws_synth(int n) { return up((size_t)n * 16) + up((size_t)(n / 2 + 1) * n * 16); }
@@ -176,12 +177,12 @@ int resolve_ws(void* ws, size_t bytes, size_t need, cudaStream_t s, Carver* c) {
 enum KClass {
     K_TWIDDLES, K_SYNTH_ROWS, K_SYNTH_COLS, K_PROP_TABLES, K_PROP_ROWS, K_PROP_COLS,
     K_SMOOTH_FWD, K_SMOOTH_ROWS, K_SMOOTH_INV, K_LIGHTCURVE, K_MOMENTS,
-    K_LC_ADJ, K_ADJ_COLS, K_ADJ_ROWS, K_DOT, K_COUNT
+    K_LC_ADJ, K_ADJ_COLS, K_ADJ_ROWS, K_DOT, K_RADIAL, K_CREC, K_COUNT
 };
 const char* const kClassName[K_COUNT] = {
     "twiddles", "synth_rows", "synth_cols", "prop_tables", "prop_rows", "prop_cols",
     "smooth_fwd_cols", "smooth_rows", "smooth_inv_cols", "lightcurve", "moments",
-    "lightcurve_adjoint", "adj_cols", "adj_rows", "dot"};
+    "lightcurve_adjoint", "adj_cols", "adj_rows", "dot", "radial_spectrum", "structure_rec"};
 
 struct ProfRec {
     int cls;
@@ -689,6 +690,74 @@ int scint_rdiff_gradient(const scint_params* p, const double* phi, const double*
     // phi ~ R_diff^((2 - beta)/2) at a fixed seed
     const double scale = (2.0 - p->beta) / (2.0 * p->r_diff_km);
     SCINT_LAUNCH(K_DOT, 16.0 * (double)nn, 0.0, s, launch_scaled_dot(phi, grad_phi, nn, scale, partial, out, s));
+    return ok();
+}
+
+// ---- screen check of Sect. 3.1.1 ------------------------------------------------
+namespace {
+int check_screen_check_params(const scint_params* p) {
+    if (!p) return fail(SCINT_EINVAL, "params is NULL");
+    if (p->n < SCINT_MIN_N || p->n > SCINT_MAX_CHECK_N || (p->n & 1))
+        return fail(SCINT_EINVAL, "n=%d must be even in [%d, %d]", p->n, SCINT_MIN_N, SCINT_MAX_CHECK_N);
+    if (p->reserved0 || p->reserved1) return fail(SCINT_EINVAL, "reserved fields must be 0");
+    if (!(p->pixel_km > 0) || !std::isfinite(p->pixel_km)) return fail(SCINT_EINVAL, "pixel_km must be > 0");
+    if (!(p->r_diff_km > 0) || !std::isfinite(p->r_diff_km)) return fail(SCINT_EINVAL, "r_diff_km must be > 0");
+    if (!(p->beta > 2.0 && p->beta < 4.0)) return fail(SCINT_EINVAL, "beta=%g must be in (2, 4)", p->beta);
+    return SCINT_OK;
+}
+int max_annulus(int n) { return (int)std::floor(std::sqrt(2.0 * (double)(n / 2) * (n / 2)) + 0.5); }
+}  // namespace
+
+int scint_spectrum_rec(const scint_params* p, double* s_rec, uint64_t* counts, int n_bins, void* stream) {
+    int rc = check_screen_check_params(p);
+    if (rc) return rc;
+    if (n_bins < 1) return fail(SCINT_EINVAL, "n_bins=%d must be >= 1", n_bins);
+    if (!s_rec || !counts) return fail(SCINT_EINVAL, "s_rec and counts must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n_hist = std::min(n_bins, max_annulus(p->n) + 1);
+    int dev = 0, sms = 0;
+    SCINT_CUDA(cudaGetDevice(&dev));
+    SCINT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t hist_bytes = (size_t)n_hist * sizeof(uint64_t);
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(200 * 1024) / hist_bytes));
+    const int blocks = std::min(p->n, sms * per_sm);
+    SCINT_CUDA(cudaMemsetAsync(s_rec, 0, (size_t)n_bins * sizeof(double), s));
+    SCINT_CUDA(cudaMemsetAsync(counts, 0, (size_t)n_bins * sizeof(uint64_t), s));
+    SynthArgs a = synth_args(p);
+    const double L = screen_len(p);
+    // three kernels: bin counts, |F|^2 sums, normalisation; only the histograms touch memory
+    rc = launch_timed(K_RADIAL, 16.0 * n_hist * 2, 0.0, s, [&] {
+        return launch_radial_spectrum(a, 1.0 / (L * L), n_hist, s_rec, reinterpret_cast<unsigned long long*>(counts),
+                                      blocks, s);
+    }, 3);
+    if (rc) return rc;
+    return ok();
+}
+
+int scint_structure_function_rec(const scint_params* p, const double* s_rec, int n_bins, const double* r_km,
+                                 int n_r, double* d_rec, double* r_rec, void* workspace, size_t workspace_bytes,
+                                 void* stream) {
+    int rc = check_screen_check_params(p);
+    if (rc) return rc;
+    if (n_bins < 2 || !s_rec) return fail(SCINT_EINVAL, "need s_rec with n_bins >= 2");
+    if (n_r < 0 || (n_r > 0 && (!r_km || !d_rec))) return fail(SCINT_EINVAL, "r_km and d_rec must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CrecArgs a{};
+    a.s = s_rec;
+    a.J = std::min(n_bins - 1, p->n / 2);
+    a.dq = 1.0 / screen_len(p);
+    a.half_L = 0.5 * screen_len(p);
+    if (n_r > 0) SCINT_LAUNCH(K_CREC, 8.0 * (a.J + n_r), 0.0, s, launch_crec(a, r_km, n_r, d_rec, s));
+    if (r_rec) {
+        Carver c{};
+        rc = resolve_ws(workspace, workspace_bytes, up(sizeof(BisectState)), s, &c);
+        if (rc) return rc;
+        BisectState* st = c.take<BisectState>(sizeof(BisectState));
+        const int rc2 = launch_timed(K_CREC, 8.0 * a.J, 0.0, s,
+                                     [&] { return launch_bisect(a, st, kRdiffRecIterations, r_rec, s); },
+                                     kRdiffRecIterations + 1);
+        if (rc2) return rc2;
+    }
     return ok();
 }
 

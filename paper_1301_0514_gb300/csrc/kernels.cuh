@@ -137,4 +137,29 @@ cudaError_t launch_map_moments(const float* map, int n, int r0, int r1, int c0, 
 cudaError_t launch_curve_moments(const float* curves, int n_curves, int n_samples,
                                  double* out, cudaStream_t s);
 
+
+// ---- screen check of Sect. 3.1.1 (screen_check.cu) --------------------------------
+constexpr int kRadialThreads = 512;
+constexpr int kCrecThreads = 256;
+constexpr int kBisectBlocks = 128;
+// Annulus sums of |F|^2 and bin counts (rows walked by `blocks` persistent
+// blocks, n_hist annuli in shared memory), then S_rec = sum / count * inv_l2.
+// s_rec and counts must be zero on entry.
+cudaError_t launch_radial_spectrum(const SynthArgs& a, double inv_l2, int n_hist, double* s_rec,
+                                   unsigned long long* counts, int blocks, cudaStream_t s);
+struct CrecArgs {
+    const double* s;     // S_rec(q_j), j = 0..J
+    int J;               // last annulus of the integral
+    double dq;           // 1/L
+    double half_L;       // upper end of the bisection bracket
+};
+struct BisectState {
+    double lo, hi;
+    int no_root;
+    unsigned arrived;
+    double partial[kBisectBlocks];
+};
+cudaError_t launch_crec(const CrecArgs& a, const double* r_km, int n_r, double* d, cudaStream_t s);
+cudaError_t launch_bisect(const CrecArgs& a, BisectState* st, int iterations, double* out, cudaStream_t s);
+
 }  // namespace scint

@@ -1,0 +1,76 @@
+// Shaped spectral values of the phase screen (Sect. 3.1, Eq. densite): the
+// noise of FFT bin (kx, ky) from Philox4x32-10 with counter (kx, ky, screen_id,
+// 0), Box-Muller, and the amplitude sqrt(L^2 S(q)).  Shared by the synthesis
+// and by the screen check of Sect. 3.1.1, so both see the same F.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace scint {
+
+// Uniform in (0,1) from the 64-bit word (hi:lo): top 53 bits plus one half, times 2^-53.
+SCINT_DEV double uniform53(uint32_t hi, uint32_t lo) {
+    const uint64_t w = ((uint64_t)hi << 32) | lo;
+    return ((double)(w >> 11) + 0.5) * 0x1.0p-53;
+}
+
+SCINT_DEV int signed_freq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// -ln u_a of a bin's first uniform u_a = (top 53 bits of (w1:w0) + 1/2) 2^-53, in FP64.
+SCINT_DEV double neg_log_ua64(const u32x4& w) { return -log(uniform53(w.y, w.x)); }
+
+// The same in FP32: u_a rounded once to float; -ln u_a goes through
+// log1p(-(1 - u_a)) when u_a >= 1/2 so that values near 1 keep their relative
+// accuracy (1 - u_a uses the complemented bits exactly).
+SCINT_DEV float neg_log_ua32(const u32x4& w) {
+    if (w.y & 0x80000000u) {
+        const float d = fmaf((float)((~w.x) >> 11), 0x1.0p-53f, (float)(~w.y) * 0x1.0p-32f) + 0x1.0p-54f;
+        return -log1pf(-d);
+    }
+    const float ua = fmaf((float)(w.x >> 11), 0x1.0p-53f, (float)w.y * 0x1.0p-32f) + 0x1.0p-54f;
+    return -logf(ua);
+}
+
+// Bins with |mx| <= kLowK and |my| <= kLowK carry almost all of the phase
+// variance (S ~ q^-beta): their noise and amplitude are computed in FP64.  The
+// other bins have small amplitudes, so FP32 Box-Muller and pow give phase errors
+// of ~1e-7 of their (small) rms contribution.
+constexpr int kLowK = 32;
+
+// Shaped spectral value F[ky][kx] = sqrt(L^2 S(q)) (g_re + i g_im) / sqrt(2).
+SCINT_DEV double2 spectrum_bin(const SynthArgs& a, int kx, int ky) {
+    const u32x4 w = philox4x32_10(u32x4{(uint32_t)kx, (uint32_t)ky, a.screen_id, 0u}, a.key0, a.key1);
+    const int mx = signed_freq(kx, a.n), my = signed_freq(ky, a.n);
+    const int m2 = mx * mx + my * my;
+    if (m2 == 0) return make_double2(0.0, 0.0);
+    if (abs(mx) <= kLowK && abs(my) <= kLowK) {
+        const double ub = uniform53(w.w, w.z);
+        const double r = sqrt(2.0 * neg_log_ua64(w));
+        double sn, cs;
+        sincospi(2.0 * ub, &sn, &cs);
+        const double sig = a.amp * pow((double)m2, a.neg_beta_4);
+        return make_double2(sig * r * cs, sig * r * sn);
+    }
+    const float r = sqrtf(2.0f * neg_log_ua32(w));
+    const float tb = fmaf((float)(w.z >> 11), 0x1.0p-52f, (float)w.w * 0x1.0p-31f) + 0x1.0p-53f;  // 2 u_b
+    float sn, cs;
+    sincospif(tb, &sn, &cs);
+    const float sig = a.amp32 * powf((float)m2, a.neg_beta_4_32);
+    return make_double2((double)(sig * r * cs), (double)(sig * r * sn));
+}
+
+// |F[ky][kx]|^2 = sigma^2 (g_re^2 + g_im^2) / 2 = sigma^2 (-2 ln u_a) / 2 of a
+// bin with Philox words w and m2 = mx^2 + my^2 > 0 (the Box-Muller angle
+// cancels), in the precision spectrum_bin uses for it: FP64 for the low bins
+// (|mx|, |my| <= kLowK), FP32 for the others.
+SCINT_DEV bool low_bin(int mx, int my) { return abs(mx) <= kLowK && abs(my) <= kLowK; }
+SCINT_DEV double power_low(const SynthArgs& a, const u32x4& w, int m2) {
+    const double sig = a.amp * pow((double)m2, a.neg_beta_4);
+    return sig * sig * (2.0 * neg_log_ua64(w));
+}
+SCINT_DEV float power_high(const SynthArgs& a, const u32x4& w, int m2) {
+    const float sig = a.amp32 * powf((float)m2, a.neg_beta_4_32);
+    return sig * sig * (2.0f * neg_log_ua32(w));
+}
+
+}  // namespace scint

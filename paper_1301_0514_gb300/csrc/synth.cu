@@ -16,6 +16,7 @@
 #include "dispatch.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "spectrum.cuh"
 
 namespace scint {
 
@@ -42,55 +43,6 @@ cudaError_t launch_twiddles32(float2* tw, int n, cudaStream_t s) {
 cudaError_t launch_twiddles64(double2* tw, int n, cudaStream_t s) {
     twiddles64_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
     return cudaGetLastError();
-}
-
-// Uniform in (0,1) from the 64-bit word (hi:lo): top 53 bits plus one half, times 2^-53.
-SCINT_DEV double uniform53(uint32_t hi, uint32_t lo) {
-    const uint64_t w = ((uint64_t)hi << 32) | lo;
-    return ((double)(w >> 11) + 0.5) * 0x1.0p-53;
-}
-
-SCINT_DEV int signed_freq(int i, int n) { return i < n / 2 ? i : i - n; }
-
-// Bins with |mx| <= kLowK and |my| <= kLowK carry almost all of the phase
-// variance (S ~ q^-beta): their noise and amplitude are computed in FP64.  The
-// other bins have small amplitudes, so FP32 Box-Muller and pow give phase errors
-// of ~1e-7 of their (small) rms contribution.
-constexpr int kLowK = 32;
-
-// Shaped spectral value F[ky][kx] = sqrt(L^2 S(q)) (g_re + i g_im) / sqrt(2).
-SCINT_DEV double2 spectrum_bin(const SynthArgs& a, int kx, int ky) {
-    const u32x4 w = philox4x32_10(u32x4{(uint32_t)kx, (uint32_t)ky, a.screen_id, 0u}, a.key0, a.key1);
-    const int mx = signed_freq(kx, a.n), my = signed_freq(ky, a.n);
-    const int m2 = mx * mx + my * my;
-    if (m2 == 0) return make_double2(0.0, 0.0);
-    if (abs(mx) <= kLowK && abs(my) <= kLowK) {
-        const double ua = uniform53(w.y, w.x);
-        const double ub = uniform53(w.w, w.z);
-        const double r = sqrt(-2.0 * log(ua));
-        double sn, cs;
-        sincospi(2.0 * ub, &sn, &cs);
-        const double sig = a.amp * pow((double)m2, a.neg_beta_4);
-        return make_double2(sig * r * cs, sig * r * sn);
-    }
-    // FP32 with the same 53-bit uniforms, u = (top 53 bits + 1/2) 2^-53, rounded
-    // once to float; -ln u_a goes through log1p(-(1 - u_a)) when u_a >= 1/2 so
-    // that values near 1 keep their relative accuracy (1 - u_a uses the
-    // complemented bits exactly).
-    float nl;
-    if (w.y & 0x80000000u) {
-        const float d = fmaf((float)((~w.x) >> 11), 0x1.0p-53f, (float)(~w.y) * 0x1.0p-32f) + 0x1.0p-54f;
-        nl = -log1pf(-d);
-    } else {
-        const float ua = fmaf((float)(w.x >> 11), 0x1.0p-53f, (float)w.y * 0x1.0p-32f) + 0x1.0p-54f;
-        nl = -logf(ua);
-    }
-    const float r = sqrtf(2.0f * nl);
-    const float tb = fmaf((float)(w.z >> 11), 0x1.0p-52f, (float)w.w * 0x1.0p-31f) + 0x1.0p-53f;  // 2 u_b
-    float sn, cs;
-    sincospif(tb, &sn, &cs);
-    const float sig = a.amp32 * powf((float)m2, a.neg_beta_4_32);
-    return make_double2((double)(sig * r * cs), (double)(sig * r * sn));
 }
 
 // Lines per block (all transformed together); N = 16384 lines (256 KB in FP64)

@@ -170,3 +170,26 @@ def test_batch_workspace_bytes(lib):
     assert S.batch_workspace_bytes(items, 4, 5) == 3 * one       # never more lanes than items
     assert S.batch_workspace_bytes(items, 8, 1) > one            # a larger wavelength group
     assert S.batch_workspace_bytes([_batch_entry(n=100)], 4, 1) == 0
+
+
+@pytest.mark.parametrize("n,msg", [(15, "even"), (8, "even"), (32770, "even")])
+def test_screen_check_rejected_on_host(lib, n, msg):
+    p = S.params(n=n, pixel_km=10.0, r_diff_km=50.0)
+    rc = lib.scint_spectrum_rec(ctypes.byref(p), ctypes.c_void_p(16), ctypes.c_void_p(16), 10, None)
+    assert rc == 1 and msg in lib.scint_last_error().decode()
+
+
+def test_screen_check_arguments_rejected_on_host(lib):
+    p = S.params(n=14000, pixel_km=28.85, r_diff_km=500.0)
+    assert lib.scint_spectrum_rec(ctypes.byref(p), ctypes.c_void_p(16), ctypes.c_void_p(16), 0, None) == 1
+    assert lib.scint_spectrum_rec(ctypes.byref(p), None, ctypes.c_void_p(16), 10, None) == 1
+    assert lib.scint_structure_function_rec(ctypes.byref(p), ctypes.c_void_p(16), 1, None, 0, None,
+                                            ctypes.c_void_p(16), None, 0, None) == 1
+    assert lib.scint_structure_function_rec(ctypes.byref(p), ctypes.c_void_p(16), 100, None, 3, None,
+                                            None, None, 0, None) == 1
+    assert S.max_annulus(14000) == O_max_annulus(14000)
+
+
+def O_max_annulus(n):
+    import oracle as O
+    return O.max_annulus(n)
