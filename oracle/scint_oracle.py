@@ -385,6 +385,60 @@ def intensity_mono(phi, p: ScreenParams, lambda_nm: float | None = None):
     return np.abs(a_out) ** 2
 
 
+def observer_pixel_km(p: ScreenParams, lambda_nm: float) -> float:
+    """Pixel of the observer-plane pattern of the one-FFT method: Delta_0 = lambda z / (N Delta_1)
+    (the conjugate variable of Eq. intens sampled by an N-point transform; Delta_0 = Delta_1 is the
+    paper's N Delta_1^2 = 2 pi R_F^2 of Sect. 3.2.5)."""
+    return lambda_nm * KM_PER_NM * p.z_pc * KM_PER_PC / (p.n * p.pixel_km)
+
+
+def propagate_conjugate(phi, p: ScreenParams, lambda_nm: float | None = None):
+    """Point-source pattern by the paper's one-FFT method (Eq. intens with Eq. Gxy):
+
+        h(x_0) = |FT[SF(x_1) SF(y_1) G](x_0 / (lambda z))|^2 / (lambda z)^2,
+        G = exp(i (phi lambda_ref/lambda + |x_1|^2 / (2 R_F^2))),
+
+    the 1/(2 pi R_F^2) prefactor inside the modulus as in Reading R5 (a uniform screen gives 1).
+    Coordinates take integer multiples of the pixel about the optical axis (Sect. 3.2.1, Reading
+    R16): x_1 = (i - N/2) Delta_1 on the screen and x_0 = (k - N/2) Delta_0 on the observer
+    plane, Delta_0 = lambda z / (N Delta_1); the taper uses the same pixels, at (i + 1/2) Delta_1
+    from the screen edge.  The Fourier integral is the plain sum over pixels,
+        FT[G](x_0 / lambda z) = Delta_1^2 sum_i G_i exp(-2 pi i x_1 . x_0 / (lambda z)),
+    whose kernel is exp(-2 pi i (i - N/2)(k - N/2) / N): the DFT with both indices shifted by
+    N/2 (numpy's fftshift(fft2(ifftshift(.)))).
+    """
+    lam = p.lambda_nm if lambda_nm is None else lambda_nm
+    n = p.n
+    lz = lam * KM_PER_NM * p.z_pc * KM_PER_PC
+    x1 = (np.arange(n) - n // 2) * p.pixel_km
+    a_in = screen_field(phi, p, lam)
+    g = a_in * np.exp(1j * np.pi * (x1[:, None] ** 2 + x1[None, :] ** 2) / lz)
+    ft = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(g))) * p.pixel_km ** 2
+    return np.abs(ft) ** 2 / lz ** 2
+
+
+def sum_passband_conjugate(phi, p: ScreenParams, lambdas_nm, weights=None):
+    """Passband co-addition (Sect. 3.2.4) of one-FFT patterns, whose pixels differ per
+    wavelength (Delta_0 proportional to lambda).  Every pattern is resampled onto the grid of
+    p.lambda_nm about the optical axis, which is a pixel centre of every grid (Sect. 3.2.1:
+    integer pixel centres "to allow simple combinations of illumination patterns with different
+    pixel sizes"): output pixel k samples pattern l at u = (k - N/2) lambda_grid/lambda_l + N/2
+    (pattern pixels), bilinearly, periodic like the discrete transform (Reading R16).
+    """
+    lambdas_nm = np.asarray(lambdas_nm, dtype=np.float64)
+    w = np.full(len(lambdas_nm), 1.0 / len(lambdas_nm)) if weights is None else np.asarray(weights, float)
+    n = p.n
+    k = np.arange(n, dtype=np.float64) - n // 2
+    out = np.zeros((n, n))
+    for lam, wl in zip(lambdas_nm, w):
+        h = propagate_conjugate(phi, p, lam)
+        r = p.lambda_nm / lam
+        u = k * r + n // 2
+        X, Y = np.meshgrid(u, u)                       # X[row, col] = u[col], Y[row, col] = u[row]
+        out += wl * bilinear_periodic(h, X.ravel(), Y.ravel()).reshape(n, n)
+    return out
+
+
 def sum_passband(phi, p: ScreenParams, lambdas_nm, weights=None):
     """Passband co-addition (Sect. 3.2.4): sum_l w_l I_l with sum w = 1 (flat 1/N_l by default)."""
     lambdas_nm = np.asarray(lambdas_nm, dtype=np.float64)
