@@ -513,19 +513,143 @@ def run_screen_check(args):
         torch.distributed.destroy_process_group()
 
 
+def run_conjugate(args):
+    """The paper's one-FFT propagator on a passband batch at critical sampling
+    (N Delta^2 = lambda z at 550 nm), timed beside the transfer-function passband of
+    the same screens.  Metric: pixel-wavelengths/s."""
+    import torch
+    import paper_1301_0514_gb300 as S
+    from paper_1301_0514_gb300 import workloads as W
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    n, count = args.conj_n, 16
+    lam_ref = 550.0
+    pix = float(np.sqrt(lam_ref * W.KM_PER_NM * 160.0 * W.KM_PER_PC / n))
+    lams = W.passband_400_700(32)
+    rng = np.random.default_rng(W.SEED_BASE + 9400)
+    P = [S.params(n=n, pixel_km=pix, r_diff_km=float(rng.uniform(3.0, 12.0) * pix), lambda_nm=lam_ref,
+                  lambda_ref_nm=lam_ref, seed=W.SEED_BASE + 9400 + 100000 * rank + k, screen_id=k)
+         for k in range(count)]
+    phi = torch.empty((n, n), dtype=torch.float64, device=dev)
+    out = torch.empty((n, n), dtype=torch.float32, device=dev)
+    ws = torch.empty(S.workspace_bytes(P[0], len(lams)) + 4 * n * n * len(lams), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    units = float(n) * n * len(lams) * count
+
+    def step(conj=True):
+        for p in P:
+            S.make_screen(p, out=phi, workspace=ws)
+            if conj:
+                S.sum_passband_conjugate(p, phi, lams, out=out, workspace=ws)
+            else:
+                S.sum_passband(p, phi, lams, out=out, workspace=ws)
+
+    def timed(conj):
+        step(conj)
+        torch.cuda.synchronize(dev)
+        S.profile_enable(True)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            step(conj)
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ks = S.profile_read()
+        S.profile_enable(False)
+        return e0.elapsed_time(e1) / args.steps, ks
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, kstats = timed(True)
+    clk = clocks.stop()
+    ms_tf, kstats_tf = timed(False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units * world / (ms * 1e-3)
+    hbm_peak, sm_max_mhz, peak_src = _peaks()
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    dom_name, dom = max(((k, v) for k, v in kstats.items() if k.startswith("conj")), key=lambda kv: kv[1]["total_ms"])
+    tflops = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12
+    gbs = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
+            "traffic": None, "kernel": dom_name, "share": dom["total_ms"] / ms, "hbm_gbs": gbs,
+            "hbm_frac": gbs / hbm_peak, "peak_source": f"alu = {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                                       f"{sm_max_mhz:.0f} MHz; hbm {peak_src}"}
+
+    # end to end through the public API: the passband map of every screen read back
+    host = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for p in P:
+        S.make_screen(p, out=phi, workspace=ws)
+        S.sum_passband_conjugate(p, phi, lams, out=out, workspace=ws)
+        host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        po = O.ScreenParams(n=1024, pixel_km=float(np.sqrt(lam_ref * O.KM_PER_NM * 160.0 * O.KM_PER_PC / 1024)),
+                            r_diff_km=6.0 * pix * np.sqrt(n / 1024), lambda_nm=lam_ref, lambda_ref_nm=lam_ref, seed=7)
+        t0 = time.perf_counter()
+        O.sum_passband_conjugate(O.make_screen(po), po, lams[::4])
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1024 * 1024 * len(lams[::4]) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one 1024^2 critical-sampling screen x {len(lams[::4])} wavelengths, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": "one-FFT (Eq. intens) passband pixel-wavelengths/sec at critical sampling",
+                "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": f"{count} screens {n}^2, {pix:.2f} km pixels (N Delta^2 = lambda z at 550 nm), "
+                                       f"R_diff 3-12 pixels, 32 wavelengths 400-700 nm, patterns resampled onto the "
+                                       f"550 nm grid", "l2": "fields of 134 MB per screen and wavelength"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": units * world / (e2e_ms * 1e-3), "unit": UNIT,
+                        "h2d_bytes_per_step": int(count * (len(lams) * 8 + 96)), "d2h_bytes_per_step": int(count * n * n * 4),
+                        "ms_per_step": e2e_ms},
+                "transfer_function_same_screens": {"value": units * world / (ms_tf * 1e-3), "ms_per_step": ms_tf},
+                "gpu_launches": sum(v["launches"] for v in kstats.values()) * args.steps, "clocks": clk,
+                "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in kstats.items()},
+                "kernels_transfer_function": {k: {"launches": v["launches"], "ms": v["total_ms"]}
+                                              for k, v in kstats_tf.items()}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "screen_check"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "screen_check", "conjugate"])
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
+    ap.add_argument("--conj-n", type=int, default=4096, help="grid of the one-FFT workload")
     ap.add_argument("--lanes", type=int, default=4, help="streams the batch is scheduled on (1..8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload == "screen_check" and args.impl != "reference":
         run_screen_check(args)
+    elif args.workload == "conjugate" and args.impl != "reference":
+        run_conjugate(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

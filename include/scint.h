@@ -201,6 +201,43 @@ int scint_sum_passband(const scint_params* p, const double* phi,
                        void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * The paper's own propagator (Eq. intens with Eq. Gxy): one 2D Fourier
+ * transform of G = SF(x_1) SF(y_1) exp(i (phi lambda_ref/lambda + |x_1|^2/2R_F^2)),
+ *   h(x_0) = |FT[G](x_0 / (lambda z))|^2 / (lambda z)^2     (1 for a uniform screen),
+ * on the observer grid of the conjugate variable: x_0 = (k - N/2) Delta_0 with
+ * Delta_0 = lambda z / (N Delta_1) (scint_conjugate_pixel_km), screen pixels at
+ * x_1 = (i - N/2) Delta_1 about the optical axis (integer pixel centres, Sect.
+ * 3.2.1).  Unlike the transfer function this is the plain, non-periodic Fresnel
+ * sum over the screen; at critical sampling N Delta_1^2 = lambda z (the paper's
+ * N Delta^2 = 2 pi R_F^2) both give the same pattern pixel for pixel.  Half the
+ * FFT work of scint_propagate (one transform per axis instead of two).
+ *   phi        device, N*N doubles, read.   intensity  device, N*N floats, written,
+ *              row-major with the optical axis at element (N/2, N/2).
+ * Workspace: as scint_propagate.
+ */
+int scint_propagate_conjugate(const scint_params* p, const double* phi, float* intensity,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
+/* Observer-plane pixel Delta_0 = lambda z / (N Delta_1) of the one-FFT method at
+ * lambda_nm (km); NaN for invalid arguments. */
+double scint_conjugate_pixel_km(const scint_params* p, double lambda_nm);
+
+/*
+ * Passband co-addition (Sect. 3.2.4) of one-FFT patterns.  The pattern of
+ * wavelength l has pixel Delta_0(lambda_l), so each is resampled onto the grid
+ * of p->lambda_nm about the optical axis, a pixel centre of every grid: output
+ * pixel k samples pattern l bilinearly (periodic, like the discrete transform)
+ * at (k - N/2) lambda_nm/lambda_l + N/2 of its pixels, and
+ *   intensity (+)= sum_l w_l h_l(resampled).
+ * Arguments as scint_sum_passband.  Workspace: ws_prop plus 4 N^2 bytes per
+ * wavelength of a group (smaller workspaces give smaller groups).
+ */
+int scint_sum_passband_conjugate(const scint_params* p, const double* phi,
+                                 const double* lambdas_nm, const double* weights, int n_lambda,
+                                 float* intensity, int accumulate,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Extended source (Sect. 3.2.3, Eq. iprh): periodic convolution of the
  * intensity with the uniform disk of radius p->source_radius_km, applied in
  * Fourier space as K(q) = 2 J1(2 pi q R_s)/(2 pi q R_s).  R_s = 0 leaves the

@@ -12,6 +12,7 @@ from ._lib import (  # noqa: F401
     batch_workspace_bytes,
     ScintError,
     ScintParams,
+    conjugate_pixel_km,
     curve_modulation,
     fft_lines,
     lib,
@@ -26,6 +27,7 @@ from ._lib import (  # noqa: F401
     profile_enable,
     profile_read,
     propagate,
+    propagate_conjugate,
     rdiff_gradient,
     release,
     run_batch,
@@ -33,6 +35,7 @@ from ._lib import (  # noqa: F401
     spectrum_rec,
     structure_function_rec,
     sum_passband,
+    sum_passband_conjugate,
     workspace_bytes,
 )
 

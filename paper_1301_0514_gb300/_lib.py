@@ -127,6 +127,9 @@ def lib() -> ctypes.CDLL:
         "scint_batch_workspace_bytes": ([ctypes.POINTER(BatchItem), _i, _i, _i], _sz),
         "scint_run_batch": ([ctypes.POINTER(BatchItem), _i, _vp, _vp, _i, _i, _vp, _sz, _vp], _i),
         "scint_spectrum_rec": ([_P, _vp, _vp, _i, _vp], _i),
+        "scint_propagate_conjugate": ([_P, _vp, _vp, _vp, _sz, _vp], _i),
+        "scint_sum_passband_conjugate": ([_P, _vp, _vp, _vp, _i, _vp, _i, _vp, _sz, _vp], _i),
+        "scint_conjugate_pixel_km": ([_P, ctypes.c_double], ctypes.c_double),
         "scint_structure_function_rec": ([_P, _vp, _i, _vp, _i, _vp, _vp, _vp, _sz, _vp], _i),
         "scint_profile_enable": ([_i], _i),
         "scint_profile_read": ([ctypes.POINTER(KernelStat), _i, ctypes.POINTER(_i)], _i),
@@ -198,6 +201,45 @@ def sum_passband(p: ScintParams, phi: torch.Tensor, lambdas_nm: Sequence[float],
         out = torch.empty((p.n, p.n), dtype=torch.float32, device=phi.device)
     ws, wp, wb = _workspace(p, len(lam), workspace, phi.device)
     _check(lib().scint_sum_passband(
+        ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
+        lam.ctypes.data_as(ctypes.c_void_p), None if w is None else w.ctypes.data_as(ctypes.c_void_p),
+        len(lam), _dev(out, torch.float32, p.n * p.n, "intensity"), int(bool(accumulate)), wp, wb,
+        _stream(stream)))
+    return out
+
+
+def conjugate_pixel_km(p: ScintParams, lambda_nm: Optional[float] = None) -> float:
+    """Observer pixel lambda z / (N Delta) of the one-FFT method (km)."""
+    return float(lib().scint_conjugate_pixel_km(ctypes.byref(p), p.lambda_nm if lambda_nm is None else lambda_nm))
+
+
+def propagate_conjugate(p: ScintParams, phi: torch.Tensor, out: Optional[torch.Tensor] = None, workspace=None,
+                        stream=None) -> torch.Tensor:
+    """One-FFT pattern at p.lambda_nm (Eq. intens), optical axis at element (N/2, N/2)."""
+    if out is None:
+        out = torch.empty((p.n, p.n), dtype=torch.float32, device=phi.device)
+    ws, wp, wb = _workspace(p, 1, workspace, phi.device)
+    _check(lib().scint_propagate_conjugate(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
+                                           _dev(out, torch.float32, p.n * p.n, "intensity"), wp, wb,
+                                           _stream(stream)))
+    return out
+
+
+def sum_passband_conjugate(p: ScintParams, phi: torch.Tensor, lambdas_nm: Sequence[float], weights=None,
+                           out: Optional[torch.Tensor] = None, accumulate: bool = False, workspace=None,
+                           stream=None) -> torch.Tensor:
+    """Passband of one-FFT patterns resampled onto the grid of p.lambda_nm."""
+    lam = np.ascontiguousarray(lambdas_nm, dtype=np.float64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    if w is not None and w.shape != lam.shape:
+        raise ValueError("weights must match lambdas")
+    if out is None:
+        out = torch.empty((p.n, p.n), dtype=torch.float32, device=phi.device)
+    if workspace is None:
+        wp, wb = None, 0
+    else:
+        wp, wb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+    _check(lib().scint_sum_passband_conjugate(
         ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
         lam.ctypes.data_as(ctypes.c_void_p), None if w is None else w.ctypes.data_as(ctypes.c_void_p),
         len(lam), _dev(out, torch.float32, p.n * p.n, "intensity"), int(bool(accumulate)), wp, wb,

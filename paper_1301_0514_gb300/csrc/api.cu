@@ -177,12 +177,13 @@ int resolve_ws(void* ws, size_t bytes, size_t need, cudaStream_t s, Carver* c) {
 enum KClass {
     K_TWIDDLES, K_SYNTH_ROWS, K_SYNTH_COLS, K_PROP_TABLES, K_PROP_ROWS, K_PROP_COLS,
     K_SMOOTH_FWD, K_SMOOTH_ROWS, K_SMOOTH_INV, K_LIGHTCURVE, K_MOMENTS,
-    K_LC_ADJ, K_ADJ_COLS, K_ADJ_ROWS, K_DOT, K_RADIAL, K_CREC, K_COUNT
+    K_LC_ADJ, K_ADJ_COLS, K_ADJ_ROWS, K_DOT, K_RADIAL, K_CREC, K_CONJ_ROWS, K_CONJ_COLS, K_RESAMPLE, K_COUNT
 };
 const char* const kClassName[K_COUNT] = {
     "twiddles", "synth_rows", "synth_cols", "prop_tables", "prop_rows", "prop_cols",
     "smooth_fwd_cols", "smooth_rows", "smooth_inv_cols", "lightcurve", "moments",
-    "lightcurve_adjoint", "adj_cols", "adj_rows", "dot", "radial_spectrum", "structure_rec"};
+    "lightcurve_adjoint", "adj_cols", "adj_rows", "dot", "radial_spectrum", "structure_rec",
+    "conj_rows", "conj_cols", "resample"};
 
 struct ProfRec {
     int cls;
@@ -287,10 +288,10 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
     const double nn = (double)n * n;
     SCINT_LAUNCH(K_PROP_TABLES, 12.0 * g * n, 0.0, s, launch_prop_tables(ta, s));
     // rows: phi read once, one complex64 field written per wavelength; FFT_x + IFFT_x per row
-    SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * g * nn, 2.0 * g * n * fft_flops(n), s, launch_prop_rows(pa, s));
+    SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * g * nn, 2.0 * g * n * fft_flops(n), s, launch_prop_rows(pa, false, s));
     // columns: fields read, intensity written once (and read when accumulating)
     SCINT_LAUNCH(K_PROP_COLS, 8.0 * g * nn + (accumulate ? 8.0 : 4.0) * nn, 2.0 * g * n * fft_flops(n), s,
-                 launch_prop_cols(pa, s));
+                 launch_prop_cols(pa, false, s));
     return SCINT_OK;
 }
 
@@ -317,6 +318,87 @@ int passband_impl(const scint_params* p, const double* phi, const double* lambda
         const int gg = std::min(g, n_lambda - l0);
         rc = run_group(p, phi, lambdas, w.data(), l0, gg, intensity, accumulate || l0 > 0, c, tw, s);
         if (rc) return rc;
+    }
+    return ok();
+}
+
+// ---- the paper's one-FFT propagator (Eq. intens, Eq. Gxy) -----------------------
+double conj_pixel(const scint_params* p, double lambda_nm) {
+    return lz_km2(lambda_nm, p->z_pc) / (p->n * p->pixel_km);
+}
+size_t ws_conj(int n, int g, bool direct) {
+    return ws_prop(n, g) + (direct ? 0 : up((size_t)g * n * n * 4));
+}
+
+int conj_impl(const scint_params* p, const double* phi, const double* lambdas, const double* weights,
+              int n_lambda, float* intensity, int accumulate, void* ws, size_t ws_bytes, cudaStream_t s) {
+    int rc = check_passband(p, lambdas, weights, n_lambda);
+    if (rc) return rc;
+    if (!phi || !intensity) return fail(SCINT_EINVAL, "phi and intensity must be device pointers");
+    const int n = p->n;
+    std::vector<double> w(n_lambda, 1.0 / n_lambda);
+    if (weights) w.assign(weights, weights + n_lambda);
+    // one wavelength on the output grid: the column pass writes the pattern itself
+    const bool direct = n_lambda == 1 && lambdas[0] == p->lambda_nm;
+    int g = n_lambda;
+    if (ws) {
+        while (g > 1 && ws_conj(n, g, direct) > ws_bytes) --g;
+    }
+    Carver c{};
+    rc = resolve_ws(ws, ws_bytes, ws_conj(n, g, direct), s, &c);
+    if (rc) return rc;
+    float2* tw = c.take<float2>((size_t)n * 8);
+    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n, 0.0, s, launch_twiddles32(tw, n, s));
+    const double nn = (double)n * n, d1 = p->pixel_km;
+    for (int l0 = 0; l0 < n_lambda; l0 += g) {
+        const int gg = std::min(g, n_lambda - l0);
+        TableArgs ta{};
+        ta.n = n;
+        ta.count = gg;
+        PropArgs pa{};
+        pa.n = n;
+        pa.phi = phi;
+        pa.tw = tw;
+        pa.lam.count = gg;
+        ResampleArgs ra{};
+        ra.n = n;
+        ra.count = gg;
+        ra.intensity = intensity;
+        ra.accumulate = accumulate || l0 > 0;
+        for (int i = 0; i < gg; ++i) {
+            const double l = lambdas[l0 + i], lz = lz_km2(l, p->z_pc);
+            ta.lz_over_2L2[i] = lz / (2.0 * screen_len(p) * screen_len(p));   // H table (unused here)
+            ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
+            pa.lam.scale_fx[i] = (uint64_t)std::llround(p->lambda_ref_nm / l * 4294967296.0);
+            pa.lam.weight[i] = (float)w[l0 + i];
+            pa.lam.scale[i] = (float)(p->lambda_ref_nm / l);
+            // chirp turns per pixel^2, Delta^2 / (2 lambda z), reduced mod 1 and in 0.64 fixed point
+            const double c_turns = d1 * d1 / (2.0 * lz);
+            const double frac = c_turns - std::floor(c_turns);
+            pa.conj.chirp_fx[i] = (unsigned long long)std::llround(std::ldexp(frac, 52)) << 12;   // 1 turn wraps to 0
+            pa.conj.norm[i] = (float)((d1 * d1 / lz) * (d1 * d1 / lz));
+            ra.r_fx[i] = std::llround(p->lambda_nm / l * 4294967296.0);
+            ra.weight[i] = (float)w[l0 + i];
+        }
+        Carver cg = c;
+        ta.h = cg.take<float2>((size_t)gg * n * 8);
+        ta.sf = cg.take<float>((size_t)gg * n * 4);
+        pa.h = ta.h;
+        pa.sf = ta.sf;
+        pa.work = cg.take<float2>((size_t)gg * n * n * 8);
+        pa.intensity = intensity;
+        pa.accumulate = accumulate || l0 > 0;
+        pa.conj.direct = direct ? 1 : 0;
+        pa.conj.pattern = direct ? nullptr : cg.take<float>((size_t)gg * n * n * 4);
+        ra.pattern = pa.conj.pattern;
+        SCINT_LAUNCH(K_PROP_TABLES, 12.0 * gg * n, 0.0, s, launch_prop_tables(ta, s));
+        // one FFT per row and per column and wavelength
+        SCINT_LAUNCH(K_CONJ_ROWS, 8.0 * nn + 8.0 * gg * nn, 1.0 * gg * n * fft_flops(n), s,
+                     launch_prop_rows(pa, true, s));
+        SCINT_LAUNCH(K_CONJ_COLS, 8.0 * gg * nn + (direct ? (pa.accumulate ? 8.0 : 4.0) * nn : 4.0 * gg * nn),
+                     1.0 * gg * n * fft_flops(n), s, launch_prop_cols(pa, true, s));
+        if (!direct)
+            SCINT_LAUNCH(K_RESAMPLE, 4.0 * gg * nn + (ra.accumulate ? 8.0 : 4.0) * nn, 0.0, s, launch_resample(ra, s));
     }
     return ok();
 }
@@ -456,6 +538,26 @@ int scint_propagate_noalloc(const scint_params* p, const double* phi, float* int
     const double lam = p->lambda_nm, w = 1.0;
     return passband_impl(p, phi, &lam, &w, 1, intensity, 0, scratch, kStaticScratchBytes,
                          static_cast<cudaStream_t>(stream));
+}
+
+double scint_conjugate_pixel_km(const scint_params* p, double lambda_nm) {
+    if (check_params(p) || !(lambda_nm > 0) || !std::isfinite(lambda_nm)) return std::nan("");
+    return conj_pixel(p, lambda_nm);
+}
+
+int scint_propagate_conjugate(const scint_params* p, const double* phi, float* intensity, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+    if (!p) return fail(SCINT_EINVAL, "params is NULL");
+    const double lam = p->lambda_nm, w = 1.0;
+    return conj_impl(p, phi, &lam, &w, 1, intensity, 0, workspace, workspace_bytes,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int scint_sum_passband_conjugate(const scint_params* p, const double* phi, const double* lambdas_nm,
+                                 const double* weights, int n_lambda, float* intensity, int accumulate,
+                                 void* workspace, size_t workspace_bytes, void* stream) {
+    return conj_impl(p, phi, lambdas_nm, weights, n_lambda, intensity, accumulate, workspace, workspace_bytes,
+                     static_cast<cudaStream_t>(stream));
 }
 
 int scint_sum_passband(const scint_params* p, const double* phi, const double* lambdas_nm,
@@ -668,7 +770,7 @@ int scint_lightcurve_adjoint(const scint_params* p, const double* phi, const dou
         aa.accumulate = accumulate || l0 > 0;
         aa.lam = pa.lam;
         SCINT_LAUNCH(K_PROP_TABLES, 12.0 * gg * n, 0.0, s, launch_prop_tables(ta, s));
-        SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * gg * nn, 2.0 * gg * n * fft_flops(n), s, launch_prop_rows(pa, s));
+        SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * gg * nn, 2.0 * gg * n * fft_flops(n), s, launch_prop_rows(pa, false, s));
         SCINT_LAUNCH(K_ADJ_COLS, 16.0 * gg * nn + 4.0 * nn, 4.0 * gg * n * fft_flops(n), s, launch_adj_cols(aa, s));
         SCINT_LAUNCH(K_ADJ_ROWS, 8.0 * gg * nn + 8.0 * nn + (aa.accumulate ? 16.0 : 8.0) * nn,
                      2.0 * gg * n * fft_flops(n), s, launch_adj_rows(aa, s));

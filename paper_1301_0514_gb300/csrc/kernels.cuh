@@ -56,6 +56,14 @@ struct LambdaSet {
     float scale[kMaxLambda];         // s = lambda_ref/lambda (the adjoint's d(phase)/d(phi))
 };
 
+// One-FFT (conjugate-plane) mode of the propagation passes (Eq. intens, Eq. Gxy).
+struct ConjSet {
+    unsigned long long chirp_fx[kMaxLambda];   // frac(Delta^2 / (2 lambda z)) 2^64: chirp turns per pixel^2
+    float norm[kMaxLambda];                    // (Delta^2 / (lambda z))^2
+    int direct;                                // 1: w norm |A|^2 is summed into intensity
+    float* pattern;                            // 0: per lambda n*n floats norm |A|^2, row-major
+};
+
 struct PropArgs {
     int n;
     const double* phi;       // n*n radians at lambda_ref
@@ -66,6 +74,7 @@ struct PropArgs {
     float* intensity;        // n*n
     int accumulate;          // add to intensity instead of overwriting
     LambdaSet lam;
+    ConjSet conj;            // used by the one-FFT mode only
 };
 // h, sf tables for a wavelength group from host-side scalars.
 struct TableArgs {
@@ -76,8 +85,19 @@ struct TableArgs {
     float* sf;
 };
 cudaError_t launch_prop_tables(const TableArgs& a, cudaStream_t s);
-cudaError_t launch_prop_rows(const PropArgs& a, cudaStream_t s);
-cudaError_t launch_prop_cols(const PropArgs& a, cudaStream_t s);
+// conj = false: transfer function (FFT, H, IFFT per axis); true: one-FFT method.
+cudaError_t launch_prop_rows(const PropArgs& a, bool conj, cudaStream_t s);
+cudaError_t launch_prop_cols(const PropArgs& a, bool conj, cudaStream_t s);
+// Passband of one-FFT patterns: intensity (+)= sum_l w_l pattern_l resampled
+// bilinearly (periodic) at (k - n/2) r_l + n/2, r_l in 32.32 fixed point.
+struct ResampleArgs {
+    int n, count, accumulate;
+    const float* pattern;    // count patterns of n*n floats
+    float* intensity;
+    long long r_fx[kMaxLambda];
+    float weight[kMaxLambda];
+};
+cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t s);
 
 // -------- source smoothing ---------------------------------------------------
 struct SmoothArgs {

@@ -16,6 +16,8 @@
 // phi s scaled by 2^64, so the reduction modulo 2 pi is exact integer
 // arithmetic (error |phi s| 2^-33 / 2 pi turns from rounding s) and only the
 // reduced angle goes to the FP32 sine/cosine.
+#include <algorithm>
+
 #include "dispatch.cuh"
 #include "propagate.cuh"
 
@@ -54,7 +56,7 @@ cudaError_t launch_prop_tables(const TableArgs& a, cudaStream_t s) {
 }
 
 // ---- row pass ------------------------------------------------------------------
-template <int N>
+template <int N, bool CONJ>
 __global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
 prop_rows_kernel(PropArgs a) {
     using Pl = FftPlan<N>;
@@ -85,14 +87,25 @@ prop_rows_kernel(PropArgs a) {
         const float2* h = a.h + (size_t)l * N;
         const float sfy = sf[y];
         float2 v[E];
+        if constexpr (CONJ) {
+            // G = SF SF exp(i (phi s + |x_1|^2 / 2 R_F^2)) (-1)^(x + y), Eq. Gxy
+            const unsigned long long C = a.conj.chirp_fx[l];
+            const unsigned long long cy = chirp_turns(C, y, N);
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = unit_phasor(P[m * TL], S) * (sfy * __ldg(sf + t + m * T));
+            for (int m = 0; m < E; ++m)
+                v[m] = unit_phasor(P[m * TL], S, cy + chirp_turns(C, t + m * T, N)) * (sfy * __ldg(sf + t + m * T));
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = unit_phasor(P[m * TL], S) * (sfy * __ldg(sf + t + m * T));
+        }
         if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
         else fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, twp);
+        if constexpr (!CONJ) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
-        if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
-        else fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, twp);
+            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
+            if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
+            else fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, twp);
+        }
         float2* dst = a.work + (size_t)l * N * N;
 #pragma unroll
         for (int m = 0; m < E; ++m) dst[strip_index<W>(y, t + m * T, N)] = v[m];
@@ -101,7 +114,7 @@ prop_rows_kernel(PropArgs a) {
 }
 
 // ---- column pass ---------------------------------------------------------------
-template <int N>
+template <int N, bool CONJ>
 __global__ void __launch_bounds__(pcol_threads<N>(), 1)
 prop_cols_kernel(PropArgs a) {
     using Pl = FftPlan<N, kColEPT>;
@@ -133,13 +146,35 @@ prop_cols_kernel(PropArgs a) {
         for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * WL + w];
         if constexpr (TWM == 2) fft_line_tr<float2, N, -1, kColEPT, W>(v, buf, t, tr);
         else fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
+        if constexpr (CONJ) {
+            // h = (Delta^2 / lambda z)^2 |FT G|^2 on the pattern grid of this wavelength (Eq. intens)
+            const float nrm = a.conj.norm[l];
+            if (a.conj.direct) {
+                const float wn = a.lam.weight[l] * nrm;
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
-        if constexpr (TWM == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
-        else fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);
+                for (int m = 0; m < E; ++m) acc[m * TL] = fmaf(wn, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m * TL]);
+            } else {
+                // column-major: this column's values are contiguous, so the stores coalesce
+                float* pat = a.conj.pattern + (size_t)l * N * N + (size_t)x * N;
+#pragma unroll
+                for (int m = 0; m < E; ++m) pat[t + m * T] = nrm * fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
+            }
+            continue;
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
+            if constexpr (TWM == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
+            else fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);
+        }
         const float wl = a.lam.weight[l];
 #pragma unroll
         for (int m = 0; m < E; ++m) acc[m * TL] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m * TL]);
+    }
+    if constexpr (CONJ) {
+        if (!a.conj.direct) {
+            if constexpr (CS == 2) line_sync<CS>();
+            return;
+        }
     }
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -149,32 +184,132 @@ prop_cols_kernel(PropArgs a) {
     if constexpr (CS == 2) line_sync<CS>();
 }
 
-cudaError_t launch_prop_rows(const PropArgs& a, cudaStream_t s) {
+template <bool CONJ>
+cudaError_t launch_rows(const PropArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
         if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            cudaError_t e = set_smem(prop_rows_kernel<N>, prow_smem<N>());
+            cudaError_t e = set_smem(prop_rows_kernel<N, CONJ>, prow_smem<N>());
             if (e != cudaSuccess) return e;
-            return launch_k(prop_rows_kernel<N>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
+            return launch_k(prop_rows_kernel<N, CONJ>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
                             dim3(prow_threads<N>()), prow_smem<N>(), s, a);
         }
     });
 }
 
-cudaError_t launch_prop_cols(const PropArgs& a, cudaStream_t s) {
+template <bool CONJ>
+cudaError_t launch_cols(const PropArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
         if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            cudaError_t e = set_smem(prop_cols_kernel<N>, pcol_smem<N>());
+            cudaError_t e = set_smem(prop_cols_kernel<N, CONJ>, pcol_smem<N>());
             if (e != cudaSuccess) return e;
-            return launch_k(prop_cols_kernel<N>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
+            return launch_k(prop_cols_kernel<N, CONJ>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
                             dim3(pcol_threads<N>()), pcol_smem<N>(), s, a);
         }
     });
+}
+
+cudaError_t launch_prop_rows(const PropArgs& a, bool conj, cudaStream_t s) {
+    return conj ? launch_rows<true>(a, s) : launch_rows<false>(a, s);
+}
+cudaError_t launch_prop_cols(const PropArgs& a, bool conj, cudaStream_t s) {
+    return conj ? launch_cols<true>(a, s) : launch_cols<false>(a, s);
+}
+
+// ---- passband of one-FFT patterns --------------------------------------------------
+// Output pixel (X, Y) samples pattern l at (X - n/2) r_l + n/2 and (Y - n/2) r_l + n/2
+// pattern pixels; the products are exact in 32.32 fixed point (|X - n/2| r_l < 2^47).
+// Patterns are column-major (element (x, y) at x n + y).
+struct Sample {
+    int i0;       // integer part, not yet wrapped
+    float f;      // fraction
+};
+SCINT_DEV Sample sample_at(int X, int n, long long r_fx) {
+    const long long u = (long long)(X - n / 2) * r_fx + ((long long)(n / 2) << 32);
+    return Sample{(int)(u >> 32), (float)(unsigned)(u & 0xFFFFFFFFll) * 0x1.0p-32f};
+}
+
+// Tiled form: a block makes a 32 x 32 output tile and keeps it in registers over
+// all wavelengths.  Lanes take consecutive output rows of one column, so the
+// four bilinear taps of a warp read consecutive elements of two pattern columns
+// (patterns are column-major); the tile goes out through shared memory as rows.
+constexpr int kResTile = 32;
+__global__ void __launch_bounds__(256) resample_tiled_kernel(ResampleArgs a) {
+    __shared__ float tile[kResTile][kResTile + 1];   // [x][y]
+    const int n = a.n;
+    const int X0 = blockIdx.x * kResTile, Y0 = blockIdx.y * kResTile;
+    const int ly = threadIdx.x % kResTile, lx = threadIdx.x / kResTile;   // lx in [0, 8)
+    float acc[kResTile / 8] = {};
+    for (int l = 0; l < a.count; ++l) {
+        const long long r = a.r_fx[l];
+        const float* h = a.pattern + (size_t)l * n * n;
+        const Sample sy = sample_at(Y0 + ly, n, r);
+        const int y0 = sy.i0 & (n - 1), y1 = (y0 + 1) & (n - 1);
+        const float wl = a.weight[l];
+#pragma unroll
+        for (int q = 0; q < kResTile / 8; ++q) {
+            const Sample sx = sample_at(X0 + lx + 8 * q, n, r);
+            const int x0 = sx.i0 & (n - 1), x1 = (x0 + 1) & (n - 1);
+            const float* c0 = h + (size_t)x0 * n;
+            const float* c1 = h + (size_t)x1 * n;
+            const float h00 = __ldg(c0 + y0), h01 = __ldg(c0 + y1), h10 = __ldg(c1 + y0), h11 = __ldg(c1 + y1);
+            const float left = fmaf(sy.f, h01 - h00, h00), right = fmaf(sy.f, h11 - h10, h10);
+            acc[q] = fmaf(wl, fmaf(sx.f, right - left, left), acc[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kResTile / 8; ++q) tile[lx + 8 * q][ly] = acc[q];
+    __syncthreads();
+    // rows out: lanes take consecutive x of one row
+#pragma unroll
+    for (int q = 0; q < kResTile / 8; ++q) {
+        const int oy = lx + 8 * q, ox = ly;
+        float* o = a.intensity + (size_t)(Y0 + oy) * n + X0 + ox;
+        const float v = tile[ox][oy];
+        *o = a.accumulate ? *o + v : v;
+    }
+}
+
+// Plain form for grids below one tile and scale factors beyond the patch.
+__global__ void resample_kernel(ResampleArgs a) {
+    const int n = a.n;
+    const size_t total = (size_t)n * n;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int X = (int)(i % n), Y = (int)(i / n);
+        float acc = 0.0f;
+        for (int l = 0; l < a.count; ++l) {
+            const Sample sx = sample_at(X, n, a.r_fx[l]), sy = sample_at(Y, n, a.r_fx[l]);
+            const int x0 = sx.i0 & (n - 1), y0 = sy.i0 & (n - 1);
+            const int x1 = (x0 + 1) & (n - 1), y1 = (y0 + 1) & (n - 1);
+            const float* h = a.pattern + (size_t)l * total;
+            const float h00 = __ldg(h + (size_t)x0 * n + y0), h10 = __ldg(h + (size_t)x1 * n + y0);
+            const float h01 = __ldg(h + (size_t)x0 * n + y1), h11 = __ldg(h + (size_t)x1 * n + y1);
+            const float top = fmaf(sx.f, h10 - h00, h00), bot = fmaf(sx.f, h11 - h01, h01);
+            acc = fmaf(a.weight[l], fmaf(sy.f, bot - top, top), acc);
+        }
+        a.intensity[i] = a.accumulate ? a.intensity[i] + acc : acc;
+    }
+}
+
+cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t s) {
+    const bool tiled = a.n >= kResTile;
+    if (tiled) {
+        resample_tiled_kernel<<<dim3(a.n / kResTile, a.n / kResTile), 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const size_t total = (size_t)a.n * a.n;
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)sms * 8);
+    resample_kernel<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace scint

@@ -74,15 +74,25 @@ template <int WL> SCINT_DEV size_t strip_index(int y, int x, int n) {
 // phi (radians) -> 64-bit fixed-point turns, P = round(phi 2^32 / 2 pi)
 SCINT_DEV long long phase_fixed(double phi) { return __double2ll_rn(phi * (4294967296.0 / (2.0 * kPi))); }
 
-// exp(i phi s) from P and S = round(s 2^32): the low 64 bits of P S are the
-// fractional turns of phi s times 2^64 (exact reduction mod 2 pi); the angle
-// in [-pi, pi) goes to the hardware sine/cosine (abs. error ~4e-7 there).
-SCINT_DEV float2 unit_phasor(long long P, unsigned long long S) {
-    const unsigned long long prod = (unsigned long long)P * S;
+// exp(i (phi s + add 2^-64 turns)) from P and S = round(s 2^32): the low 64
+// bits of P S are the fractional turns of phi s times 2^64 (exact reduction
+// mod 2 pi); the angle in [-pi, pi) goes to the hardware sine/cosine (abs.
+// error ~4e-7 there).
+SCINT_DEV float2 unit_phasor(long long P, unsigned long long S, unsigned long long add = 0ull) {
+    const unsigned long long prod = (unsigned long long)P * S + add;   // + extra turns 2^-64
     const float ang = (float)(int)(prod >> 32) * (float)(2.0 * kPi * 0x1.0p-32);
     float sn, cs;
     __sincosf(ang, &sn, &cs);
     return make_float2(cs, sn);
+}
+
+// One-FFT mode: chirp |x_1|^2 / (2 R_F^2) with x_1 = (i - n/2) Delta in fixed-point
+// turns, C (i - n/2)^2 mod 2^64 (exact), plus half a turn for odd i: the factor
+// (-1)^i that centres the transform on the optical axis (the sum over
+// (i - n/2)(k - n/2) is the plain DFT times (-1)^(i + k) and a constant).
+SCINT_DEV unsigned long long chirp_turns(unsigned long long C, int i, int n) {
+    const long long d = (long long)i - n / 2;
+    return C * (unsigned long long)(d * d) + ((unsigned long long)(i & 1) << 63);
 }
 
 }  // namespace scint

@@ -193,3 +193,14 @@ def test_screen_check_arguments_rejected_on_host(lib):
 def O_max_annulus(n):
     import oracle as O
     return O.max_annulus(n)
+
+
+def test_conjugate_host_checks(lib):
+    p = S.params(n=64, pixel_km=10.0, r_diff_km=50.0, lambda_nm=500.0)
+    assert lib.scint_conjugate_pixel_km(ctypes.byref(p), 500.0) == pytest.approx(
+        500.0 * 1e-12 * 160.0 * 3.0856775814913673e13 / 640.0, rel=1e-15)
+    import math
+    assert math.isnan(lib.scint_conjugate_pixel_km(ctypes.byref(p.replace(n=100)), 500.0))
+    assert lib.scint_propagate_conjugate(ctypes.byref(p.replace(beta=5.0)), ctypes.c_void_p(16),
+                                         ctypes.c_void_p(16), None, 0, None) == 1
+    assert lib.scint_propagate_conjugate(ctypes.byref(p), None, ctypes.c_void_p(16), None, 0, None) == 1
