@@ -634,15 +634,122 @@ def run_conjugate(args):
         torch.distributed.destroy_process_group()
 
 
+def run_m_sweep(args):
+    """Sect. 4.1 modulation-index sweep through scint_run_batch: R_diff 50..500 km x
+    r_s 0.25..1.5 R_sun (Kolmogorov), 8192^2 screens, K_s passband of 21 wavelengths,
+    disk, m over the fiducial zone.  Metric: pixel-wavelengths/s."""
+    import torch
+    import paper_1301_0514_gb300 as S
+    import paper_1301_0514_gb300.sweeps as SW
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    pts = SW.sweep_points(n=args.sweep_n, seed=20130514 + 9500 + 100000 * rank)
+    lams = SW.KS_BAND_NM
+    m = torch.empty((len(pts), 4), dtype=torch.float64, device=dev)
+    batch = S.batch_items([dict(params=pt.params, m_map=m[i]) for i, pt in enumerate(pts)])
+    ws = torch.empty(S.batch_workspace_bytes(batch, len(lams), args.lanes), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        S.run_batch(batch, lams, n_lanes=args.lanes, workspace=ws)
+
+    step()
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    units = float(args.sweep_n) ** 2 * len(lams) * len(pts)
+    value = units * world / (ms * 1e-3)
+    # serial replay for per-kernel times
+    S.profile_enable(True)
+    pg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(pg, capture_error_mode="relaxed"):
+        S.run_batch(batch, lams, n_lanes=1, workspace=ws)
+    pg.replay()
+    torch.cuda.synchronize(dev)
+    kstats = S.profile_read()
+    S.profile_enable(False)
+    hbm_peak, sm_max_mhz, peak_src = _peaks()
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    dom_name, dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
+    tflops = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
+            "traffic": None, "kernel": dom_name, "timing": "serial one-lane replay, CUDA events per launch"}
+    mm = m.cpu().numpy()
+    rows = SW.summarize(pts, mm[:, 0])
+    host = torch.empty((len(pts), 4), dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    step()
+    host.copy_(m, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        pt = SW.sweep_points(r_diffs=(300.0,), radii_rsun=(0.5,), n=1024, pixels_per_rdiff=0.5)[0]
+        po = O.ScreenParams(**pt.params.as_dict())
+        t0 = time.perf_counter()
+        I = O.smooth_source(O.sum_passband(O.make_screen(po), po, lams), po.pixel_km, po.source_radius_km)
+        O.modulation_index_map(I, po)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1024 * 1024 * len(lams) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one 1024^2 sweep screen x {len(lams)} wavelengths + disk + m, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": "m-sweep pixel-wavelengths/sec (Sect. 4.1, through scint_run_batch)", "value": value,
+                "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": f"{len(pts)} Kolmogorov screens {args.sweep_n}^2, R_diff 50..500 km x "
+                                       f"r_s 0.25..1.5 R_sun, pixel R_diff/3, z0 160 pc, z1 1 kpc, K_s passband "
+                                       f"21 wavelengths, disk, m over the fiducial zone, {args.lanes} lanes",
+                           "l2": "fields of 268 MB per screen and wavelength"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": units * world / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 21 * 8 + 144 * len(pts),
+                        "d2h_bytes_per_step": 32 * len(pts), "ms_per_step": e2e_ms},
+                "gpu_launches": sum(v["launches"] for v in kstats.values()) * args.steps, "clocks": clk,
+                "xparam": [{"m_theory_bin": r[0], "m_mean": r[1], "m_rms": r[2], "patterns": r[3]} for r in rows],
+                "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in kstats.items()}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "screen_check", "conjugate"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "screen_check", "conjugate",
+                                                              "m_sweep"])
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
     ap.add_argument("--conj-n", type=int, default=4096, help="grid of the one-FFT workload")
+    ap.add_argument("--sweep-n", type=int, default=8192, help="grid of the m-sweep workload")
     ap.add_argument("--lanes", type=int, default=4, help="streams the batch is scheduled on (1..8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -650,6 +757,8 @@ def main():
         run_screen_check(args)
     elif args.workload == "conjugate" and args.impl != "reference":
         run_conjugate(args)
+    elif args.workload == "m_sweep" and args.impl != "reference":
+        run_m_sweep(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -274,6 +274,16 @@ int scint_modulation_index(const scint_params* p, const float* intensity, double
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * The fiducial zone that scint_modulation_index uses: pixel index range
+ * [*i0, *i1) on both axes whose centres lie at least L_m + R_ref/2 + R_s from
+ * every border (Sect. 3.2.1, 3.2.3), with lambda = p->lambda_nm; *r_ref_km
+ * (may be NULL) receives R_ref = lambda z / R_diff(lambda).  Host only.
+ * Returns SCINT_EUNSUPPORTED (with [0, N)) when the zone is empty, SCINT_OK
+ * otherwise (also when the taper is off: the whole map).
+ */
+int scint_fiducial_zone(const scint_params* p, int32_t* i0, int32_t* i1, double* r_ref_km);
+
+/*
  * Modulation index of each light curve: out[c] = {m, mean, sigma} for curve c
  * of curves (n_curves x n_samples, row-major).
  *   out   device, 3 * n_curves doubles, written.

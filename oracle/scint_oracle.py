@@ -560,6 +560,40 @@ def modulation_index_map(I, p: ScreenParams):
 
 
 # ---------------------------------------------------------------------------
+# Modulation-index sweeps (Sect. 4.1): Eq. xparam and the number of refractive
+# regions in the fiducial zone
+# ---------------------------------------------------------------------------
+R_SUN_KM = 695700.0
+
+
+def xparam_m(r_diff_km: float, lambda_nm: float, z0_pc: float, source_radius_km: float) -> float:
+    """Eq. xparam, first form: m ~ (R_diff / R_F)^(1/3) (R_ref / (2 pi R_s))^(7/6), with
+    R_F = sqrt(lambda z_0 / 2 pi) and R_ref = lambda z_0 / R_diff (strong, quenched regime)."""
+    lz = lambda_nm * KM_PER_NM * z0_pc * KM_PER_PC
+    r_f = math.sqrt(lz / (2.0 * math.pi))
+    r_ref = lz / r_diff_km
+    return (r_diff_km / r_f) ** (1.0 / 3.0) * (r_ref / (2.0 * math.pi * source_radius_km)) ** (7.0 / 6.0)
+
+
+def xparam_m_numeric(r_diff_km: float, lambda_nm: float, z0_pc: float, r_s_over_z1_rsun_per_10kpc: float,
+                     coefficient: float = 0.035) -> float:
+    """Eq. xparam, numerical form: 0.035 (lambda/1 um) (z_0/1 kpc)^(-1/6) (R_diff/1000 km)^(-5/6)
+    ((r_s/z_1) / (R_sun/10 kpc))^(-7/6)."""
+    return (coefficient * (lambda_nm / 1000.0) * (z0_pc / 1000.0) ** (-1.0 / 6.0)
+            * (r_diff_km / 1000.0) ** (-5.0 / 6.0) * r_s_over_z1_rsun_per_10kpc ** (-7.0 / 6.0))
+
+
+def refractive_regions(p: ScreenParams) -> float:
+    """N_R ~ d^2 / R_ref^2 (Sect. 4.1): R_ref-size regions in the fiducial zone of side d
+    (0 when the zone is empty)."""
+    i0, i1, whole = fiducial_slice(p)
+    if whole and p.margin_km != 0.0:
+        return 0.0
+    d = (i1 - i0) * p.pixel_km
+    return d * d / refraction_radius_km(p, p.lambda_nm) ** 2
+
+
+# ---------------------------------------------------------------------------
 # Whole forward path and its adjoint (gradient of a light-curve misfit)
 # ---------------------------------------------------------------------------
 def forward(p: ScreenParams, lambdas_nm, tracks, n_samples: int, weights=None, phi=None):

@@ -15,6 +15,7 @@ from ._lib import (  # noqa: F401
     conjugate_pixel_km,
     curve_modulation,
     fft_lines,
+    fiducial_zone,
     lib,
     lightcurve,
     lightcurve_adjoint,

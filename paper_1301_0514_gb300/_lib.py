@@ -127,6 +127,8 @@ def lib() -> ctypes.CDLL:
         "scint_batch_workspace_bytes": ([ctypes.POINTER(BatchItem), _i, _i, _i], _sz),
         "scint_run_batch": ([ctypes.POINTER(BatchItem), _i, _vp, _vp, _i, _i, _vp, _sz, _vp], _i),
         "scint_spectrum_rec": ([_P, _vp, _vp, _i, _vp], _i),
+        "scint_fiducial_zone": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(ctypes.c_double)], _i),
         "scint_propagate_conjugate": ([_P, _vp, _vp, _vp, _sz, _vp], _i),
         "scint_sum_passband_conjugate": ([_P, _vp, _vp, _vp, _i, _vp, _i, _vp, _sz, _vp], _i),
         "scint_conjugate_pixel_km": ([_P, ctypes.c_double], ctypes.c_double),
@@ -206,6 +208,15 @@ def sum_passband(p: ScintParams, phi: torch.Tensor, lambdas_nm: Sequence[float],
         len(lam), _dev(out, torch.float32, p.n * p.n, "intensity"), int(bool(accumulate)), wp, wb,
         _stream(stream)))
     return out
+
+
+def fiducial_zone(p: ScintParams):
+    """(i0, i1, r_ref_km, exists): the fiducial pixel range of scint_modulation_index."""
+    i0, i1, rr = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+    rc = lib().scint_fiducial_zone(ctypes.byref(p), ctypes.byref(i0), ctypes.byref(i1), ctypes.byref(rr))
+    if rc not in (SCINT_OK, 5):
+        _check(rc)
+    return i0.value, i1.value, rr.value, rc == SCINT_OK
 
 
 def conjugate_pixel_km(p: ScintParams, lambda_nm: Optional[float] = None) -> float:

@@ -403,6 +403,30 @@ int conj_impl(const scint_params* p, const double* phi, const double* lambdas, c
     return ok();
 }
 
+// Fiducial zone: pixel centres at least L_m + R_ref/2 + R_s from both borders
+// (Sect. 3.2.1, 3.2.3); the whole map when the taper is off or the zone is
+// empty.  Returns 1 when the zone exists (or the taper is off), 0 when empty.
+int fiducial_zone(const scint_params* p, int* i0, int* i1) {
+    const int n = p->n;
+    *i0 = 0;
+    *i1 = n;
+    if (p->margin_km == 0.0) return 1;
+    const double L = screen_len(p);
+    const double m = taper_margin(p, p->lambda_nm) + 0.5 * refraction_radius(p, p->lambda_nm) + p->source_radius_km;
+    int a = -1, b = -1;
+    for (int i = 0; i < n; ++i) {
+        const double x = (i + 0.5) * p->pixel_km;
+        if (x >= m && x <= L - m) {
+            if (a < 0) a = i;
+            b = i;
+        }
+    }
+    if (a < 0) return 0;
+    *i0 = a;
+    *i1 = b + 1;
+    return 1;
+}
+
 SynthArgs synth_args(const scint_params* p) {
     SynthArgs a{};
     const double L = screen_len(p);
@@ -631,29 +655,25 @@ int scint_modulation_index(const scint_params* p, const float* intensity, double
     if (rc) return rc;
     const int n = p->n;
     int i0 = 0, i1 = n;
-    if (p->margin_km != 0.0) {
-        // fiducial zone: pixel centres at least L_m + R_ref/2 + R_s from both borders
-        const double L = screen_len(p);
-        const double m = taper_margin(p, p->lambda_nm) + 0.5 * refraction_radius(p, p->lambda_nm) +
-                         p->source_radius_km;
-        int a = -1, b = -1;
-        for (int i = 0; i < n; ++i) {
-            const double x = (i + 0.5) * p->pixel_km;
-            if (x >= m && x <= L - m) {
-                if (a < 0) a = i;
-                b = i;
-            }
-        }
-        if (a >= 0) {
-            i0 = a;
-            i1 = b + 1;
-        }
-    }
+    fiducial_zone(p, &i0, &i1);
     double* partial = c.take<double>((size_t)kMomentBlocks * 2 * sizeof(double));
     // two kernels: per-block partial sums, then the final reduction
     const int rc2 = launch_timed(K_MOMENTS, 4.0 * (double)(i1 - i0) * (i1 - i0), 0.0, s,
                                  [&] { return launch_map_moments(intensity, n, i0, i1, i0, i1, partial, out, s); }, 2);
     if (rc2) return rc2;
+    return ok();
+}
+
+int scint_fiducial_zone(const scint_params* p, int32_t* i0, int32_t* i1, double* r_ref_km) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!i0 || !i1) return fail(SCINT_EINVAL, "i0 and i1 must be host pointers");
+    int a = 0, b = 0;
+    const int has = fiducial_zone(p, &a, &b);
+    *i0 = a;
+    *i1 = b;
+    if (r_ref_km) *r_ref_km = refraction_radius(p, p->lambda_nm);
+    if (!has) return fail(SCINT_EUNSUPPORTED, "the fiducial zone is empty (margin exceeds half the screen)");
     return ok();
 }
 
