@@ -594,6 +594,37 @@ def refractive_regions(p: ScreenParams) -> float:
 
 
 # ---------------------------------------------------------------------------
+# Light-curve time analysis (Sect. 5): power spectra and the decorrelation of
+# two telescopes
+# ---------------------------------------------------------------------------
+def periodogram(curves):
+    """One-sided periodogram of each light curve, P_k = |sum_s (c_s - mean c) e^{-2 pi i k s / n}|^2 / n
+    for k = 0..n/2 (the time power spectrum whose slope breaks near 1/t_ref, Sect. 5)."""
+    c = np.atleast_2d(np.asarray(curves, dtype=np.float64))
+    x = c - c.mean(axis=1, keepdims=True)
+    return np.abs(np.fft.rfft(x, axis=1)) ** 2 / c.shape[1]
+
+
+def pearson(a, b):
+    """Correlation coefficient of light curves a and b (rows): how far two telescopes' curves
+    decorrelate (Sect. 5)."""
+    a = np.atleast_2d(np.asarray(a, dtype=np.float64))
+    b = np.atleast_2d(np.asarray(b, dtype=np.float64))
+    da = a - a.mean(axis=1, keepdims=True)
+    db = b - b.mean(axis=1, keepdims=True)
+    return (da * db).sum(axis=1) / np.sqrt((da * da).sum(axis=1) * (db * db).sum(axis=1))
+
+
+def parallel_tracks(track, separations_px):
+    """Tracks parallel to `track` (x0, y0, theta, ds), offset perpendicularly by each separation
+    (pixels): the sections two telescopes a distance apart sweep (Sect. 5)."""
+    x0, y0, th, ds = track
+    sep = np.asarray(separations_px, dtype=np.float64)
+    return np.stack([x0 - sep * math.sin(th), y0 + sep * math.cos(th), np.full(sep.shape, th),
+                     np.full(sep.shape, ds)], axis=1)
+
+
+# ---------------------------------------------------------------------------
 # Whole forward path and its adjoint (gradient of a light-curve misfit)
 # ---------------------------------------------------------------------------
 def forward(p: ScreenParams, lambdas_nm, tracks, n_samples: int, weights=None, phi=None):
