@@ -739,6 +739,119 @@ def run_m_sweep(args):
         torch.distributed.destroy_process_group()
 
 
+def run_timeseries(args):
+    """Sect. 5 light-curve analysis on one 8192^2 disk-source pattern: curves along
+    1024 base tracks and their parallels at 6 separations (0.05..4 R_ref), periodograms
+    of every curve, correlation of each base curve with its parallels.
+    Metric: curve samples analysed per second."""
+    import torch
+    import paper_1301_0514_gb300 as S
+    import paper_1301_0514_gb300.timeseries as TS
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    n, pix, ns, nb = 8192, 10.0, 4096, 1024
+    r_ref = 550.0 * 1e-12 * 160.0 * 3.0856775814913673e13 / 300.0
+    p = S.params(n=n, pixel_km=pix, r_diff_km=300.0, lambda_nm=550.0, source_radius_km=0.5 * r_ref,
+                 seed=20130514 + 9600 + 100000 * rank)
+    I = S.propagate(p, S.make_screen(p))
+    S.smooth_source(p, I)
+    rng = np.random.default_rng(20130514 + 9601 + rank)
+    base = np.stack([rng.uniform(0, n, nb), rng.uniform(0, n, nb), rng.uniform(0, np.pi, nb), np.ones(nb)], axis=1)
+    sep = np.array([0.0, 0.05, 0.2, 1.0, 2.5, 4.0]) * r_ref / pix
+    tracks = np.concatenate([TS.parallel_tracks(tr, sep) for tr in base], axis=0)
+    nc = len(tracks)
+    curves = torch.empty((nc, ns), dtype=torch.float32, device=dev)
+    power = torch.empty((nc, ns // 2 + 1), dtype=torch.float32, device=dev)
+    r = torch.empty((nb, len(sep)), dtype=torch.float64, device=dev)
+    ws = torch.empty(8 * ns + 256, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        S.lightcurve(p, I, tracks, ns, out=curves)
+        S.curve_power_spectrum(curves, out=power, workspace=ws)
+        S.curve_correlation(curves, curves, out=r.view(-1), a_rows=nb, a_stride=len(sep) * ns)
+
+    step()
+    torch.cuda.synchronize(dev)
+    S.profile_enable(True)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    kstats = S.profile_read()
+    S.profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    units = float(nc) * ns
+    value = units * world / (ms * 1e-3)
+    hbm_peak, sm_max_mhz, peak_src = _peaks()
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    ps = kstats["power_spectrum"]
+    tflops = ps["flops"] / (ps["total_ms"] * 1e-3) / 1e12
+    gbs = ps["bytes"] / (ps["total_ms"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+            "traffic": None, "kernel": "power_spectrum", "fft_tflops": tflops, "alu_frac": tflops / alu_peak,
+            "peak_source": f"hbm {peak_src} (MEASURED_PEAKS.json)",
+            "note": "per-launch events inside the replayed graph"}
+    rm = r.cpu().numpy().mean(axis=0)
+    host_r = torch.empty_like(r, device="cpu").pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    step()
+    host_r.copy_(r, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        hc = curves.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        O.periodogram(hc)
+        for i in range(nb):
+            O.pearson(np.repeat(hc[6 * i:6 * i + 1], 6, 0), hc[6 * i:6 * i + 6])
+        dt = time.perf_counter() - t0
+        cpu = {"value": hc.size / dt, "unit": "curve samples/s", "cores": 1, "kind": "oracle",
+               "sample": f"periodograms and correlations of {hc.shape[0]} of the {nc} curves, {dt:.2f} s"}
+    if rank == 0:
+        line = {"metric": "light-curve samples analysed/sec (Sect. 5: periodograms + two-telescope correlations)",
+                "value": value, "unit": "curve samples/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": f"one {n}^2 disk-source pattern (R_diff 300 km, R_s = R_ref/2 at 550 nm), "
+                                       f"{nb} tracks x 6 parallels (0..4 R_ref) x {ns} samples",
+                           "l2": "curves 100 MB, the map 268 MB"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": units * world / (e2e_ms * 1e-3), "unit": "curve samples/s",
+                        "h2d_bytes_per_step": int(tracks.nbytes), "d2h_bytes_per_step": int(r.numel() * 8),
+                        "ms_per_step": e2e_ms},
+                "gpu_launches": sum(v["launches"] for v in kstats.values()) * args.steps, "clocks": clk,
+                "mean_correlation_vs_separation_in_R_ref": {f"{d:.2f}": float(v) for d, v in
+                                                           zip(sep * pix / r_ref, rm)},
+                "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in kstats.items()}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -746,7 +859,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "screen_check", "conjugate",
-                                                              "m_sweep"])
+                                                              "m_sweep", "timeseries"])
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
     ap.add_argument("--conj-n", type=int, default=4096, help="grid of the one-FFT workload")
     ap.add_argument("--sweep-n", type=int, default=8192, help="grid of the m-sweep workload")
@@ -759,6 +872,8 @@ def main():
         run_conjugate(args)
     elif args.workload == "m_sweep" and args.impl != "reference":
         run_m_sweep(args)
+    elif args.workload == "timeseries" and args.impl != "reference":
+        run_timeseries(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -292,6 +292,33 @@ int scint_curve_modulation(const float* curves, int n_curves, int n_samples,
                            double* out, void* stream);
 
 /*
+ * Time power spectrum of light curves (Sect. 5: its slope breaks near 1/t_ref,
+ * t_ref = R_ref / V_T), the periodogram
+ *   power[c][k] = |sum_s (c_s - mean c) exp(-2 pi i k s / n)|^2 / n,  k = 0..n/2,
+ * with n = n_samples a power of two in [SCINT_MIN_N, 8192].  The mean is
+ * removed in FP64 before the FP32 transform.
+ *   curves   device, n_curves x n_samples floats, read.
+ *   power    device, n_curves x (n_samples/2 + 1) floats, written.
+ * Needs workspace (8 n_samples bytes).
+ */
+int scint_curve_power_spectrum(const float* curves, int n_curves, int n_samples, float* power,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Correlation coefficient of pairs of light curves (Sect. 5: two telescopes a
+ * distance apart see decorrelated curves once it exceeds 2 max(R_ref, R_s)):
+ *   r[i] = sum (a_j - mean a_j)(b_i - mean b_i) / sqrt(sum (a_j - ..)^2 sum (b_i - ..)^2),
+ * FP64, where b_i is row i of b and a_j row j = i / (n_pairs / a_rows) of a: the
+ * pairs come in a_rows equal groups, each against one curve of a (a reference
+ * telescope against its parallels).
+ *   a  device, a_rows rows of n_samples floats, a_stride floats apart (ignored
+ *      when a_rows == 1);  b  device, n_pairs x n_samples floats;
+ *   r  device, n_pairs doubles, written.   a_rows must divide n_pairs.
+ */
+int scint_curve_correlation(const float* a, int a_rows, int64_t a_stride, const float* b, int n_pairs,
+                            int n_samples, double* r, void* stream);
+
+/*
  * Batch of independent screens, each run through the whole forward path of the
  * paper's polychromatic extended-source simulation (Sect. 3.1 synthesis,
  * Sect. 3.2 propagation with taper, Sect. 3.2.4 passband co-addition,

@@ -13,7 +13,9 @@ from ._lib import (  # noqa: F401
     ScintError,
     ScintParams,
     conjugate_pixel_km,
+    curve_correlation,
     curve_modulation,
+    curve_power_spectrum,
     fft_lines,
     fiducial_zone,
     lib,

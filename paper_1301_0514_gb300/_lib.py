@@ -127,6 +127,8 @@ def lib() -> ctypes.CDLL:
         "scint_batch_workspace_bytes": ([ctypes.POINTER(BatchItem), _i, _i, _i], _sz),
         "scint_run_batch": ([ctypes.POINTER(BatchItem), _i, _vp, _vp, _i, _i, _vp, _sz, _vp], _i),
         "scint_spectrum_rec": ([_P, _vp, _vp, _i, _vp], _i),
+        "scint_curve_power_spectrum": ([_vp, _i, _i, _vp, _vp, _sz, _vp], _i),
+        "scint_curve_correlation": ([_vp, _i, ctypes.c_int64, _vp, _i, _i, _vp, _vp], _i),
         "scint_fiducial_zone": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                  ctypes.POINTER(ctypes.c_double)], _i),
         "scint_propagate_conjugate": ([_P, _vp, _vp, _vp, _sz, _vp], _i),
@@ -207,6 +209,43 @@ def sum_passband(p: ScintParams, phi: torch.Tensor, lambdas_nm: Sequence[float],
         lam.ctypes.data_as(ctypes.c_void_p), None if w is None else w.ctypes.data_as(ctypes.c_void_p),
         len(lam), _dev(out, torch.float32, p.n * p.n, "intensity"), int(bool(accumulate)), wp, wb,
         _stream(stream)))
+    return out
+
+
+def curve_power_spectrum(curves: torch.Tensor, out: Optional[torch.Tensor] = None, workspace=None,
+                         stream=None) -> torch.Tensor:
+    """Periodogram (n_curves, n/2 + 1) of light curves (n_curves, n), mean removed (Sect. 5)."""
+    nc, ns = curves.shape
+    if out is None:
+        out = torch.empty((nc, ns // 2 + 1), dtype=torch.float32, device=curves.device)
+    if workspace is None:
+        wp, wb = None, 0
+    else:
+        wp, wb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+    _check(lib().scint_curve_power_spectrum(_dev(curves, torch.float32, nc * ns, "curves"), nc, ns,
+                                            _dev(out, torch.float32, nc * (ns // 2 + 1), "power"), wp, wb,
+                                            _stream(stream)))
+    return out
+
+
+def curve_correlation(a: torch.Tensor, b: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None,
+                      a_rows: Optional[int] = None, a_stride: Optional[int] = None) -> torch.Tensor:
+    """Correlation coefficient of row i of b with row i // (n_pairs // a_rows) of a (Sect. 5).
+    By default a's rows are contiguous and a_rows is its row count; a strided view of a
+    larger tensor can be given with a_rows and a_stride (in floats)."""
+    b2 = b.reshape(-1, b.shape[-1])
+    n_pairs, ns = b2.shape
+    if a_rows is None:
+        a2 = a.reshape(-1, a.shape[-1])
+        _dev(a2, torch.float32, a2.numel(), "a")
+        a_rows, a_stride = a2.shape[0], ns
+    elif not (a.is_cuda and a.dtype == torch.float32):
+        raise ValueError("a must be a float32 CUDA tensor")
+    if out is None:
+        out = torch.empty(n_pairs, dtype=torch.float64, device=b.device)
+    _check(lib().scint_curve_correlation(ctypes.c_void_p(a.data_ptr()), int(a_rows), int(a_stride),
+                                         _dev(b2, torch.float32, b2.numel(), "b"), n_pairs, ns,
+                                         _dev(out, torch.float64, n_pairs, "r"), _stream(stream)))
     return out
 
 

@@ -177,13 +177,13 @@ int resolve_ws(void* ws, size_t bytes, size_t need, cudaStream_t s, Carver* c) {
 enum KClass {
     K_TWIDDLES, K_SYNTH_ROWS, K_SYNTH_COLS, K_PROP_TABLES, K_PROP_ROWS, K_PROP_COLS,
     K_SMOOTH_FWD, K_SMOOTH_ROWS, K_SMOOTH_INV, K_LIGHTCURVE, K_MOMENTS,
-    K_LC_ADJ, K_ADJ_COLS, K_ADJ_ROWS, K_DOT, K_RADIAL, K_CREC, K_CONJ_ROWS, K_CONJ_COLS, K_RESAMPLE, K_COUNT
+    K_LC_ADJ, K_ADJ_COLS, K_ADJ_ROWS, K_DOT, K_RADIAL, K_CREC, K_CONJ_ROWS, K_CONJ_COLS, K_RESAMPLE, K_POWER, K_CORR, K_COUNT
 };
 const char* const kClassName[K_COUNT] = {
     "twiddles", "synth_rows", "synth_cols", "prop_tables", "prop_rows", "prop_cols",
     "smooth_fwd_cols", "smooth_rows", "smooth_inv_cols", "lightcurve", "moments",
     "lightcurve_adjoint", "adj_cols", "adj_rows", "dot", "radial_spectrum", "structure_rec",
-    "conj_rows", "conj_cols", "resample"};
+    "conj_rows", "conj_cols", "resample", "power_spectrum", "correlation"};
 
 struct ProfRec {
     int cls;
@@ -661,6 +661,37 @@ int scint_modulation_index(const scint_params* p, const float* intensity, double
     const int rc2 = launch_timed(K_MOMENTS, 4.0 * (double)(i1 - i0) * (i1 - i0), 0.0, s,
                                  [&] { return launch_map_moments(intensity, n, i0, i1, i0, i1, partial, out, s); }, 2);
     if (rc2) return rc2;
+    return ok();
+}
+
+int scint_curve_power_spectrum(const float* curves, int n_curves, int n_samples, float* power, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+    if (n_curves < 0) return fail(SCINT_EINVAL, "n_curves must be >= 0");
+    if (!pow2(n_samples) || n_samples < SCINT_MIN_N || n_samples > 8192)
+        return fail(SCINT_EINVAL, "n_samples=%d must be a power of two in [%d, 8192]", n_samples, SCINT_MIN_N);
+    if (n_curves == 0) return ok();
+    if (!curves || !power) return fail(SCINT_EINVAL, "curves and power must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Carver c{};
+    int rc = resolve_ws(workspace, workspace_bytes, up((size_t)n_samples * 8), s, &c);
+    if (rc) return rc;
+    float2* tw = c.take<float2>((size_t)n_samples * 8);
+    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n_samples, 0.0, s, launch_twiddles32(tw, n_samples, s));
+    SCINT_LAUNCH(K_POWER, 4.0 * n_curves * (double)n_samples + 4.0 * n_curves * (n_samples / 2 + 1),
+                 n_curves * fft_flops(n_samples), s, launch_power_spectrum(curves, n_curves, n_samples, power, tw, s));
+    return ok();
+}
+
+int scint_curve_correlation(const float* a, int a_rows, int64_t a_stride, const float* b, int n_pairs,
+                            int n_samples, double* r, void* stream) {
+    if (n_pairs < 0 || n_samples < 2) return fail(SCINT_EINVAL, "need n_pairs >= 0 and n_samples >= 2");
+    if (n_pairs == 0) return ok();
+    if (a_rows < 1 || n_pairs % a_rows) return fail(SCINT_EINVAL, "a_rows=%d must divide n_pairs=%d", a_rows, n_pairs);
+    if (a_rows > 1 && a_stride < n_samples) return fail(SCINT_EINVAL, "a_stride must be >= n_samples");
+    if (!a || !b || !r) return fail(SCINT_EINVAL, "a, b and r must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SCINT_LAUNCH(K_CORR, 4.0 * (double)n_samples * (n_pairs + a_rows) + 8.0 * n_pairs, 0.0, s,
+                 launch_correlation(a, a_rows, a_stride, b, n_pairs, n_samples, r, s));
     return ok();
 }
 

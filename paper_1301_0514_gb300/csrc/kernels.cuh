@@ -182,4 +182,15 @@ struct BisectState {
 cudaError_t launch_crec(const CrecArgs& a, const double* r_km, int n_r, double* d, cudaStream_t s);
 cudaError_t launch_bisect(const CrecArgs& a, BisectState* st, int iterations, double* out, cudaStream_t s);
 
+
+// ---- light-curve time analysis (timeseries.cu) -------------------------------------
+// Periodogram |DFT(c - mean c)|^2 / n, k = 0..n/2, of n_curves curves of n samples
+// (n a power of two up to 8192); tw: FP32 twiddles of n.
+cudaError_t launch_power_spectrum(const float* curves, int n_curves, int n, float* power, const float2* tw,
+                                  cudaStream_t s);
+// Pearson correlation of row i of b with row i / (n_pairs / a_rows) of a (rows of a
+// a_stride floats apart); a_rows divides n_pairs.
+cudaError_t launch_correlation(const float* a, int a_rows, long long a_stride, const float* b, int n_pairs, int n,
+                               double* r, cudaStream_t s);
+
 }  // namespace scint

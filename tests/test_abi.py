@@ -204,3 +204,16 @@ def test_conjugate_host_checks(lib):
     assert lib.scint_propagate_conjugate(ctypes.byref(p.replace(beta=5.0)), ctypes.c_void_p(16),
                                          ctypes.c_void_p(16), None, 0, None) == 1
     assert lib.scint_propagate_conjugate(ctypes.byref(p), None, ctypes.c_void_p(16), None, 0, None) == 1
+
+
+def test_timeseries_host_checks(lib):
+    assert lib.scint_curve_power_spectrum(ctypes.c_void_p(16), 3, 1000, ctypes.c_void_p(16), None, 0, None) == 1
+    assert "power of two" in lib.scint_last_error().decode()
+    assert lib.scint_curve_power_spectrum(ctypes.c_void_p(16), 3, 16384, ctypes.c_void_p(16), None, 0, None) == 1
+    assert lib.scint_curve_power_spectrum(None, 0, 256, None, None, 0, None) == 0      # nothing to do
+    assert lib.scint_curve_correlation(ctypes.c_void_p(16), 2, 100, ctypes.c_void_p(16), 3, 100,
+                                       ctypes.c_void_p(16), None) == 1          # 2 does not divide 3
+    assert lib.scint_curve_correlation(ctypes.c_void_p(16), 3, 50, ctypes.c_void_p(16), 3, 100,
+                                       ctypes.c_void_p(16), None) == 1          # rows of a overlap
+    assert lib.scint_curve_correlation(ctypes.c_void_p(16), 1, 0, ctypes.c_void_p(16), 3, 1,
+                                       ctypes.c_void_p(16), None) == 1
