@@ -79,6 +79,17 @@ def _workload(name: str, rank: int):
     return items, desc
 
 
+def _max_over_ranks(ms: float, world: int, device) -> float:
+    """The step time of the job: the slowest rank's (all-reduce MAX; identity on one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _kernel_source_hash(files):
     """Hash of the CUDA sources a kernel is built from (a traffic record is void once they change)."""
     h = hashlib.sha256()
@@ -276,11 +287,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(ms, world, dev)
     value = units * world / (ms * 1e-3)
 
     # Per-kernel times: concurrent lanes share the SMs, so an event pair around a
@@ -441,10 +448,7 @@ def run_screen_check(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(ms, world, dev)
     units = float(n) * n
     value = units * world / (ms * 1e-3)
 
@@ -576,10 +580,7 @@ def run_conjugate(args):
     ms, kstats = timed(True)
     clk = clocks.stop()
     ms_tf, kstats_tf = timed(False)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(ms, world, dev)
     value = units * world / (ms * 1e-3)
     hbm_peak, sm_max_mhz, peak_src = _peaks()
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
@@ -678,10 +679,7 @@ def run_m_sweep(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(ms, world, dev)
     units = float(args.sweep_n) ** 2 * len(lams) * len(pts)
     value = units * world / (ms * 1e-3)
     # serial replay for per-kernel times
@@ -797,10 +795,7 @@ def run_timeseries(args):
     kstats = S.profile_read()
     S.profile_enable(False)
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(ms, world, dev)
     units = float(nc) * ns
     value = units * world / (ms * 1e-3)
     hbm_peak, sm_max_mhz, peak_src = _peaks()
