@@ -254,6 +254,17 @@ int check_passband(const scint_params* p, const double* lambdas, const double* w
     return SCINT_OK;
 }
 
+// Per-wavelength scalars of the propagation passes (slot i of a group).
+void fill_lambda(LambdaSet& ls, int i, const scint_params* p, double lam, double w) {
+    const double L = screen_len(p);
+    ls.scale_fx[i] = (uint64_t)std::llround(p->lambda_ref_nm / lam * 4294967296.0);
+    ls.weight[i] = (float)w;
+    ls.scale[i] = (float)(p->lambda_ref_nm / lam);
+    // H_x = exp(-2 pi i c m^2), c = lambda z / (2 L^2): -frac(c) in 0.64 fixed point (52 bits kept)
+    const double c = lz_km2(lam, p->z_pc) / (2.0 * L * L);
+    ls.h_fx[i] = 0ull - ((uint64_t)std::llround(std::ldexp(c - std::floor(c), 52)) << 12);
+}
+
 // Propagate one wavelength group [l0, l0 + g) into the intensity map.
 int run_group(const scint_params* p, const double* phi, const double* lam, const double* wts,
               int l0, int g, float* intensity, int accumulate, Carver& c, const float2* tw,
@@ -273,9 +284,7 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
         const double l = lam[l0 + i];
         ta.lz_over_2L2[i] = lz_km2(l, p->z_pc) / (2.0 * L * L);
         ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
-        pa.lam.scale_fx[i] = (uint64_t)std::llround(p->lambda_ref_nm / l * 4294967296.0);
-        pa.lam.weight[i] = (float)wts[l0 + i];
-        pa.lam.scale[i] = (float)(p->lambda_ref_nm / l);
+        fill_lambda(pa.lam, i, p, l, wts[l0 + i]);
     }
     Carver cg = c;   // group buffers restart at the same offset for every group
     ta.h = cg.take<float2>((size_t)g * n * 8);
@@ -369,9 +378,7 @@ int conj_impl(const scint_params* p, const double* phi, const double* lambdas, c
             const double l = lambdas[l0 + i], lz = lz_km2(l, p->z_pc);
             ta.lz_over_2L2[i] = lz / (2.0 * screen_len(p) * screen_len(p));   // H table (unused here)
             ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
-            pa.lam.scale_fx[i] = (uint64_t)std::llround(p->lambda_ref_nm / l * 4294967296.0);
-            pa.lam.weight[i] = (float)w[l0 + i];
-            pa.lam.scale[i] = (float)(p->lambda_ref_nm / l);
+            fill_lambda(pa.lam, i, p, l, w[l0 + i]);
             // chirp turns per pixel^2, Delta^2 / (2 lambda z), reduced mod 1 and in 0.64 fixed point
             const double c_turns = d1 * d1 / (2.0 * lz);
             const double frac = c_turns - std::floor(c_turns);
@@ -799,9 +806,7 @@ int scint_lightcurve_adjoint(const scint_params* p, const double* phi, const dou
             const double l = lambdas_nm[l0 + i];
             ta.lz_over_2L2[i] = lz_km2(l, p->z_pc) / (2.0 * L * L);
             ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
-            pa.lam.scale_fx[i] = (uint64_t)std::llround(p->lambda_ref_nm / l * 4294967296.0);
-            pa.lam.weight[i] = (float)w[l0 + i];
-            pa.lam.scale[i] = (float)(p->lambda_ref_nm / l);
+            fill_lambda(pa.lam, i, p, l, w[l0 + i]);
         }
         Carver cg = cp;
         ta.h = cg.take<float2>((size_t)gg * n * 8);

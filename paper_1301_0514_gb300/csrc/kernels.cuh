@@ -52,6 +52,7 @@ cudaError_t launch_noise_spectrum(const SynthArgs& a, double2* F, cudaStream_t s
 struct LambdaSet {
     int count;                       // wavelengths in this group
     uint64_t scale_fx[kMaxLambda];   // round(lambda_ref/lambda * 2^32)
+    uint64_t h_fx[kMaxLambda];       // frac(-lambda z / (2 L^2)) 2^64: H_x phase turns per index^2
     float weight[kMaxLambda];        // passband weight w_l
     float scale[kMaxLambda];         // s = lambda_ref/lambda (the adjoint's d(phase)/d(phi))
 };

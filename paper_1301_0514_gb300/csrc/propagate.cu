@@ -6,7 +6,9 @@
 // one along y.  Each 1D propagator is FFT -> multiply -> inverse FFT on a line
 // held in registers and shared memory, so a wavelength costs two HBM passes:
 //   row pass:    phi (read once per wavelength group) -> exact phase reduction
-//                -> sin/cos -> taper -> FFT_x -> H_x/N -> IFFT_x -> field (write)
+//                -> sin/cos -> taper -> FFT_x -> H_x/N -> IFFT_x -> field (write);
+//                H_x comes from a scalar (no table load), its phase exact in
+//                fixed-point turns like the screen phase
 //   column pass: field (read) -> FFT_y -> H_y/N -> IFFT_y -> w |A|^2, summed over
 //                the group in registers -> intensity (one write per group)
 //
@@ -83,8 +85,8 @@ prop_rows_kernel(PropArgs a) {
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         const unsigned long long S = a.lam.scale_fx[l];
+        // the taper from its table; H_x from a scalar (its phase exact in fixed-point turns)
         const float* sf = a.sf + (size_t)l * N;
-        const float2* h = a.h + (size_t)l * N;
         const float sfy = sf[y];
         float2 v[E];
         if constexpr (CONJ) {
@@ -101,8 +103,9 @@ prop_rows_kernel(PropArgs a) {
         if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
         else fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, twp);
         if constexpr (!CONJ) {
+            const unsigned long long hc = a.lam.h_fx[l];
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
+            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
             if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
             else fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, twp);
         }
@@ -120,22 +123,23 @@ prop_cols_kernel(PropArgs a) {
     using Pl = FftPlan<N, kColEPT>;
     constexpr int CS = pcs<N>(), TWM = pcol_twm<N>();
     constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
-    constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
+    constexpr int TL = T / CS, BUFL = Pl::BUF / CS;
     extern __shared__ float2 smem32[];
     const int w = threadIdx.x % W, tl = threadIdx.x / W;
     const int t = line_rank<CS>() * TL + tl;
     const int x0 = (blockIdx.x / CS) * W;    // first column of the block: strip x0 / WL, offset x0 % WL
     const int x = x0 + w;
     float2* buf = smem32 + w;     // W lines interleaved: element e of line w at pad16(e) * W + w
-    // passband accumulator of this thread's pixels (own entries only)
-    float* acc = reinterpret_cast<float*>(smem32 + W * BUFL) + w * NL + tl;
-    float2* tws = smem32 + W * BUFL + (W * NL) / 2;   // shared twiddle table (after acc)
+    // passband accumulator of this thread's pixels, in registers (a shared-memory
+    // copy would add a read-modify-write per wavelength to the busiest queue)
+    float acc[E];
+    float2* tws = smem32 + W * BUFL;   // shared twiddle table (after the line buffers)
     const float2* twp = TWM == 1 ? tws : a.tw;
     TwiddleRegs<float2, N, kColEPT> tr;
     if constexpr (TWM == 2) tr.load(a.tw, t);
     else if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
-    for (int m = 0; m < E; ++m) acc[m * TL] = 0.0f;
+    for (int m = 0; m < E; ++m) acc[m] = 0.0f;
     line_sync<CS>();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
@@ -152,7 +156,7 @@ prop_cols_kernel(PropArgs a) {
             if (a.conj.direct) {
                 const float wn = a.lam.weight[l] * nrm;
 #pragma unroll
-                for (int m = 0; m < E; ++m) acc[m * TL] = fmaf(wn, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m * TL]);
+                for (int m = 0; m < E; ++m) acc[m] = fmaf(wn, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m]);
             } else {
                 // column-major: this column's values are contiguous, so the stores coalesce
                 float* pat = a.conj.pattern + (size_t)l * N * N + (size_t)x * N;
@@ -168,7 +172,7 @@ prop_cols_kernel(PropArgs a) {
         }
         const float wl = a.lam.weight[l];
 #pragma unroll
-        for (int m = 0; m < E; ++m) acc[m * TL] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m * TL]);
+        for (int m = 0; m < E; ++m) acc[m] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m]);
     }
     if constexpr (CONJ) {
         if (!a.conj.direct) {
@@ -179,7 +183,7 @@ prop_cols_kernel(PropArgs a) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float* o = a.intensity + (size_t)(t + m * T) * N + x;
-        *o = a.accumulate ? *o + acc[m * TL] : acc[m * TL];
+        *o = a.accumulate ? *o + acc[m] : acc[m];
     }
     if constexpr (CS == 2) line_sync<CS>();
 }

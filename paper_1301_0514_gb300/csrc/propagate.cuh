@@ -47,9 +47,9 @@ template <int N> constexpr size_t prow_smem() {
     return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) / pcs<N>() +
            ptws_bytes<N>(prow_twm<N>());
 }
-// column pass: line buffers, accumulators and (when it fits) the twiddle table
+// column pass: line buffers and (when it fits) the twiddle table
 template <int N> __host__ __device__ constexpr size_t pcol_base_bytes() {
-    return (size_t)pcol_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(float)) / pcs<N>();
+    return (size_t)pcol_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / pcs<N>();
 }
 template <int N> __host__ __device__ constexpr int pcol_twm() {
     return pcs<N>() == 2 ? 0
@@ -84,6 +84,13 @@ SCINT_DEV float2 unit_phasor(long long P, unsigned long long S, unsigned long lo
     float sn, cs;
     __sincosf(ang, &sn, &cs);
     return make_float2(cs, sn);
+}
+
+// H_x(k)/n = exp(-i pi lambda z k^2)/n at FFT index i, from C = frac(-lambda z / 2L^2) 2^64:
+// the phase C m^2 mod 2^64 (m the signed frequency index) is exact in fixed-point turns.
+SCINT_DEV float2 transfer_at(unsigned long long C, int i, int n) {
+    const long long m = sfreq(i, n);
+    return unit_phasor(0, 0ull, C * (unsigned long long)(m * m)) * (1.0f / n);
 }
 
 // One-FFT mode: chirp |x_1|^2 / (2 R_F^2) with x_1 = (i - n/2) Delta in fixed-point
