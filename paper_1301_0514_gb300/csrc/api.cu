@@ -532,11 +532,12 @@ int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_
     rc = resolve_ws(workspace, workspace_bytes, ws_synth(p->n), s, &c);
     if (rc) return rc;
     SynthArgs a = synth_args(p);
-    a.tw = c.take<double2>((size_t)p->n * 16);
-    a.work = c.take<double2>((size_t)(p->n / 2 + 1) * p->n * 16);
+    dfc* tw = c.take<dfc>((size_t)p->n * 16);
+    a.tw = tw;
+    a.work = c.take<dfc>((size_t)(p->n / 2 + 1) * p->n * 16);
     a.phi = phi;
     const double nn = (double)p->n * p->n;
-    SCINT_LAUNCH(K_TWIDDLES, 16.0 * p->n, 0.0, s, launch_twiddles64(const_cast<double2*>(a.tw), p->n, s));
+    SCINT_LAUNCH(K_TWIDDLES, 16.0 * p->n, 0.0, s, launch_twiddles_df(tw, p->n, s));
     // rows: the noise is generated in registers, the half-transformed field is written
     const double half = (double)(p->n / 2 + 1) * p->n * 16.0;
     // rows: the noise is generated in registers, rows 0..n/2 of the x-transformed field are written

@@ -55,6 +55,57 @@ template <> SCINT_DEV float2 make_c<float2>(double re, double im) { return make_
 template <> SCINT_DEV double2 make_c<double2>(double re, double im) { return make_double2(re, im); }
 
 // ---------------------------------------------------------------------------
+// Double-float arithmetic: a real is the unevaluated sum hi + lo of two FP32
+// numbers with |lo| <= ulp(hi)/2, about 44 significant bits.  Sums use Knuth's
+// two-sum and products Dekker's exact product (here through a fused multiply-
+// add), the error-free transformations of the double-double literature (Hida,
+// Li & Bailey 2001) on FP32 pairs.  The addition is the short form, whose error
+// is bounded relative to the operands (not to the result), which is the
+// normwise accuracy an FFT needs.  On GB300 these run on the FP32 pipes, which
+// are 64 times wider than the FP64 pipe.
+// ---------------------------------------------------------------------------
+struct dfl {
+    float hi, lo;
+    dfl() = default;
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr explicit dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+};
+SCINT_DEV dfl two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return dfl(s, (a - (s - bb)) + (b - bb));
+}
+SCINT_DEV dfl fast_two_sum(float a, float b) {   // requires |a| >= |b| or a == 0
+    const float s = a + b;
+    return dfl(s, b - (s - a));
+}
+SCINT_DEV dfl operator+(dfl a, dfl b) {
+    const dfl s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+SCINT_DEV dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+SCINT_DEV dfl operator-(dfl a, dfl b) { return a + (-b); }
+SCINT_DEV dfl operator*(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
+    return fast_two_sum(p, e);
+}
+SCINT_DEV double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+// complex double-float (x real, y imaginary), 16 bytes like double2
+struct __align__(16) dfc {
+    dfl x, y;
+};
+SCINT_DEV dfc operator+(dfc a, dfc b) { return dfc{a.x + b.x, a.y + b.y}; }
+SCINT_DEV dfc operator-(dfc a, dfc b) { return dfc{a.x - b.x, a.y - b.y}; }
+SCINT_DEV dfc cmul(dfc a, dfc b) { return dfc{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+SCINT_DEV dfc cmulc(dfc a, dfc b) { return dfc{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }
+SCINT_DEV dfc conjc(dfc a) { return dfc{a.x, -a.y}; }
+template <int DIR> SCINT_DEV dfc mul_i(dfc a) { return DIR > 0 ? dfc{-a.y, a.x} : dfc{a.y, -a.x}; }
+template <> struct real_of<dfc> { using type = dfl; };
+template <> SCINT_DEV dfc make_c<dfc>(double re, double im) { return dfc{dfl(re), dfl(im)}; }
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11)
 // ---------------------------------------------------------------------------
 struct u32x4 { uint32_t x, y, z, w; };

@@ -1,5 +1,5 @@
 // Shared-memory Stockham FFT for one line of N points held by a team of
-// threads (FP32 float2 or FP64 double2).
+// threads (FP32 float2, FP64 double2 or double-float dfc).
 //
 // A team of T = N/E threads (E = 16 or 32) transforms one line; thread t holds the E values at
 // positions t + m*T (m = 0..E-1) in registers, both on entry and on exit (the
@@ -183,6 +183,11 @@ SCINT_DEV int pad16(int a) { return a + (a >> 4); }
 
 template <typename C>
 SCINT_DEV C ld_tw(const C* __restrict__ p) { return __ldg(p); }
+template <>
+SCINT_DEV dfc ld_tw<dfc>(const dfc* __restrict__ p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return dfc{dfl(v.x, v.y), dfl(v.z, v.w)};
+}
 
 
 // LW: lane width of the buffer.  Element e of the line sits at buf[pad16(e) * LW]

@@ -36,10 +36,11 @@ struct SynthArgs {
     double neg_beta_4;   // -beta/4
     float amp32, neg_beta_4_32;   // the same in FP32 for the high-frequency bins
     double out_scale;    // sqrt(2) / L^2
-    const double2* tw;   // FP64 twiddles for n
-    double2* work;       // (n/2 + 1) x n complex128, row-major: rows ky = 0..n/2 after the x transform
+    const dfc* tw;       // double-float twiddles for n
+    dfc* work;           // (n/2 + 1) x n double-float complex, row-major: rows ky = 0..n/2 after the x transform
     double* phi;         // n*n, row-major
 };
+cudaError_t launch_twiddles_df(dfc* tw, int n, cudaStream_t s);
 cudaError_t launch_synth_rows(const SynthArgs& a, cudaStream_t s);
 cudaError_t launch_synth_cols(const SynthArgs& a, cudaStream_t s);
 

@@ -7,8 +7,8 @@
 // held in registers and shared memory, so a wavelength costs two HBM passes:
 //   row pass:    phi (read once per wavelength group) -> exact phase reduction
 //                -> sin/cos -> taper -> FFT_x -> H_x/N -> IFFT_x -> field (write);
-//                H_x comes from a scalar (no table load), its phase exact in
-//                fixed-point turns like the screen phase
+//                H_x and H_y come from one scalar per wavelength (no table
+//                loads), their phases exact in fixed-point turns like the screen phase
 //   column pass: field (read) -> FFT_y -> H_y/N -> IFFT_y -> w |A|^2, summed over
 //                the group in registers -> intensity (one write per group)
 //
@@ -144,7 +144,6 @@ prop_cols_kernel(PropArgs a) {
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         const float2* src = a.work + (size_t)l * N * N + (size_t)(x0 / WL) * N * WL + (x0 % WL);
-        const float2* h = a.h + (size_t)l * N;
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * WL + w];
@@ -165,8 +164,9 @@ prop_cols_kernel(PropArgs a) {
             }
             continue;
         } else {
+            const unsigned long long hc = a.lam.h_fx[l];
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
+            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
             if constexpr (TWM == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
             else fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);
         }

@@ -37,26 +37,55 @@ SCINT_DEV float neg_log_ua32(const u32x4& w) {
 // of ~1e-7 of their (small) rms contribution.
 constexpr int kLowK = 32;
 
-// Shaped spectral value F[ky][kx] = sqrt(L^2 S(q)) (g_re + i g_im) / sqrt(2).
-SCINT_DEV double2 spectrum_bin(const SynthArgs& a, int kx, int ky) {
+// A bin's shaped value F[ky][kx] = sqrt(L^2 S(q)) (g_re + i g_im) / sqrt(2), in the
+// precision it is computed in: FP64 for the low bins (low = true, d), FP32 for the
+// others (f).  The DC bin is 0 (low = true).
+struct BinValue {
+    bool low;
+    double2 d;
+    float2 f;
+};
+SCINT_DEV BinValue spectrum_value(const SynthArgs& a, int kx, int ky) {
     const u32x4 w = philox4x32_10(u32x4{(uint32_t)kx, (uint32_t)ky, a.screen_id, 0u}, a.key0, a.key1);
     const int mx = signed_freq(kx, a.n), my = signed_freq(ky, a.n);
     const int m2 = mx * mx + my * my;
-    if (m2 == 0) return make_double2(0.0, 0.0);
+    BinValue v;
+    v.low = true;
+    v.d = make_double2(0.0, 0.0);
+    v.f = make_float2(0.0f, 0.0f);
+    if (m2 == 0) return v;
     if (abs(mx) <= kLowK && abs(my) <= kLowK) {
         const double ub = uniform53(w.w, w.z);
         const double r = sqrt(2.0 * neg_log_ua64(w));
         double sn, cs;
         sincospi(2.0 * ub, &sn, &cs);
         const double sig = a.amp * pow((double)m2, a.neg_beta_4);
-        return make_double2(sig * r * cs, sig * r * sn);
+        v.d = make_double2(sig * r * cs, sig * r * sn);
+        return v;
     }
+    // FP32 with the same 53-bit uniforms, each rounded once to float
     const float r = sqrtf(2.0f * neg_log_ua32(w));
     const float tb = fmaf((float)(w.z >> 11), 0x1.0p-52f, (float)w.w * 0x1.0p-31f) + 0x1.0p-53f;  // 2 u_b
     float sn, cs;
     sincospif(tb, &sn, &cs);
     const float sig = a.amp32 * powf((float)m2, a.neg_beta_4_32);
-    return make_double2((double)(sig * r * cs), (double)(sig * r * sn));
+    v.low = false;
+    v.f = make_float2(sig * r * cs, sig * r * sn);
+    return v;
+}
+
+// F[ky][kx] in FP64 (the inspection hook's form)
+SCINT_DEV double2 spectrum_bin(const SynthArgs& a, int kx, int ky) {
+    const BinValue v = spectrum_value(a, kx, ky);
+    return v.low ? v.d : make_double2((double)v.f.x, (double)v.f.y);
+}
+
+// F[ky][kx] as a double-float: FP32 bins are exact with lo = 0, so only the few
+// low bins touch the FP64 pipe
+SCINT_DEV dfc spectrum_bin_df(const SynthArgs& a, int kx, int ky) {
+    const BinValue v = spectrum_value(a, kx, ky);
+    if (v.low) return dfc{dfl(v.d.x), dfl(v.d.y)};
+    return dfc{dfl(v.f.x, 0.0f), dfl(v.f.y, 0.0f)};
 }
 
 // |F[ky][kx]|^2 = sigma^2 (g_re^2 + g_im^2) / 2 = sigma^2 (-2 ln u_a) / 2 of a

@@ -11,8 +11,13 @@
 // Column pass: two real columns per complex transform: Z(ky) = G_a(ky) + i
 //   G_b(ky) over all ky (Hermitian extension), inverse transform along y, and
 //   phi_a = sqrt(2)/L^2 Re, phi_b = sqrt(2)/L^2 Im.
-// This halves the FP64 transform work and the intermediate (row-major,
-// (N/2+1) x N complex128).  The noise is never stored.
+// This halves the transform work and the intermediate (row-major, (N/2+1) x N).
+// The noise is never stored.
+//
+// Precision: the transforms run in double-float arithmetic (dfc: pairs of FP32
+// numbers, ~44 significant bits; common.cuh) on the FP32 pipes, which on GB300
+// are 64 times wider than the FP64 pipe; the low bins are drawn in FP64 and
+// the phase is written in FP64.
 #include "dispatch.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
@@ -36,6 +41,18 @@ __global__ void twiddles64_kernel(double2* tw, int n) {
         tw[j] = make_double2(c, s);
     }
 }
+__global__ void twiddles_df_kernel(dfc* tw, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) {
+        double s, c;
+        sincospi(-2.0 * (double)j / (double)n, &s, &c);
+        tw[j] = dfc{dfl(c), dfl(s)};
+    }
+}
+cudaError_t launch_twiddles_df(dfc* tw, int n, cudaStream_t s) {
+    twiddles_df_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+    return cudaGetLastError();
+}
 cudaError_t launch_twiddles32(float2* tw, int n, cudaStream_t s) {
     twiddles32_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
     return cudaGetLastError();
@@ -53,20 +70,21 @@ template <int N> __host__ __device__ constexpr int synth_threads() { return synt
 // column pass: complex lines (each two real output columns) per block, at most N/2
 template <int N> __host__ __device__ constexpr int synth_col_lines() { return synth_lines<N>() < N / 2 ? synth_lines<N>() : N / 2; }
 template <int N> __host__ __device__ constexpr int synth_col_threads() { return synth_col_lines<N>() * FftPlan<N>::T / synth_cs<N>(); }
-template <int N> constexpr size_t synth_smem() { return (size_t)synth_lines<N>() * FftPlan<N>::BUF * sizeof(double2) / synth_cs<N>(); }
-template <int N> constexpr size_t synth_col_smem() { return (size_t)synth_col_lines<N>() * FftPlan<N>::BUF * sizeof(double2) / synth_cs<N>(); }
+template <int N> constexpr size_t synth_smem() { return (size_t)synth_lines<N>() * FftPlan<N>::BUF * sizeof(dfc) / synth_cs<N>(); }
+template <int N> constexpr size_t synth_col_smem() { return (size_t)synth_col_lines<N>() * FftPlan<N>::BUF * sizeof(dfc) / synth_cs<N>(); }
 
 template <int CS> SCINT_DEV int synth_rank() {
     if constexpr (CS == 1) return 0;
     else return (int)cooperative_groups::this_cluster().block_rank();
 }
 
-// F_h(ky, kx) = (F(ky, kx) + conj F(-ky, -kx)) / 2
-SCINT_DEV double2 hermitian_bin(const SynthArgs& a, int kx, int ky) {
+// F_h(ky, kx) = (F(ky, kx) + conj F(-ky, -kx)) / 2 (the halving is exact)
+SCINT_DEV dfl half(dfl v) { return dfl(0.5f * v.hi, 0.5f * v.lo); }
+SCINT_DEV dfc hermitian_bin(const SynthArgs& a, int kx, int ky) {
     const int n = a.n;
-    const double2 f = spectrum_bin(a, kx, ky);
-    const double2 g = spectrum_bin(a, (n - kx) & (n - 1), (n - ky) & (n - 1));
-    return make_double2(0.5 * (f.x + g.x), 0.5 * (f.y - g.y));
+    const dfc f = spectrum_bin_df(a, kx, ky);
+    const dfc g = spectrum_bin_df(a, (n - kx) & (n - 1), (n - ky) & (n - 1));
+    return dfc{half(f.x + g.x), half(f.y - g.y)};
 }
 
 template <int N>
@@ -75,16 +93,16 @@ synth_rows_kernel(SynthArgs a) {
     using Pl = FftPlan<N>;
     constexpr int CS = synth_cs<N>();
     constexpr int T = Pl::T, E = Pl::E, B = synth_lines<N>(), TL = T / CS;
-    extern __shared__ double2 smem64[];
+    extern __shared__ dfc smem_df[];
     const int team = threadIdx.x / TL;
     const int t = synth_rank<CS>() * TL + threadIdx.x % TL;
     const int ky = (blockIdx.x / CS) * B + team;
     const bool live = ky <= N / 2;                 // rows above N/2 are the conjugates of rows below
-    double2 v[E];
+    dfc v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = live ? hermitian_bin(a, t + m * T, ky) : make_double2(0.0, 0.0);
+    for (int m = 0; m < E; ++m) v[m] = live ? hermitian_bin(a, t + m * T, ky) : make_c<dfc>(0.0, 0.0);
     line_sync<CS>();
-    fft_line<double2, N, +1, 16, 1, 0, CS>(v, smem64 + team * (Pl::BUF / CS), t, a.tw);
+    fft_line<dfc, N, +1, 16, 1, 0, CS>(v, smem_df + team * (Pl::BUF / CS), t, a.tw);
     if (live) {
 #pragma unroll
         for (int m = 0; m < E; ++m) a.work[(size_t)ky * N + t + m * T] = v[m];
@@ -99,28 +117,28 @@ synth_cols_kernel(SynthArgs a) {
     using Pl = FftPlan<N>;
     constexpr int CS = synth_cs<N>();
     constexpr int T = Pl::T, E = Pl::E, W = synth_col_lines<N>(), TL = T / CS;
-    extern __shared__ double2 smem64[];
+    extern __shared__ dfc smem_df[];
     const int w = threadIdx.x % W;
     const int t = synth_rank<CS>() * TL + threadIdx.x / W;
     const int xa = ((blockIdx.x / CS) * W + w) * 2;
-    double2 v[E];
+    dfc v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int ky = t + m * T;
         const bool lo = ky <= N / 2;
-        const double2* g = a.work + (size_t)(lo ? ky : N - ky) * N + xa;
-        const double2 ga = g[0], gb = g[1];
+        const dfc* g = a.work + (size_t)(lo ? ky : N - ky) * N + xa;
+        const dfc ga = g[0], gb = g[1];
         // G(ky) = conj G(N - ky) above N/2; Z = G_a + i G_b
-        const double2 za = lo ? ga : conjc(ga), zb = lo ? gb : conjc(gb);
-        v[m] = make_double2(za.x - zb.y, za.y + zb.x);
+        const dfc za = lo ? ga : conjc(ga), zb = lo ? gb : conjc(gb);
+        v[m] = dfc{za.x - zb.y, za.y + zb.x};
     }
     line_sync<CS>();
-    fft_line<double2, N, +1, 16, W, 0, CS>(v, smem64 + w, t, a.tw);     // W lines interleaved
+    fft_line<dfc, N, +1, 16, W, 0, CS>(v, smem_df + w, t, a.tw);     // W lines interleaved
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         double* o = a.phi + (size_t)(t + m * T) * N + xa;
-        o[0] = a.out_scale * v[m].x;
-        o[1] = a.out_scale * v[m].y;
+        o[0] = a.out_scale * to_double(v[m].x);
+        o[1] = a.out_scale * to_double(v[m].y);
     }
     if constexpr (CS == 2) line_sync<CS>();
 }
