@@ -55,18 +55,26 @@ __device__ void block_sum2(double& a, double& b) {
     }
 }
 
-// Pass 1: each block sums a contiguous share of the region's rows.
+// Pass 1: block b sums rows r0 + b, r0 + b + gridDim.x, ...; each thread a
+// strided share of a row's columns.  The sums are of d = v - v0 and d^2, with v0
+// the region's first pixel: shifted by a value inside the data, they cancel
+// little when the variance is formed, so a thread may add one row's share in
+// FP32 (a few dozen values) and fold it into its FP64 sums once per row; the
+// FP64 pipe then sees two additions per row share instead of per pixel.
 __global__ void __launch_bounds__(256) map_moments_kernel(const float* map, int n, int r0, int r1,
                                                           int c0, int c1, double* partial) {
-    const int rows = r1 - r0, cols = c1 - c0;
-    const long long tot = (long long)rows * cols;
+    const float v0 = __ldg(map + (size_t)r0 * n + c0);
     double s = 0.0, s2 = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(i / cols), c = (int)(i % cols);
-        const double v = (double)__ldg(map + (size_t)(r0 + r) * n + c0 + c);
-        s += v;
-        s2 = fma(v, v, s2);
+    for (int r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
+        const float* row = map + (size_t)r * n;
+        float a = 0.0f, a2 = 0.0f;
+        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            const float d = __ldg(row + c) - v0;
+            a += d;
+            a2 = fmaf(d, d, a2);
+        }
+        s += (double)a;
+        s2 += (double)a2;
     }
     block_sum2(s, s2);
     if (threadIdx.x == 0) {
@@ -77,7 +85,7 @@ __global__ void __launch_bounds__(256) map_moments_kernel(const float* map, int 
 
 // Pass 2: one block reduces the partial sums (fixed order: deterministic).
 __global__ void __launch_bounds__(256) moments_final_kernel(const double* partial, int nblocks,
-                                                            double count, double* out) {
+                                                            double count, const float* v0p, double* out) {
     double s = 0.0, s2 = 0.0;
     for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
         s += partial[2 * i];
@@ -85,9 +93,10 @@ __global__ void __launch_bounds__(256) moments_final_kernel(const double* partia
     }
     block_sum2(s, s2);
     if (threadIdx.x == 0) {
-        const double mean = s / count;
-        const double var = fmax(s2 / count - mean * mean, 0.0);
+        const double md = s / count;                        // mean of d = v - v0
+        const double var = fmax(s2 / count - md * md, 0.0);
         const double sd = sqrt(var);
+        const double mean = (double)*v0p + md;
         out[0] = sd / mean;
         out[1] = mean;
         out[2] = sd;
@@ -100,7 +109,8 @@ cudaError_t launch_map_moments(const float* map, int n, int r0, int r1, int c0, 
     map_moments_kernel<<<kMomentBlocks, 256, 0, s>>>(map, n, r0, r1, c0, c1, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    moments_final_kernel<<<1, 256, 0, s>>>(partial, kMomentBlocks, (double)(r1 - r0) * (c1 - c0), out);
+    moments_final_kernel<<<1, 256, 0, s>>>(partial, kMomentBlocks, (double)(r1 - r0) * (c1 - c0),
+                                           map + (size_t)r0 * n + c0, out);
     return cudaGetLastError();
 }
 
