@@ -847,6 +847,123 @@ def run_timeseries(args):
         torch.distributed.destroy_process_group()
 
 
+def run_gradient(args):
+    """Gradient of a light-curve misfit (the differentiable path): 8 screens of 2048^2,
+    R_diff 100 km, 500 nm, one track of 10^4 samples at 0.2 px per screen.  A step is the
+    forward pass (screen -> propagation -> curve) and the adjoint (dL/dphi, dL/dR_diff)
+    for every screen.  Metric: screen pixels differentiated per second."""
+    import torch
+    import paper_1301_0514_gb300 as S
+    from paper_1301_0514_gb300 import workloads as W
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    items = W.config5()
+    for it in items:
+        it["seed"] += 100000 * rank
+    P = [S.params(**{k: it[k] for k in PARAM_KEYS}) for it in items]
+    n = items[0]["n"]
+    lams = items[0]["lambdas_nm"]
+    ws = torch.empty(S.workspace_bytes(P[0], len(lams)), dtype=torch.uint8, device=dev)
+    phi = [torch.empty((n, n), dtype=torch.float64, device=dev) for _ in items]
+    inten = torch.empty((n, n), dtype=torch.float32, device=dev)
+    curves = [torch.empty((1, it["n_samples"]), dtype=torch.float32, device=dev) for it in items]
+    targets = [torch.rand((1, it["n_samples"]), generator=torch.Generator().manual_seed(7 + i)).to(dev)
+               for i, it in enumerate(items)]
+    gcur = [torch.empty_like(c) for c in curves]
+    gphi = [torch.empty((n, n), dtype=torch.float64, device=dev) for _ in items]
+    grd = [torch.empty(1, dtype=torch.float64, device=dev) for _ in items]
+    for p, f in zip(P, phi):
+        S.make_screen(p, out=f, workspace=ws)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for i, (p, it) in enumerate(zip(P, items)):
+            S.sum_passband(p, phi[i], lams, out=inten, workspace=ws)
+            S.lightcurve(p, inten, it["tracks"], it["n_samples"], out=curves[i])
+            torch.sub(curves[i], targets[i], out=gcur[i])          # dL/dc of L = sum (c - t)^2 / 2
+            S.lightcurve_adjoint(p, phi[i], lams, it["tracks"], it["n_samples"], gcur[i], out=gphi[i],
+                                 workspace=ws)
+            S.rdiff_gradient(p, phi[i], gphi[i], workspace=ws, out=grd[i])
+
+    step()
+    torch.cuda.synchronize(dev)
+    S.profile_enable(True)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    kstats = S.profile_read()
+    S.profile_enable(False)
+    ms = _max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    units = float(n) * n * len(items)
+    value = units * world / (ms * 1e-3)
+    hbm_peak, sm_max_mhz, peak_src = _peaks()
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    dom_name, dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
+    tflops = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12 if dom["flops"] else 0.0
+    gbs = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9
+    roof = ({"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak}
+            if dom["flops"] else {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak})
+    roof.update({"traffic": None, "kernel": dom_name, "share": dom["total_ms"] / ms,
+                 "timing": "per-launch events inside the replayed graph"})
+    host = torch.empty(len(items), dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    step()
+    host.copy_(torch.cat(grd), non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        it = dict(items[0])
+        po = O.ScreenParams(**{k: it[k] for k in PARAM_KEYS}).with_(n=1024)
+        phi_o = O.make_screen(po)
+        tgt = np.zeros((1, it["n_samples"]))
+        tr = np.array(it["tracks"], dtype=np.float64).reshape(-1, 4).copy()
+        tr[:, [0, 1, 3]] *= 0.5                   # the same track on a half-size grid
+        t0 = time.perf_counter()
+        O.misfit_gradient(po, phi_o, lams, tr, it["n_samples"], tgt)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1024 * 1024 / dt, "unit": "screen pixels/s", "cores": 1, "kind": "oracle",
+               "sample": f"one 1024^2 screen, forward + adjoint, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": "screen pixels differentiated/sec (forward + adjoint of a light-curve misfit)",
+                "value": value, "unit": "screen pixels/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": f"{len(items)} screens {n}^2, 10 km pixels, R_diff 100 km, 500 nm, one track of "
+                                       f"10^4 samples at 0.2 px; forward + dL/dphi + dL/dR_diff per screen",
+                           "l2": "fields of 34 MB per screen"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": units * world / (e2e_ms * 1e-3), "unit": "screen pixels/s",
+                        "h2d_bytes_per_step": int(len(items) * (32 + 8 + 96)), "d2h_bytes_per_step": 8 * len(items),
+                        "ms_per_step": e2e_ms},
+                "gpu_launches": sum(v["launches"] for v in kstats.values()) * args.steps, "clocks": clk,
+                "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in kstats.items()}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -854,7 +971,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "screen_check", "conjugate",
-                                                              "m_sweep", "timeseries"])
+                                                              "m_sweep", "timeseries", "gradient"])
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
     ap.add_argument("--conj-n", type=int, default=4096, help="grid of the one-FFT workload")
     ap.add_argument("--sweep-n", type=int, default=8192, help="grid of the m-sweep workload")
@@ -869,6 +986,8 @@ def main():
         run_m_sweep(args)
     elif args.workload == "timeseries" and args.impl != "reference":
         run_timeseries(args)
+    elif args.workload == "gradient" and args.impl != "reference":
+        run_gradient(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

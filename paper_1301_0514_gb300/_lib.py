@@ -356,9 +356,10 @@ def lightcurve_adjoint(p: ScintParams, phi: torch.Tensor, lambdas_nm, tracks, n_
 
 
 def rdiff_gradient(p: ScintParams, phi: torch.Tensor, grad_phi: torch.Tensor, workspace=None,
-                   stream=None) -> torch.Tensor:
+                   out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """dL/dR_diff (1-element float64 device tensor) from dL/dphi at a fixed seed."""
-    out = torch.empty(1, dtype=torch.float64, device=phi.device)
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=phi.device)
     ws, wp, wb = _workspace(p, 1, workspace, phi.device)
     _check(lib().scint_rdiff_gradient(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
                                       _dev(grad_phi, torch.float64, p.n * p.n, "grad_phi"),
