@@ -40,6 +40,7 @@ UNIT = "pixel-wavelengths/s"
 PARAM_KEYS = ("n", "pixel_km", "r_diff_km", "beta", "lambda_nm", "lambda_ref_nm", "z_pc",
               "source_radius_km", "seed", "screen_id", "margin_km")
 SM_COUNT = 152
+CPU_SAMPLE_N = 2048       # the batch screen the oracle is timed on (about 10 s on one core)
 FP32_LANES_PER_SM = 128
 
 
@@ -146,9 +147,9 @@ class ClockSampler:
 
 
 def _cpu_baseline(items, gpu_maps):
-    """FP64 oracle on one 1024^2 screen of the batch (all 32 wavelengths, disk, tracks), one core."""
+    """FP64 oracle on one 2048^2 screen of the batch (all 32 wavelengths, disk, tracks), one core."""
     import oracle as O
-    it = [x for x in items if x["n"] == 1024][0]
+    it = [x for x in items if x["n"] == CPU_SAMPLE_N][0]
     p = O.ScreenParams(**{k: it[k] for k in PARAM_KEYS})
     t0 = time.perf_counter()
     phi = O.make_screen(p)
@@ -160,7 +161,7 @@ def _cpu_baseline(items, gpu_maps):
     dt = time.perf_counter() - t0
     units = p.n * p.n * len(it["lambdas_nm"])
     out = {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"one 1024^2 screen of the batch x {len(it['lambdas_nm'])} wavelengths + disk + "
+           "sample": f"one {p.n}^2 screen of the batch x {len(it['lambdas_nm'])} wavelengths + disk + "
                      f"{len(it['tracks'])} tracks, {dt:.1f} s"}
     err = None
     if gpu_maps is not None and it["seed"] in gpu_maps:
@@ -226,8 +227,9 @@ def run_ours(args):
     m_map = torch.empty((len(items), 4), dtype=torch.float64, device=dev)
     m_curve = [torch.empty((len(it["tracks"]), 3), dtype=torch.float64, device=dev) for it in items]
     # the screen checked against the oracle keeps its intensity map; the others live in lane scratch
-    par_i = next((i for i, p in enumerate(P) if p.n == 1024), None)
-    par_I = torch.empty((1024, 1024), dtype=torch.float32, device=dev) if par_i is not None else None
+    par_i = next((i for i, p in enumerate(P) if p.n == CPU_SAMPLE_N), None)
+    par_I = (torch.empty((CPU_SAMPLE_N, CPU_SAMPLE_N), dtype=torch.float32, device=dev)
+             if par_i is not None else None)
     entries = [dict(params=p, tracks=it["tracks"], n_samples=it["n_samples"], curves=curves[i],
                     m_map=m_map[i], m_curves=m_curve[i], intensity=par_I if i == par_i else None)
                for i, (p, it) in enumerate(zip(P, items))]
@@ -371,7 +373,7 @@ def run_ours(args):
 
     cpu = None
     err = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and any(x["n"] == 1024 for x in items):
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and par_i is not None:
         it = items[par_i]
         step()
         torch.cuda.synchronize(dev)

@@ -118,7 +118,7 @@ prop_rows_kernel(PropArgs a) {
 
 // ---- column pass ---------------------------------------------------------------
 template <int N, bool CONJ>
-__global__ void __launch_bounds__(pcol_threads<N>(), 1)
+__global__ void __launch_bounds__(pcol_threads<N>(), (pcol_threads<N>() <= 256 ? 2 : 1))
 prop_cols_kernel(PropArgs a) {
     using Pl = FftPlan<N, kColEPT>;
     constexpr int CS = pcs<N>(), TWM = pcol_twm<N>();

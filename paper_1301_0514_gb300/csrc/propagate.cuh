@@ -35,7 +35,13 @@ template <int N> __host__ __device__ constexpr int pcol_twm();   // below: depen
 // are transformed together); threads are per block
 template <int N> __host__ __device__ constexpr int prow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N ? kTileRow32 / N : N); }
 template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T / pcs<N>(); }
-template <int N> __host__ __device__ constexpr int pcol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N ? kTileCol32 / N : N); }
+// Column-pass blocks take 256 threads (two blocks per SM, so a stage barrier idles
+// half the SM, not all of it) wherever a block still holds two or more columns of
+// a strip; at N = 4096 that would leave one column (a quarter of every 32-byte
+// sector read), so there a block holds two columns in 512 threads.
+template <int N> __host__ __device__ constexpr int pcol_lines() {
+    return N >= 8192 ? 1 : (N >= 4096 ? 2 : (4096 / N < N ? 4096 / N : N));
+}
 template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_lines<N>() * FftPlan<N, kColEPT>::T / pcs<N>(); }
 // Strip width of the intermediate: at least 4 columns, so that every row of the
 // row pass writes whole 32-byte sectors; a column block then reads its
