@@ -49,7 +49,8 @@ extern "C" {
 #define SCINT_EINVAL       1   /* invalid argument (checked on the host) */
 #define SCINT_ENOMEM       2   /* workspace too small or allocation failed */
 #define SCINT_ECUDA        3   /* a CUDA runtime call failed */
-#define SCINT_ETIMEOUT     4   /* a bounded device-side wait gave up */
+#define SCINT_ETIMEOUT     4   /* reserved for a bounded device-side wait that gives up;
+                                  no kernel of this version waits on a flag or a peer */
 #define SCINT_EUNSUPPORTED 5   /* valid parameters this build does not support */
 
 #define SCINT_MAX_LAMBDA   128 /* wavelengths per passband call */

@@ -217,3 +217,18 @@ def test_timeseries_host_checks(lib):
                                        ctypes.c_void_p(16), None) == 1          # rows of a overlap
     assert lib.scint_curve_correlation(ctypes.c_void_p(16), 1, 0, ctypes.c_void_p(16), 3, 1,
                                        ctypes.c_void_p(16), None) == 1
+
+
+def test_wavelength_count_limits(lib):
+    p = S.params(n=64, pixel_km=20.0, r_diff_km=50.0)
+    lam = (ctypes.c_double * (S.MAX_LAMBDA + 1))(*([500.0] * (S.MAX_LAMBDA + 1)))
+    for count in (0, S.MAX_LAMBDA + 1):
+        rc = lib.scint_sum_passband(ctypes.byref(p), ctypes.c_void_p(16), lam, None, count, ctypes.c_void_p(16), 0,
+                                    None, 0, None)
+        assert rc == 1 and "n_lambda" in lib.scint_last_error().decode()
+    bad = (ctypes.c_double * 2)(500.0, -1.0)
+    assert lib.scint_sum_passband(ctypes.byref(p), ctypes.c_void_p(16), bad, None, 2, ctypes.c_void_p(16), 0,
+                                  None, 0, None) == 1
+    nan_w = (ctypes.c_double * 2)(0.5, float("nan"))
+    assert lib.scint_sum_passband(ctypes.byref(p), ctypes.c_void_p(16), lam, nan_w, 2, ctypes.c_void_p(16), 0,
+                                  None, 0, None) == 1

@@ -265,3 +265,28 @@ def test_config3_like_screen_passband_and_disk():
     c_o = O.lightcurves(I_o, it["tracks"], it["n_samples"])
     assert np.abs(c_g - c_o).max() <= I_TOL
     assert S.modulation_index(p_g, I_g).cpu().numpy()[0] == pytest.approx(O.modulation_index_map(I_o, p_o), rel=M_TOL)
+
+
+def test_passband_at_the_wavelength_limit():
+    """SCINT_MAX_LAMBDA wavelengths in one call (one group when the workspace allows, else groups)."""
+    it = W._item(64, 20.0, 50.0, lambda_nm=550.0, lambda_ref_nm=550.0, seed=W.SEED_BASE + 77, screen_id=3)
+    p_g, p_o = gpu_params(it), oracle_params(it)
+    lams = np.linspace(420.0, 690.0, S.MAX_LAMBDA)
+    w = np.linspace(1.0, 2.0, S.MAX_LAMBDA)
+    w /= w.sum()
+    phi = O.make_screen(p_o)
+    got = S.sum_passband(p_g, torch.from_numpy(phi).cuda(), lams, w).cpu().numpy()
+    assert np.abs(got - O.sum_passband(phi, p_o, lams, w)).max() <= I_TOL
+    ws = torch.empty(S.workspace_bytes(p_g, 7), dtype=torch.uint8, device="cuda")   # groups of 7
+    got7 = S.sum_passband(p_g, torch.from_numpy(phi).cuda(), lams, w, workspace=ws).cpu().numpy()
+    assert np.abs(got7 - got).max() <= 1e-5
+
+
+def test_empty_batch_and_empty_curves():
+    S.run_batch([], [550.0])
+    p = gpu_params(W._item(64, 20.0, 50.0))
+    I = torch.ones((64, 64), device="cuda")
+    assert S.lightcurve(p, I, np.zeros((0, 4)), 10).shape == (0, 10)
+    out = S.curve_modulation(torch.empty((0, 5), device="cuda"))
+    assert out.shape == (0, 3)
+    torch.cuda.synchronize()
