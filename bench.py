@@ -146,6 +146,68 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _cufft_comparison(items, dev, lams_every=4):
+    """The same passband propagation of one 4096^2 screen from library FFTs: torch's cuFFT
+    fft2/ifft2 plus elementwise tensor ops (phase reduced mod 2 pi in FP64, field and FFTs in
+    complex64), timed with CUDA events, and its map compared with this library's.  A
+    comparison only: it is not the product path."""
+    import torch
+    import paper_1301_0514_gb300 as S
+    it = [x for x in items if x["n"] == 4096][0]
+    p = S.params(**{k: it[k] for k in PARAM_KEYS})
+    lams = it["lambdas_nm"][::lams_every]
+    w = np.full(len(lams), 1.0 / len(lams))
+    n = p.n
+    L = n * p.pixel_km
+    phi = S.make_screen(p)
+    ours = S.sum_passband(p, phi, lams, w)
+    k = torch.fft.fftfreq(n, d=p.pixel_km, dtype=torch.float64, device=dev)
+    x = (torch.arange(n, dtype=torch.float64, device=dev) + 0.5) * p.pixel_km
+    stream = torch.cuda.current_stream(dev)
+
+    def tables(lam):
+        lz = lam * 1e-12 * p.z_pc * 3.0856775814913673e13
+        lm = min(10.0 * np.sqrt(lz / (2 * np.pi)), L / 4) if p.margin_km < 0 else p.margin_km
+        u = torch.minimum(x, L - x)
+        sf = torch.where(u <= lm, torch.sin(np.pi * u / (2 * lm)) ** 2, torch.ones_like(u)) if lm > 0 else torch.ones_like(u)
+        turns = lz * k * k / 2.0
+        ph = -2.0 * np.pi * (turns - torch.round(turns))
+        h = torch.polar(torch.ones_like(ph), ph).to(torch.complex64)
+        return sf.float(), h
+
+    tab = [tables(l) for l in lams]
+
+    def run():
+        out = torch.zeros((n, n), dtype=torch.float32, device=dev)
+        for (sf, h), lam, wl in zip(tab, lams, w):
+            turns = phi * (p.lambda_ref_nm / lam) / (2 * np.pi)
+            a = torch.polar(torch.ones((n, n), dtype=torch.float32, device=dev),
+                            (2 * np.pi * (turns - torch.round(turns))).float())
+            a = a * (sf[:, None] * sf[None, :])
+            f = torch.fft.ifft2(torch.fft.fft2(a) * (h[:, None] * h[None, :]))
+            out += float(wl) * (f.real ** 2 + f.imag ** 2)
+        return out
+
+    run()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = run()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    e0.record(stream)
+    S.sum_passband(p, phi, lams, w, out=ours)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_ours = e0.elapsed_time(e1)
+    units = float(n) * n * len(lams)
+    return {"value": units / (ms * 1e-3), "ms": ms, "unit": UNIT, "ours_value": units / (ms_ours * 1e-3),
+            "ours_ms": ms_ours, "max_abs_diff": float((res - ours).abs().max().item()),
+            "form": f"one 4096^2 screen x {len(lams)} wavelengths: torch cuFFT fft2/ifft2 + elementwise ops, "
+                    f"against scint_sum_passband on the same screen"}
+
+
 def _cpu_baseline(items, gpu_maps):
     """FP64 oracle on one 2048^2 screen of the batch (all 32 wavelengths, disk, tracks), one core."""
     import oracle as O
@@ -319,6 +381,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     ms_plain = p0.elapsed_time(p1)
 
+    cufft = _cufft_comparison(items, dev) if any(it["n"] == 4096 for it in items) else None
+
     # end to end through the public API with host inputs and host results
     pinned_curves = [torch.empty(c.shape, dtype=c.dtype, pin_memory=True) for c in curves]
     pinned_m = torch.empty(m_map.shape, dtype=m_map.dtype, pin_memory=True)
@@ -395,7 +459,7 @@ def run_ours(args):
                            "form": "the same batch on one lane (kernels in sequence), with per-launch events"},
                 "plain": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                           "form": "one screen and one wavelength per call, no graph"},
-                "parity": err, "kernels": kernels}
+                "cufft_comparison": cufft, "parity": err, "kernels": kernels}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
