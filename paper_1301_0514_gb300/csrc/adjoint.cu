@@ -53,47 +53,47 @@ cudaError_t launch_lightcurve_adjoint(const CurveAdjArgs& a, cudaStream_t s) {
 // ---- adjoint column pass ----------------------------------------------------------
 // buffers, the g_I columns (in place of the accumulator) and the twiddle table
 template <int N> constexpr size_t acol_smem() {
-    return (size_t)pcol_lines<N>() * (FftPlan<N, kColEPT>::BUF * sizeof(float2) + N * sizeof(float)) / pcs<N>() +
+    return (size_t)pcol_lines<N>() * FftPlan<N, kColEPT>::BUF * sizeof(float2) / pcs<N>() +
            (pcs<N>() == 2 ? 0 : (size_t)FftPlan<N>::TWS * sizeof(float2));
 }
 
 template <int N>
-__global__ void __launch_bounds__(pcol_threads<N>(), 1)
+__global__ void __launch_bounds__(pcol_threads<N>(), (pcol_threads<N>() <= 256 ? 2 : 1))
 adj_cols_kernel(AdjArgs a) {
     using Pl = FftPlan<N, kColEPT>;
     constexpr int CS = pcs<N>(), TWM = pcs<N>() == 2 ? 0 : 1;   // shared twiddle table unless split
     constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
-    constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
+    constexpr int TL = T / CS, BUFL = Pl::BUF / CS;
     extern __shared__ float2 smem32[];
     const int w = threadIdx.x % W, tl = threadIdx.x / W;
     const int t = line_rank<CS>() * TL + tl;
     const int x0 = (blockIdx.x / CS) * W;
     const int x = x0 + w;
     float2* buf = smem32 + w;
-    float* gi = reinterpret_cast<float*>(smem32 + W * BUFL) + w * NL + tl;   // g_I of this column (own entries)
-    float2* tws = smem32 + W * BUFL + (W * NL) / 2;
+    float gi[E];                                  // g_I of this column (own entries), in registers
+    float2* tws = smem32 + W * BUFL;
     const float2* twp = TWM == 1 ? tws : a.tw;
     if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
-    for (int m = 0; m < E; ++m) gi[m * TL] = a.grad_map[(size_t)(t + m * T) * N + x];
+    for (int m = 0; m < E; ++m) gi[m] = a.grad_map[(size_t)(t + m * T) * N + x];
     line_sync<CS>();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         float2* f = a.work + (size_t)l * N * N + (size_t)(x0 / WL) * N * WL + (x0 % WL);
-        const float2* h = a.h + (size_t)l * N;
+        const unsigned long long hc = a.lam.h_fx[l];    // H_y from its fixed-point phase
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = f[(size_t)(t + m * T) * WL + w];
         fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(h + t + m * T));
+        for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
         fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);          // A_out of this column
         const float c2w = 2.0f * a.lam.weight[l];
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = v[m] * (c2w * gi[m * TL]);     // G_out
+        for (int m = 0; m < E; ++m) v[m] = v[m] * (c2w * gi[m]);          // G_out
         fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], __ldg(h + t + m * T));
+        for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], transfer_at(hc, t + m * T, N));
         fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);          // P_y^H G_out
 #pragma unroll
         for (int m = 0; m < E; ++m) f[(size_t)(t + m * T) * WL + w] = v[m];
@@ -102,61 +102,61 @@ adj_cols_kernel(AdjArgs a) {
 }
 
 // ---- adjoint row pass --------------------------------------------------------------
-// buffers, fixed-point phases, twiddle table, g_phi accumulators
+// buffers and fixed-point phases (the g_phi sums live in registers; the twiddle
+// bases in registers too unless the line is split, which uses the global table)
 template <int N> constexpr size_t arow_smem() {
-    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long) + N * sizeof(float)) / pcs<N>() +
-           (pcs<N>() == 2 ? 0 : (size_t)FftPlan<N>::TWS * sizeof(float2));
+    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) / pcs<N>();
 }
 
 template <int N>
-__global__ void __launch_bounds__(prow_threads<N>(), 1)
+__global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
 adj_rows_kernel(AdjArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int CS = pcs<N>(), TWM = pcs<N>() == 2 ? 0 : 1;   // shared twiddle table unless split
+    constexpr int CS = pcs<N>(), TWM = pcs<N>() == 2 ? 0 : 2;   // register twiddle bases unless split
     constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), WL = pstrip<N>();
     constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
-    constexpr int TWSL = TWM == 1 ? Pl::TWS : 0;
     extern __shared__ float2 smem32[];
     const int team = threadIdx.x / TL, tl = threadIdx.x % TL;
     const int t = line_rank<CS>() * TL + tl;
     const int y = (blockIdx.x / CS) * B + team;
     float2* buf = smem32 + team * BUFL;
     long long* P = reinterpret_cast<long long*>(smem32 + B * BUFL) + team * NL + tl;
-    float2* tws = smem32 + B * BUFL + B * NL;
-    float* acc = reinterpret_cast<float*>(tws + TWSL) + team * NL + tl;   // g_phi of this row (own entries)
-    const float2* twp = TWM == 1 ? tws : a.tw;
-    if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
+    float acc[E];                                 // g_phi of this row (own entries)
+    TwiddleRegs<float2, N, 16> tr;
+    if constexpr (TWM == 2) tr.load(a.tw, t);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         P[m * TL] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
-        acc[m * TL] = 0.0f;
+        acc[m] = 0.0f;
     }
     line_sync<CS>();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         const float2* f = a.work + (size_t)l * N * N;
-        const float2* h = a.h + (size_t)l * N;
+        const unsigned long long hc = a.lam.h_fx[l];    // H_x from its fixed-point phase
         const float* sf = a.sf + (size_t)l * N;
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = f[strip_index<WL>(y, t + m * T, N)];
-        fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, twp);
+        if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
+        else fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, a.tw);
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], __ldg(h + t + m * T));
-        fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, twp);              // G_in of this row
+        for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], transfer_at(hc, t + m * T, N));
+        if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);   // G_in of this row
+        else fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, a.tw);
         const unsigned long long S = a.lam.scale_fx[l];
         const float s_l = a.lam.scale[l], sfy = sf[y];
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const float2 A = unit_phasor(P[m * TL], S) * (sfy * __ldg(sf + t + m * T));
             // s Im(conj(A_in) G_in)
-            acc[m * TL] = fmaf(s_l, A.x * v[m].y - A.y * v[m].x, acc[m * TL]);
+            acc[m] = fmaf(s_l, A.x * v[m].y - A.y * v[m].x, acc[m]);
         }
     }
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         double* o = a.grad_phi + (size_t)y * N + t + m * T;
-        *o = a.accumulate ? *o + (double)acc[m * TL] : (double)acc[m * TL];
+        *o = a.accumulate ? *o + (double)acc[m] : (double)acc[m];
     }
     if constexpr (CS == 2) line_sync<CS>();
 }

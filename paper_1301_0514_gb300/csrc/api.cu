@@ -95,8 +95,9 @@ constexpr int kRdiffRecIterations = 64;   // bisection steps for R_diff^rec (res
 size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
 size_t ws_synth(int n) { return up((size_t)n * 16) + up((size_t)(n / 2 + 1) * n * 16); }
+// twiddles, the taper table per wavelength, one field per wavelength of the group
 size_t ws_prop(int n, int g) {
-    return up((size_t)n * 8) + up((size_t)g * n * 8) + up((size_t)g * n * 4) + up((size_t)g * n * n * 8);
+    return up((size_t)n * 8) + up((size_t)g * n * 4) + up((size_t)g * n * n * 8);
 }
 size_t ws_smooth(int n) { return up((size_t)n * 8) + up((size_t)(n / 2 + 1) * n * 8); }
 // adjoint: twiddles, g_I map, half spectrum for its disk filter, then the propagation group buffers
@@ -270,7 +271,6 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
               int l0, int g, float* intensity, int accumulate, Carver& c, const float2* tw,
               cudaStream_t s) {
     const int n = p->n;
-    const double L = screen_len(p);
     static_assert(kMaxLambda >= SCINT_MAX_LAMBDA, "lambda table size");
     TableArgs ta{};
     ta.n = n;
@@ -282,20 +282,17 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
     pa.lam.count = g;
     for (int i = 0; i < g; ++i) {
         const double l = lam[l0 + i];
-        ta.lz_over_2L2[i] = lz_km2(l, p->z_pc) / (2.0 * L * L);
         ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
         fill_lambda(pa.lam, i, p, l, wts[l0 + i]);
     }
     Carver cg = c;   // group buffers restart at the same offset for every group
-    ta.h = cg.take<float2>((size_t)g * n * 8);
     ta.sf = cg.take<float>((size_t)g * n * 4);
-    pa.h = ta.h;
     pa.sf = ta.sf;
     pa.work = cg.take<float2>((size_t)g * n * n * 8);
     pa.intensity = intensity;
     pa.accumulate = accumulate;
     const double nn = (double)n * n;
-    SCINT_LAUNCH(K_PROP_TABLES, 12.0 * g * n, 0.0, s, launch_prop_tables(ta, s));
+    SCINT_LAUNCH(K_PROP_TABLES, 4.0 * g * n, 0.0, s, launch_prop_tables(ta, s));
     // rows: phi read once, one complex64 field written per wavelength; FFT_x + IFFT_x per row
     SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * g * nn, 2.0 * g * n * fft_flops(n), s, launch_prop_rows(pa, false, s));
     // columns: fields read, intensity written once (and read when accumulating)
@@ -376,7 +373,6 @@ int conj_impl(const scint_params* p, const double* phi, const double* lambdas, c
         ra.accumulate = accumulate || l0 > 0;
         for (int i = 0; i < gg; ++i) {
             const double l = lambdas[l0 + i], lz = lz_km2(l, p->z_pc);
-            ta.lz_over_2L2[i] = lz / (2.0 * screen_len(p) * screen_len(p));   // H table (unused here)
             ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
             fill_lambda(pa.lam, i, p, l, w[l0 + i]);
             // chirp turns per pixel^2, Delta^2 / (2 lambda z), reduced mod 1 and in 0.64 fixed point
@@ -388,9 +384,7 @@ int conj_impl(const scint_params* p, const double* phi, const double* lambdas, c
             ra.weight[i] = (float)w[l0 + i];
         }
         Carver cg = c;
-        ta.h = cg.take<float2>((size_t)gg * n * 8);
         ta.sf = cg.take<float>((size_t)gg * n * 4);
-        pa.h = ta.h;
         pa.sf = ta.sf;
         pa.work = cg.take<float2>((size_t)gg * n * n * 8);
         pa.intensity = intensity;
@@ -398,7 +392,7 @@ int conj_impl(const scint_params* p, const double* phi, const double* lambdas, c
         pa.conj.direct = direct ? 1 : 0;
         pa.conj.pattern = direct ? nullptr : cg.take<float>((size_t)gg * n * n * 4);
         ra.pattern = pa.conj.pattern;
-        SCINT_LAUNCH(K_PROP_TABLES, 12.0 * gg * n, 0.0, s, launch_prop_tables(ta, s));
+        SCINT_LAUNCH(K_PROP_TABLES, 4.0 * gg * n, 0.0, s, launch_prop_tables(ta, s));
         // one FFT per row and per column and wavelength
         SCINT_LAUNCH(K_CONJ_ROWS, 8.0 * nn + 8.0 * gg * nn, 1.0 * gg * n * fft_flops(n), s,
                      launch_prop_rows(pa, true, s));
@@ -802,31 +796,26 @@ int scint_lightcurve_adjoint(const scint_params* p, const double* phi, const dou
         pa.phi = phi;
         pa.tw = tw;
         pa.lam.count = gg;
-        const double L = screen_len(p);
         for (int i = 0; i < gg; ++i) {
             const double l = lambdas_nm[l0 + i];
-            ta.lz_over_2L2[i] = lz_km2(l, p->z_pc) / (2.0 * L * L);
             ta.margin_px[i] = taper_margin(p, l) / p->pixel_km;
             fill_lambda(pa.lam, i, p, l, w[l0 + i]);
         }
         Carver cg = cp;
-        ta.h = cg.take<float2>((size_t)gg * n * 8);
         ta.sf = cg.take<float>((size_t)gg * n * 4);
-        pa.h = ta.h;
         pa.sf = ta.sf;
         pa.work = cg.take<float2>((size_t)gg * n * n * 8);
         AdjArgs aa{};
         aa.n = n;
         aa.phi = phi;
         aa.tw = tw;
-        aa.h = ta.h;
         aa.sf = ta.sf;
         aa.work = pa.work;
         aa.grad_map = gmap;
         aa.grad_phi = grad_phi;
         aa.accumulate = accumulate || l0 > 0;
         aa.lam = pa.lam;
-        SCINT_LAUNCH(K_PROP_TABLES, 12.0 * gg * n, 0.0, s, launch_prop_tables(ta, s));
+        SCINT_LAUNCH(K_PROP_TABLES, 4.0 * gg * n, 0.0, s, launch_prop_tables(ta, s));
         SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * gg * nn, 2.0 * gg * n * fft_flops(n), s, launch_prop_rows(pa, false, s));
         SCINT_LAUNCH(K_ADJ_COLS, 16.0 * gg * nn + 4.0 * nn, 4.0 * gg * n * fft_flops(n), s, launch_adj_cols(aa, s));
         SCINT_LAUNCH(K_ADJ_ROWS, 8.0 * gg * nn + 8.0 * nn + (aa.accumulate ? 16.0 : 8.0) * nn,

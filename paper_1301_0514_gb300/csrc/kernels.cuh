@@ -70,7 +70,6 @@ struct PropArgs {
     int n;
     const double* phi;       // n*n radians at lambda_ref
     const float2* tw;        // FP32 twiddles
-    const float2* h;         // per lambda: n entries exp(-i pi lambda z k^2) / n
     const float* sf;         // per lambda: n taper values
     float2* work;            // per lambda: n*n complex64, strip layout
     float* intensity;        // n*n
@@ -78,12 +77,10 @@ struct PropArgs {
     LambdaSet lam;
     ConjSet conj;            // used by the one-FFT mode only
 };
-// h, sf tables for a wavelength group from host-side scalars.
+// The taper table of a wavelength group (SF at the pixel centres, per wavelength).
 struct TableArgs {
     int n, count;
-    double lz_over_2L2[kMaxLambda];   // lambda z / (2 L^2): H phase in turns per index^2
     double margin_px[kMaxLambda];     // taper margin in pixels (0 = no taper)
-    float2* h;
     float* sf;
 };
 cudaError_t launch_prop_tables(const TableArgs& a, cudaStream_t s);
@@ -136,7 +133,6 @@ struct AdjArgs {
     int n;
     const double* phi;
     const float2* tw;
-    const float2* h;           // per lambda: H / n
     const float* sf;           // per lambda: taper
     float2* work;              // per lambda: forward row-pass field, overwritten by P_y^H G_out
     const float* grad_map;     // dL/dI after the disk filter

@@ -25,20 +25,15 @@
 
 namespace scint {
 
-// ---- tables -----------------------------------------------------------------
+// ---- taper table --------------------------------------------------------------
+// raised-sine taper SF at the pixel centre (i + 1/2), symmetric about the centre
+// (Sect. 3.2.1); H is not tabulated: the passes compute it from one fixed-point
+// constant per wavelength (transfer_at)
 __global__ void prop_tables_kernel(TableArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int l = blockIdx.y;
     if (i >= a.n) return;
     const int n = a.n;
-    // H(k)/n with the phase in turns reduced in FP64 before sincospi
-    const double m = (double)sfreq(i, n);
-    const double turns = a.lz_over_2L2[l] * m * m;
-    const double fr = turns - rint(turns);
-    double s, c;
-    sincospi(-2.0 * fr, &s, &c);
-    a.h[(size_t)l * n + i] = make_float2((float)(c / n), (float)(s / n));
-    // raised-sine taper SF at the pixel centre (i + 1/2), symmetric about the centre
     const double lm = a.margin_px[l];
     double sf = 1.0;
     if (lm > 0.0) {
