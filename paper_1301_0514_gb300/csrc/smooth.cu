@@ -30,7 +30,7 @@ template <int CS> SCINT_DEV int srank() {
 
 // forward: two real columns (xa, xa+1) -> half spectra rows 0..N/2 of spec
 template <int N>
-__global__ void __launch_bounds__(scol_threads<N>(), 1)
+__global__ void __launch_bounds__(scol_threads<N>(), (scol_threads<N>() <= 256 ? 2 : 1))
 smooth_fwd_cols_kernel(SmoothArgs a) {
     using Pl = FftPlan<N>;
     constexpr int CS = scs<N>();
@@ -81,8 +81,11 @@ smooth_fwd_cols_kernel(SmoothArgs a) {
 }
 
 // rows of the half spectrum: FFT_x, times K/N^2, IFFT_x
+// register twiddle bases below the split size (the row pass's loads stay in registers)
+template <int N> __host__ __device__ constexpr int srow_twm() { return scs<N>() == 1 ? 2 : 0; }
+
 template <int N>
-__global__ void __launch_bounds__(srow_threads<N>(), 1)
+__global__ void __launch_bounds__(srow_threads<N>(), (srow_threads<N>() <= 256 ? 2 : 1))
 smooth_rows_kernel(SmoothArgs a) {
     using Pl = FftPlan<N>;
     constexpr int CS = scs<N>();
@@ -93,15 +96,16 @@ smooth_rows_kernel(SmoothArgs a) {
     const int ky = (blockIdx.x / CS) * B + team;
     const bool live = ky <= N / 2;
     float2* row = a.spec + (size_t)(live ? ky : 0) * N;
-    constexpr int TWM = stwm<N>();
-    float2* tws = smem32 + B * (Pl::BUF / CS);
-    if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
-    const float2* twp = TWM == 1 ? tws : a.tw;
+    constexpr int TWM = srow_twm<N>();
+    TwiddleRegs<float2, N, 16> tr;
+    if constexpr (TWM == 2) tr.load(a.tw, t);
+    float2* buf = smem32 + team * (Pl::BUF / CS);
     float2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = live ? row[t + m * T] : make_float2(0.f, 0.f);
     line_sync<CS>();
-    fft_line<float2, N, -1, 16, 1, TWM, CS>(v, smem32 + team * (Pl::BUF / CS), t, twp);
+    if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
+    else fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, a.tw);
     // mx^2 + my^2 <= N^2/2 is exact in FP32 for N <= 4096 and within one rounding above
     const float inv = 1.0f / ((float)N * (float)N);
     const float twopi_r = (float)(2.0 * kPi * a.radius_over_L);
@@ -113,7 +117,8 @@ smooth_rows_kernel(SmoothArgs a) {
         const float K = u > 0.0f ? 2.0f * j1f(u) / u : 1.0f;
         v[m] = v[m] * (K * inv);
     }
-    fft_line<float2, N, +1, 16, 1, TWM, CS>(v, smem32 + team * (Pl::BUF / CS), t, twp);
+    if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
+    else fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, a.tw);
     if (live) {
 #pragma unroll
         for (int m = 0; m < E; ++m) row[t + m * T] = v[m];
@@ -123,7 +128,7 @@ smooth_rows_kernel(SmoothArgs a) {
 
 // inverse: half spectra -> two real columns
 template <int N>
-__global__ void __launch_bounds__(scol_threads<N>(), 1)
+__global__ void __launch_bounds__(scol_threads<N>(), (scol_threads<N>() <= 256 ? 2 : 1))
 smooth_inv_cols_kernel(SmoothArgs a) {
     using Pl = FftPlan<N>;
     constexpr int CS = scs<N>();
@@ -156,7 +161,7 @@ smooth_inv_cols_kernel(SmoothArgs a) {
 }
 
 template <int N> constexpr size_t scol_smem() { return (size_t)scol_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>() + stws_bytes<N>(); }
-template <int N> constexpr size_t srow_smem() { return (size_t)srow_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>() + stws_bytes<N>(); }
+template <int N> constexpr size_t srow_smem() { return (size_t)srow_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>(); }
 
 // which = 0: forward column pass, 1: row pass, 2: inverse column pass
 cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {
