@@ -416,7 +416,9 @@ int scint_lightcurve_adjoint(const scint_params* p, const double* phi,
 int scint_rdiff_gradient(const scint_params* p, const double* phi, const double* grad_phi, double* out,
                          void* workspace, size_t workspace_bytes, void* stream);
 
-/* Release the library's internal per-device workspace pools and tables. */
+/* Release the library's internal per-device workspace pools, the twiddle tables
+ * it keeps per (device, grid size) after their first use, and the batch
+ * executor's streams.  Waits for the work that may still read them. */
 void scint_release(void);
 
 /*

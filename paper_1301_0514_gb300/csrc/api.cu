@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -171,6 +173,52 @@ int resolve_ws(void* ws, size_t bytes, size_t need, cudaStream_t s, Carver* c) {
     return SCINT_OK;
 }
 
+// ---- twiddle tables kept per (device, size, kind) -----------------------------------
+// A table is computed once, outside stream capture, synchronously (so every stream
+// may read it at once), and kept until scint_release.  A call that is capturing and
+// finds no table, or that must not allocate, computes one in its own workspace.
+enum TwKind { kTw32 = 0, kTwDf = 1 };
+struct TwCache {
+    std::mutex mu;
+    std::map<std::tuple<int, int, int>, void*> tab;
+};
+TwCache g_tw;
+
+int cached_twiddles(int n, int kind, cudaStream_t s, const void** out) {
+    *out = nullptr;
+    int dev = 0;
+    SCINT_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, n, kind);
+    {
+        std::lock_guard<std::mutex> lk(g_tw.mu);
+        const auto it = g_tw.tab.find(key);
+        if (it != g_tw.tab.end()) {
+            *out = it->second;
+            return SCINT_OK;
+        }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SCINT_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SCINT_OK;
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)n * (kind == kTwDf ? 16 : 8)) != cudaSuccess) {
+        cudaGetLastError();
+        return SCINT_OK;   // no room: the caller uses its workspace
+    }
+    cudaError_t e = kind == kTwDf ? launch_twiddles_df(static_cast<dfc*>(p), n, s)
+                                  : launch_twiddles32(static_cast<float2*>(p), n, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return fail(SCINT_ECUDA, "twiddle table: %s", cudaGetErrorString(e));
+    }
+    std::lock_guard<std::mutex> lk(g_tw.mu);
+    const auto ins = g_tw.tab.emplace(key, p);
+    if (!ins.second) cudaFree(p);   // another thread made it first
+    *out = ins.first->second;
+    return SCINT_OK;
+}
+
 // ---- kernel profiler -------------------------------------------------------------
 // When enabled, every kernel launch is bracketed by two CUDA events recorded on
 // its stream (they become event nodes when the stream is being captured), and
@@ -232,6 +280,23 @@ int launch_timed(KClass c, double bytes, double flops, cudaStream_t s, F&& launc
         const int rc_ = launch_timed(cls, bytes, flops, stream, [&] { return (call); }); \
         if (rc_) return rc_;                                                              \
     } while (0)
+
+// FP32 twiddles of n: the kept table, else (capturing, no room, or cache off)
+// computed into the slot reserved for it in the workspace
+int twiddles32(int n, bool use_cache, cudaStream_t s, float2* slot, const float2** tw) {
+    const void* kept = nullptr;
+    if (use_cache) {
+        const int rc = cached_twiddles(n, kTw32, s, &kept);
+        if (rc) return rc;
+    }
+    if (kept) {
+        *tw = static_cast<const float2*>(kept);
+        return SCINT_OK;
+    }
+    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n, 0.0, s, launch_twiddles32(slot, n, s));
+    *tw = slot;
+    return SCINT_OK;
+}
 
 void prof_clear_locked() {
     for (auto& r : g_prof.recs) {
@@ -303,7 +368,7 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
 
 int passband_impl(const scint_params* p, const double* phi, const double* lambdas, const double* weights,
                   int n_lambda, float* intensity, int accumulate, void* ws, size_t ws_bytes,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool keep_tables = true) {
     int rc = check_passband(p, lambdas, weights, n_lambda);
     if (rc) return rc;
     if (!phi || !intensity) return fail(SCINT_EINVAL, "phi and intensity must be device pointers");
@@ -318,8 +383,9 @@ int passband_impl(const scint_params* p, const double* phi, const double* lambda
     Carver c{};
     rc = resolve_ws(ws, ws_bytes, ws_prop(n, g), s, &c);
     if (rc) return rc;
-    float2* tw = c.take<float2>((size_t)n * 8);
-    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n, 0.0, s, launch_twiddles32(tw, n, s));
+    const float2* tw = nullptr;
+    rc = twiddles32(n, keep_tables, s, c.take<float2>((size_t)n * 8), &tw);
+    if (rc) return rc;
     for (int l0 = 0; l0 < n_lambda; l0 += g) {
         const int gg = std::min(g, n_lambda - l0);
         rc = run_group(p, phi, lambdas, w.data(), l0, gg, intensity, accumulate || l0 > 0, c, tw, s);
@@ -353,8 +419,9 @@ int conj_impl(const scint_params* p, const double* phi, const double* lambdas, c
     Carver c{};
     rc = resolve_ws(ws, ws_bytes, ws_conj(n, g, direct), s, &c);
     if (rc) return rc;
-    float2* tw = c.take<float2>((size_t)n * 8);
-    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n, 0.0, s, launch_twiddles32(tw, n, s));
+    const float2* tw = nullptr;
+    rc = twiddles32(n, true, s, c.take<float2>((size_t)n * 8), &tw);
+    if (rc) return rc;
     const double nn = (double)n * n, d1 = p->pixel_km;
     for (int l0 = 0; l0 < n_lambda; l0 += g) {
         const int gg = std::min(g, n_lambda - l0);
@@ -526,12 +593,15 @@ int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_
     rc = resolve_ws(workspace, workspace_bytes, ws_synth(p->n), s, &c);
     if (rc) return rc;
     SynthArgs a = synth_args(p);
-    dfc* tw = c.take<dfc>((size_t)p->n * 16);
-    a.tw = tw;
+    dfc* tw_slot = c.take<dfc>((size_t)p->n * 16);
+    const void* kept = nullptr;
+    rc = cached_twiddles(p->n, kTwDf, s, &kept);
+    if (rc) return rc;
+    a.tw = kept ? static_cast<const dfc*>(kept) : tw_slot;
     a.work = c.take<dfc>((size_t)(p->n / 2 + 1) * p->n * 16);
     a.phi = phi;
     const double nn = (double)p->n * p->n;
-    SCINT_LAUNCH(K_TWIDDLES, 16.0 * p->n, 0.0, s, launch_twiddles_df(tw, p->n, s));
+    if (!kept) SCINT_LAUNCH(K_TWIDDLES, 16.0 * p->n, 0.0, s, launch_twiddles_df(tw_slot, p->n, s));
     // rows: the noise is generated in registers, the half-transformed field is written
     const double half = (double)(p->n / 2 + 1) * p->n * 16.0;
     // rows: the noise is generated in registers, rows 0..n/2 of the x-transformed field are written
@@ -563,7 +633,7 @@ int scint_propagate_noalloc(const scint_params* p, const double* phi, float* int
     // read, so stale contents from the previous call need no clearing.
     const double lam = p->lambda_nm, w = 1.0;
     return passband_impl(p, phi, &lam, &w, 1, intensity, 0, scratch, kStaticScratchBytes,
-                         static_cast<cudaStream_t>(stream));
+                         static_cast<cudaStream_t>(stream), false);
 }
 
 double scint_conjugate_pixel_km(const scint_params* p, double lambda_nm) {
@@ -606,13 +676,13 @@ int scint_smooth_source(const scint_params* p, float* intensity, void* workspace
     SmoothArgs a{};
     a.n = p->n;
     a.radius_over_L = p->source_radius_km / screen_len(p);
-    float2* tw = c.take<float2>((size_t)p->n * 8);
-    a.tw = tw;
+    float2* tw_slot = c.take<float2>((size_t)p->n * 8);
     a.spec = c.take<float2>((size_t)(p->n / 2 + 1) * p->n * 8);
     a.intensity = intensity;
     const int n = p->n;
     const double half = (double)(n / 2 + 1) * n * 8.0, nn = (double)n * n;
-    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n, 0.0, s, launch_twiddles32(tw, n, s));
+    rc = twiddles32(n, true, s, tw_slot, &a.tw);
+    if (rc) return rc;
     SCINT_LAUNCH(K_SMOOTH_FWD, 4.0 * nn + half, (n / 2) * fft_flops(n), s, launch_smooth_pass(a, 0, s));
     SCINT_LAUNCH(K_SMOOTH_ROWS, 2.0 * half, 2.0 * (n / 2 + 1) * fft_flops(n), s, launch_smooth_pass(a, 1, s));
     SCINT_LAUNCH(K_SMOOTH_INV, half + 4.0 * nn, (n / 2) * fft_flops(n), s, launch_smooth_pass(a, 2, s));
@@ -677,8 +747,9 @@ int scint_curve_power_spectrum(const float* curves, int n_curves, int n_samples,
     Carver c{};
     int rc = resolve_ws(workspace, workspace_bytes, up((size_t)n_samples * 8), s, &c);
     if (rc) return rc;
-    float2* tw = c.take<float2>((size_t)n_samples * 8);
-    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n_samples, 0.0, s, launch_twiddles32(tw, n_samples, s));
+    const float2* tw = nullptr;
+    rc = twiddles32(n_samples, true, s, c.take<float2>((size_t)n_samples * 8), &tw);
+    if (rc) return rc;
     SCINT_LAUNCH(K_POWER, 4.0 * n_curves * (double)n_samples + 4.0 * n_curves * (n_samples / 2 + 1),
                  n_curves * fft_flops(n_samples), s, launch_power_spectrum(curves, n_curves, n_samples, power, tw, s));
     return ok();
@@ -755,9 +826,10 @@ int scint_lightcurve_adjoint(const scint_params* p, const double* phi, const dou
     float* gmap = c.take<float>((size_t)n * n * 4);
     float2* spec = c.take<float2>((size_t)(n / 2 + 1) * n * 8);
     Carver cp = c;                       // propagation buffers: twiddles, then group tables and fields
-    float2* tw = cp.take<float2>((size_t)n * 8);
+    const float2* tw = nullptr;
+    rc = twiddles32(n, true, s, cp.take<float2>((size_t)n * 8), &tw);
+    if (rc) return rc;
     const double nn = (double)n * n;
-    SCINT_LAUNCH(K_TWIDDLES, 8.0 * n, 0.0, s, launch_twiddles32(tw, n, s));
     // g_I = B^T g_c
     SCINT_CUDA(cudaMemsetAsync(gmap, 0, (size_t)n * n * 4, s));
     for (int t0 = 0; t0 < n_tracks && n_samples > 0; t0 += kTracksPerLaunch) {
@@ -941,6 +1013,18 @@ int scint_profile_read(scint_kernel_stat* stats, int max_stats, int* n_stats) {
 
 void scint_release(void) {
     scint::release_lanes();
+    {
+        std::lock_guard<std::mutex> lk(g_tw.mu);
+        int cur = 0;
+        cudaGetDevice(&cur);
+        for (auto& kv : g_tw.tab) {
+            cudaSetDevice(std::get<0>(kv.first));
+            cudaDeviceSynchronize();
+            cudaFree(kv.second);
+        }
+        g_tw.tab.clear();
+        cudaSetDevice(cur);
+    }
     std::lock_guard<std::mutex> lk(g_pool.mu);
     int cur = 0;
     cudaGetDevice(&cur);
