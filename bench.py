@@ -71,6 +71,10 @@ def _workload(name: str, rank: int):
         items[0]["lambdas_nm"] = items[0]["lambdas_nm"][::4]
         desc = ("profiling case: one 4096^2 screen of the batched workload x 8 wavelengths "
                 "(~1.2 GB on the device, above the L2 size)")
+    elif name == "config4":
+        items = [W.config4(beta=11.0 / 3.0, disk=True)]
+        desc = ("one 16384^2 screen (lines split over two-block clusters), 5 km pixels, R_diff 100 km, "
+                "Kolmogorov, 500 nm, disk of one R_ref")
     else:
         items = W.config2(r_diffs=(100.0,))
         items[0]["lambdas_nm"] = np.array([500.0])
@@ -1036,7 +1040,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "screen_check", "conjugate",
+    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "config4", "screen_check", "conjugate",
                                                               "m_sweep", "timeseries", "gradient"])
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
     ap.add_argument("--conj-n", type=int, default=4096, help="grid of the one-FFT workload")

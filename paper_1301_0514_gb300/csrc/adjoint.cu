@@ -206,12 +206,18 @@ __global__ void __launch_bounds__(256) dot_partial_kernel(const double* a, const
     }
 }
 
-__global__ void dot_final_kernel(const double* partial, int nb, double scale, double* out) {
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < nb; ++i) t += partial[i];
-        out[0] = scale * t;
+// fixed-order reduction of the block partials (the same bits on every run)
+__global__ void __launch_bounds__(256) dot_final_kernel(const double* partial, int nb, double scale, double* out) {
+    __shared__ double red[256];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) t += partial[i];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) out[0] = scale * red[0];
 }
 
 cudaError_t launch_scaled_dot(const double* a, const double* b, long long n, double scale, double* partial,
@@ -219,7 +225,7 @@ cudaError_t launch_scaled_dot(const double* a, const double* b, long long n, dou
     dot_partial_kernel<<<kMomentBlocks, 256, 0, s>>>(a, b, n, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dot_final_kernel<<<1, 32, 0, s>>>(partial, kMomentBlocks, scale, out);
+    dot_final_kernel<<<1, 256, 0, s>>>(partial, kMomentBlocks, scale, out);
     return cudaGetLastError();
 }
 

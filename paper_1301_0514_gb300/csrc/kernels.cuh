@@ -148,7 +148,7 @@ cudaError_t launch_scaled_dot(const double* a, const double* b, long long n, dou
 
 // FP64 moments of a rectangular region [r0, r1) x [c0, c1) of an n x n map;
 // out = {m, mean, sigma, count}.  partial: workspace of >= kMomentBlocks*2 doubles.
-constexpr int kMomentBlocks = 304;
+constexpr int kMomentBlocks = 1216;     // 8 per SM of a 152-SM GPU
 cudaError_t launch_map_moments(const float* map, int n, int r0, int r1, int c0, int c1,
                                double* partial, double* out, cudaStream_t s);
 // per-curve {m, mean, sigma}

@@ -67,14 +67,26 @@ __global__ void __launch_bounds__(256) map_moments_kernel(const float* map, int 
     double s = 0.0, s2 = 0.0;
     for (int r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         const float* row = map + (size_t)r * n;
-        float a = 0.0f, a2 = 0.0f;
-        for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            const float d = __ldg(row + c) - v0;
-            a += d;
-            a2 = fmaf(d, d, a2);
+        // four independent loads in flight per iteration (one would leave the pass latency-bound)
+        float a[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        int c = c0 + threadIdx.x;
+        for (; c + 3 * (int)blockDim.x < c1; c += 4 * blockDim.x) {
+            float d[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = __ldg(row + c + k * blockDim.x) - v0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                a[k] += d[k];
+                a2[k] = fmaf(d[k], d[k], a2[k]);
+            }
         }
-        s += (double)a;
-        s2 += (double)a2;
+        for (; c < c1; c += blockDim.x) {
+            const float d = __ldg(row + c) - v0;
+            a[0] += d;
+            a2[0] = fmaf(d, d, a2[0]);
+        }
+        s += (double)((a[0] + a[1]) + (a[2] + a[3]));
+        s2 += (double)((a2[0] + a2[1]) + (a2[2] + a2[3]));
     }
     block_sum2(s, s2);
     if (threadIdx.x == 0) {
