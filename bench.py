@@ -463,6 +463,12 @@ def run_ours(args):
                            "form": "the same batch on one lane (kernels in sequence), with per-launch events"},
                 "plain": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                           "form": "one screen and one wavelength per call, no graph"},
+                "three_pass_equivalent": {
+                    "bytes_per_px_lambda": 48, "GBps": value / world * 48 / 1e9,
+                    "frac_of_hbm": value / world * 48 / 1e9 / hbm_peak,
+                    "note": "this throughput expressed in the bytes of a three-pass design (FFT_x | "
+                            "FFT_y H IFFT_y | IFFT_x |A|^2, 48 B per pixel-wavelength); the two-pass "
+                            "kernels move 16 B, so their own DRAM fraction is lower by design"},
                 "cufft_comparison": cufft, "parity": err, "kernels": kernels}
         print(json.dumps(line), flush=True)
     if world > 1:
