@@ -97,9 +97,11 @@ constexpr int kRdiffRecIterations = 64;   // bisection steps for R_diff^rec (res
 size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
 size_t ws_synth(int n) { return up((size_t)n * 16) + up((size_t)(n / 2 + 1) * n * 16); }
-// twiddles, the taper table per wavelength, one field per wavelength of the group
+// twiddles, the taper table per wavelength, one field per wavelength of the group, and at
+// n = 16384 the column pass's column-major intensity
 size_t ws_prop(int n, int g) {
-    return up((size_t)n * 8) + up((size_t)g * n * 4) + up((size_t)g * n * n * 8);
+    return up((size_t)n * 8) + up((size_t)g * n * 4) + up((size_t)g * n * n * 8) +
+           (n >= kSplitN ? up((size_t)n * n * 4) : 0);
 }
 size_t ws_smooth(int n) { return up((size_t)n * 8) + up((size_t)(n / 2 + 1) * n * 8); }
 // adjoint: twiddles, g_I map, half spectrum for its disk filter, then the propagation group buffers
@@ -354,6 +356,7 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
     ta.sf = cg.take<float>((size_t)g * n * 4);
     pa.sf = ta.sf;
     pa.work = cg.take<float2>((size_t)g * n * n * 8);
+    pa.scratch = n >= kSplitN ? cg.take<float>((size_t)n * n * 4) : nullptr;
     pa.intensity = intensity;
     pa.accumulate = accumulate;
     const double nn = (double)n * n;

@@ -47,6 +47,42 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
     return e;
 }
 
+// Clusters of cs blocks of a kernel that are resident on the device at once (the
+// grid of a persistent kernel), queried once per kernel and device; call after set_smem.
+template <typename K>
+inline cudaError_t active_clusters(K kernel, int cs, int threads, size_t smem, int* out) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> seen;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_pair(dev, reinterpret_cast<const void*>(kernel));
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = seen.find(key);
+    if (it != seen.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * 1024);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    e = cudaOccupancyMaxActiveClusters(&nc, kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nc < 1) return cudaErrorInvalidConfiguration;
+    seen[key] = nc;
+    *out = nc;
+    return cudaSuccess;
+}
+
 // Launch k with clusters of cs blocks along x (cs == 1: ordinary launch).
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*k)(KArgs...), int cs, dim3 grid, dim3 block, size_t smem, cudaStream_t s,

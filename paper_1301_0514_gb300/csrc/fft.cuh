@@ -165,16 +165,17 @@ struct FftPlan {
     static constexpr int TWS = twoff(NSTAGE);            // table entries
 };
 
-// Fill a block's shared twiddle table from the global table tw[j] = exp(-2 pi i j / N).
+// Fill a block's shared twiddle table from the global table tw[j * stride] = exp(-2 pi i j / N)
+// (stride 2: the table of a line twice as long).
 template <typename C, int N>
-SCINT_DEV void fill_twiddle_table(C* tws, const C* __restrict__ tw, int tid, int nthreads) {
+SCINT_DEV void fill_twiddle_table(C* tws, const C* __restrict__ tw, int tid, int nthreads, int stride = 1) {
     using Pl = FftPlan<N>;
 #pragma unroll
     for (int s = 1; s < Pl::NSTAGE; ++s) {
         const int R = Pl::radix(s), P = Pl::span(s), base = Pl::twoff(s);
         for (int e = tid; e < (R - 1) * P; e += nthreads) {
             const int k = e / (R - 1), r = e % (R - 1) + 1;
-            tws[base + e] = __ldg(tw + r * k * (N / (P * R)));
+            tws[base + e] = __ldg(tw + r * k * (N / (P * R)) * stride);
         }
     }
 }
@@ -202,14 +203,15 @@ struct TwiddleRegs {
     static constexpr int NS = Pl::NSTAGE > 1 ? Pl::NSTAGE : 2;
     static constexpr int MAXNB = Pl::E;     // >= E / R for every stage
     C w[NS][MAXNB][2];
-    SCINT_DEV void load(const C* __restrict__ tw, int t) {
+    // tw[j * stride] = exp(-2 pi i j / N)
+    SCINT_DEV void load(const C* __restrict__ tw, int t, int stride = 1) {
 #pragma unroll
         for (int s = 1; s < Pl::NSTAGE; ++s) {
             const int R = Pl::radix(s), P = Pl::span(s);
 #pragma unroll
             for (int b = 0; b < Pl::E / R; ++b) {
                 const int k = (t + b * Pl::T) & (P - 1);
-                const int step = k * (N / (P * R));
+                const int step = k * (N / (P * R)) * stride;
                 w[s][b][0] = __ldg(tw + step);
                 w[s][b][1] = R >= 8 ? __ldg(tw + 4 * step) : w[s][b][0];
             }
@@ -251,7 +253,45 @@ template <int CS> SCINT_DEV void line_sync() {
     else cooperative_groups::this_cluster().sync();
 }
 
-template <typename C, int N, int DIR, int EPT, int LW, int TWM, int CS, int S>
+// the two halves of a cluster barrier, for work between them
+SCINT_DEV void cluster_arrive() { asm volatile("barrier.cluster.arrive.aligned;" ::: "memory"); }
+SCINT_DEV void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
+
+// 32-bit shared::cluster address of the same shared-memory offset in block `rank`
+// of the cluster (32-bit arithmetic instead of 64-bit generic pointers)
+SCINT_DEV unsigned cluster_addr(const void* local, unsigned rank) {
+    unsigned r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(local)), "r"(rank));
+    return r;
+}
+template <typename C> SCINT_DEV C ld_cluster(unsigned addr);
+template <>
+SCINT_DEV float2 ld_cluster<float2>(unsigned addr) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
+}
+template <>
+SCINT_DEV long long ld_cluster<long long>(unsigned addr) {
+    long long v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+template <>
+SCINT_DEV double2 ld_cluster<double2>(unsigned addr) {
+    double2 v;
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr) : "memory");
+    return v;
+}
+template <>
+SCINT_DEV dfc ld_cluster<dfc>(unsigned addr) {
+    float a, b, c, d;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(a), "=f"(b), "=f"(c), "=f"(d) : "r"(addr) : "memory");
+    return dfc{dfl(a, b), dfl(c, d)};
+}
+
+template <typename C, int N, int DIR, int EPT, int LW, int TWM, int CS, int S, int TS = 1>
 SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw,
                          const TwiddleRegs<C, N, EPT>* tr) {
     using Pl = FftPlan<N, EPT>;
@@ -259,14 +299,6 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
     constexpr int R = Pl::radix(S), P = Pl::span(S), NB = E / R;
     constexpr bool FIRST = (S == 0), LAST = (S == Pl::NSTAGE - 1);
     constexpr int HALF = N / 2;
-    C* bufs[CS];
-    if constexpr (CS == 1) {
-        bufs[0] = buf;
-    } else {
-        auto cl = cooperative_groups::this_cluster();
-        bufs[0] = cl.map_shared_rank(buf, 0);
-        bufs[1] = cl.map_shared_rank(buf, 1);
-    }
     C u[E];
     if constexpr (FIRST) {
         // butterfly b takes positions t + b T + r N/R = t + (b + r NB) T
@@ -274,16 +306,26 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
         for (int b = 0; b < NB; ++b)
 #pragma unroll
             for (int r = 0; r < R; ++r) u[b * R + r] = v[b + r * NB];
-    } else {
+    } else if constexpr (CS == 1) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             // N/R is a multiple of 16 here, so pad16(i + r N/R) = pad16(i) + r (N/R)(17/16).
-            // Split line: i < N/R <= N/2, so element i + r N/R is in the upper half iff r >= R/2.
+#pragma unroll
+            for (int r = 0; r < R; ++r) u[b * R + r] = buf[pad16(t + b * T) * LW + r * ((N / R) + (N / R) / 16) * LW];
+        }
+        __syncthreads();
+    } else {
+        // Split line: i < N/R <= N/2, so element i + r N/R is in the upper half
+        // (rank 1's buffer, local index i + (r - R/2) N/R) iff r >= R/2.
+        const unsigned cb0 = cluster_addr(buf, 0), cb1 = cluster_addr(buf, 1);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const unsigned off = (unsigned)(pad16(t + b * T) * LW * sizeof(C));
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int o = (CS == 2 && r >= R / 2) ? 1 : 0;
-                const int rr = r - o * (R / 2);
-                u[b * R + r] = bufs[o][pad16(t + b * T) * LW + rr * ((N / R) + (N / R) / 16) * LW];
+                const int rr = r < R / 2 ? r : r - R / 2;
+                u[b * R + r] = ld_cluster<C>((r < R / 2 ? cb0 : cb1) + off +
+                                             (unsigned)(rr * ((N / R) + (N / R) / 16) * LW * sizeof(C)));
             }
         }
         line_sync<CS>();
@@ -303,7 +345,7 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
                 for (int r = 1; r < R; ++r) {
                     // W_{PR}^{r k}: shared entry [k][r - 1] or global tw[r k N / (P R)]
                     const C w = TWM == 1 ? tw[Pl::twoff(S) + k * (R - 1) + (r - 1)]
-                                         : ld_tw(tw + r * k * (N / (P * R)));
+                                         : ld_tw(tw + r * k * (N / (P * R)) * TS);
                     u[b * R + r] = DIR < 0 ? cmul(u[b * R + r], w) : cmulc(u[b * R + r], w);
                 }
             }
@@ -316,43 +358,41 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
 #pragma unroll
             for (int r = 0; r < R; ++r) v[b + r * NB] = u[b * R + r];
     } else {
+        // Split line: with one butterfly per thread (NB = 1) and P <= T/2, the outputs
+        // j + r P, j = (i/P) P R + i mod P, of thread i all lie in [0, N/2) iff i < T/2,
+        // i.e. in the half its own block holds: every store is local, at j mod N/2.
+        static_assert(CS == 1 || (NB == 1 && P <= T / 2), "split-line stores must stay in the block");
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int i = t + b * T;
             const int k = i & (P - 1);
-            const int j = (i - k) * R + k;
-            if constexpr (CS == 1) {
-                // P >= 16: pad16(j + r P) = pad16(j) + r P (17/16); P == 1: j = i R and r < R <= 16
-                C* dst = buf + pad16(j) * LW;
+            int j = (i - k) * R + k;
+            if constexpr (CS == 2) j &= HALF - 1;
+            // P >= 16: pad16(j + r P) = pad16(j) + r P (17/16); P == 1: j = i R and r < R <= 16
+            C* dst = buf + pad16(j) * LW;
 #pragma unroll
-                for (int r = 0; r < R; ++r) dst[(P >= 16 ? r * (P + P / 16) : r) * LW] = u[b * R + r];
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int e = j + r * P;
-                    const int o = e >= HALF ? 1 : 0;
-                    bufs[o][pad16(e - o * HALF) * LW] = u[b * R + r];
-                }
-            }
+            for (int r = 0; r < R; ++r) dst[(P >= 16 ? r * (P + P / 16) : r) * LW] = u[b * R + r];
         }
         line_sync<CS>();
-        fft_stage<C, N, DIR, EPT, LW, TWM, CS, S + 1>(v, buf, t, tw, tr);
+        fft_stage<C, N, DIR, EPT, LW, TWM, CS, S + 1, TS>(v, buf, t, tw, tr);
     }
 }
 
 // Transform the team's line in place (registers v, distribution t + m*T).
 // Every thread of the block (of the cluster, for CS = 2) must call this the
 // same number of times.
-template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0, int CS = 1>
+// TS: stride of the global table (TWM = 0), tw[j TS] = exp(-2 pi i j / N).
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0, int CS = 1, int TS = 1>
 SCINT_DEV void fft_line(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw) {
     static_assert(TWM != 2, "register twiddles: use fft_line_tr");
     static_assert(CS == 1 || (CS == 2 && FftPlan<N, EPT>::NSTAGE > 1 && N >= 512), "split lines need N >= 512");
-    fft_stage<C, N, DIR, EPT, LW, TWM, CS, 0>(v, buf, t, tw, nullptr);
+    fft_stage<C, N, DIR, EPT, LW, TWM, CS, 0, TS>(v, buf, t, tw, nullptr);
 }
 
-template <typename C, int N, int DIR, int EPT = 16, int LW = 1>
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int CS = 1>
 SCINT_DEV void fft_line_tr(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const TwiddleRegs<C, N, EPT>& tr) {
-    fft_stage<C, N, DIR, EPT, LW, 2, 1, 0>(v, buf, t, nullptr, &tr);
+    static_assert(CS == 1 || (CS == 2 && FftPlan<N, EPT>::NSTAGE > 1 && N >= 512), "split lines need N >= 512");
+    fft_stage<C, N, DIR, EPT, LW, 2, CS, 0>(v, buf, t, nullptr, &tr);
 }
 
 }  // namespace scint

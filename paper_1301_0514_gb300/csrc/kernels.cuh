@@ -14,6 +14,7 @@ constexpr int kMaxLambda = 128;
 
 // Line-tile sizes (complex elements staged in shared memory per block).
 constexpr int kTileRow32 = 4096;    // FP32 line passes over rows
+constexpr int kSplitN = 16384;      // lines this long are split over a two-block cluster
 constexpr int kTileCol32 = 8192;    // FP32 line passes over columns
 constexpr int kTile64 = 4096;       // FP64 synthesis passes
 
@@ -74,6 +75,7 @@ struct PropArgs {
     float2* work;            // per lambda: n*n complex64, strip layout
     float* intensity;        // n*n
     int accumulate;          // add to intensity instead of overwriting
+    float* scratch;          // n = 16384: the column pass's column-major intensity (n*n)
     LambdaSet lam;
     ConjSet conj;            // used by the one-FFT mode only
 };

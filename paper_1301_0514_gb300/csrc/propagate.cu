@@ -183,6 +183,181 @@ prop_cols_kernel(PropArgs a) {
     if constexpr (CS == 2) line_sync<CS>();
 }
 
+// ---- lines split over a two-block cluster (N = 16384) -------------------------------
+// One radix-2 step on each side of the line transforms divides them between the two
+// blocks of a cluster (n < N/2, W = exp(-2 pi i / N)):
+//   forward, decimation in frequency: a_n = x_n + x_{n+N/2}, b_n = (x_n - x_{n+N/2}) W^n,
+//     X_{2k} = FFT_{N/2}(a)_k, X_{2k+1} = FFT_{N/2}(b)_k;
+//   inverse, decimation in time: A' = IFFT_{N/2}(Y_{2k}), B' = IFFT_{N/2}(Y_{2k+1}),
+//     y_n = A'_n + W^{-n} B'_n, y_{n+N/2} = A'_n - W^{-n} B'_n.
+// Block r takes the parity-r half-problem, a whole N/2-point line in its own shared
+// memory with block barriers only, and H at the frequencies 2k + r.  Each block forms
+// its a or b from both halves of the input (row pass: the whole line's phases sit in
+// both blocks; column pass: both blocks read the whole column, the second read from
+// L2).  The halves meet once per wavelength: each block publishes its A' or B' and
+// fetches the half of the other one that its outputs need (block 0 makes y_n and
+// y_{n+N/2} for n < N/4, block 1 for N/4 <= n < N/2).  The fetch is followed by a
+// split arrive/wait, so the next wavelength's input is formed while the partner
+// finishes reading.
+template <int N> __host__ __device__ constexpr int psplit_threads() { return FftPlan<N / 2>::T; }
+template <int N> constexpr size_t prow_split_smem() {
+    return (size_t)FftPlan<N / 2>::BUF * sizeof(float2) + (size_t)N * sizeof(long long);
+}
+template <int N> constexpr size_t pcol_split_smem() {
+    return (size_t)(FftPlan<N / 2>::BUF + FftPlan<N / 2>::TWS) * sizeof(float2);
+}
+
+// publish this block's half (A' or B') and combine it with the partner's: emit(j, n,
+// y_n, y_{n+N/2}) for n = t + (j + r E/2) T, j < E/2
+template <int H2, typename Emit>
+SCINT_DEV void split_combine(float2 (&v)[FftPlan<H2>::E], float2* buf, int t, int r, const float2* __restrict__ tw,
+                             Emit&& emit) {
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E;
+    static_assert(T % 16 == 0, "pad16(t + j T) = pad16(t) + j T 17/16");
+#pragma unroll
+    for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = v[m];
+    line_sync<2>();
+    const unsigned pb = cluster_addr(buf, (unsigned)(r ^ 1)) + (unsigned)(pad16(t + r * (E / 2) * T) * sizeof(float2));
+    float2 q[E / 2];
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) q[j] = ld_cluster<float2>(pb + (unsigned)(j * (T + T / 16) * sizeof(float2)));
+    cluster_arrive();    // this block is done with the partner's buffer; waited on before the next write
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) {
+        const int n = t + (j + r * (E / 2)) * T;
+        const float2 own = r == 0 ? v[j] : v[j + E / 2];
+        const float2 A = r == 0 ? own : q[j], B = r == 0 ? q[j] : own;
+        const float2 bw = cmulc(B, __ldg(tw + n));
+        emit(j, n, A + bw, A - bw);
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(psplit_threads<N>(), 1) prop_rows_split_kernel(PropArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E, W = pstrip<N>();
+    extern __shared__ float2 smem32[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    float2* buf = smem32;
+    // the whole line's fixed-point phases: this block converts its half (FP64) and copies
+    // the partner's; each thread reads back only the entries it wrote
+    long long* P = reinterpret_cast<long long*>(smem32 + Pl::BUF);
+    TwiddleRegs<float2, H2, 16> tr;
+    tr.load(a.tw, t, 2);    // the N-point table at even indices
+    // persistent: the cluster takes rows y, y + clusters, ...
+#pragma unroll 1
+    for (int y = blockIdx.x / 2; y < N; y += gridDim.x / 2) {
+        const double* phi = a.phi + (size_t)y * N + r * H2;
+#pragma unroll
+        for (int m = 0; m < E; ++m) P[r * H2 + t + m * T] = phase_fixed(phi[t + m * T]);
+        line_sync<2>();
+        const unsigned pp = cluster_addr(P, (unsigned)(r ^ 1)) + (unsigned)(((r ^ 1) * H2 + t) * sizeof(long long));
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            P[(r ^ 1) * H2 + t + m * T] = ld_cluster<long long>(pp + (unsigned)(m * T * sizeof(long long)));
+        cluster_arrive();
+#pragma unroll 1
+        for (int l = 0; l < a.lam.count; ++l) {
+            const unsigned long long S = a.lam.scale_fx[l];
+            const float* sf = a.sf + (size_t)l * N;
+            const float sfy = sf[y];
+            float2 v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = t + m * T;
+                const float2 x0 = unit_phasor(P[e], S) * (sfy * __ldg(sf + e));
+                const float2 x1 = unit_phasor(P[e + H2], S) * (sfy * __ldg(sf + e + H2));
+                v[m] = r == 0 ? x0 + x1 : cmul(x0 - x1, __ldg(a.tw + e));
+            }
+            cluster_wait();      // the partner has read this block's buffer
+            fft_line_tr<float2, H2, -1, 16, 1>(v, buf, t, tr);
+            const unsigned long long hc = a.lam.h_fx[l];
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, 2 * (t + m * T) + r, N));
+            fft_line_tr<float2, H2, +1, 16, 1>(v, buf, t, tr);
+            float2* dst = a.work + (size_t)l * N * N;
+            split_combine<H2>(v, buf, t, r, a.tw, [&](int, int n, float2 y0, float2 y1) {
+                dst[strip_index<W>(y, n, N)] = y0;
+                dst[strip_index<W>(y, n + H2, N)] = y1;
+            });
+        }
+        cluster_wait();    // the partner is done with this block's buffers (no block leaves before)
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(psplit_threads<N>(), 1) prop_cols_split_kernel(PropArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E, WL = pstrip<N>();
+    extern __shared__ float2 smem32[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    float2* buf = smem32;
+    float2* tws = smem32 + Pl::BUF;
+    fill_twiddle_table<float2, H2>(tws, a.tw, t, T, 2);
+    // persistent: the cluster takes columns x, x + clusters, ...
+#pragma unroll 1
+    for (int x = blockIdx.x / 2; x < N; x += gridDim.x / 2) {
+        float acc[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) acc[m] = 0.0f;
+        cluster_arrive();    // the first wait below also publishes the twiddle table to the block
+#pragma unroll 1
+        for (int l = 0; l < a.lam.count; ++l) {
+            const float2* src = a.work + (size_t)l * N * N + (size_t)(x / WL) * N * WL + (x % WL);
+            float2 v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = t + m * T;
+                const float2 x0 = src[(size_t)e * WL], x1 = src[(size_t)(e + H2) * WL];
+                v[m] = r == 0 ? x0 + x1 : cmul(x0 - x1, __ldg(a.tw + e));
+            }
+            cluster_wait();
+            fft_line<float2, H2, -1, 16, 1, 1, 1>(v, buf, t, tws);
+            const unsigned long long hc = a.lam.h_fx[l];
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, 2 * (t + m * T) + r, N));
+            fft_line<float2, H2, +1, 16, 1, 1, 1>(v, buf, t, tws);
+            const float wl = a.lam.weight[l];
+            split_combine<H2>(v, buf, t, r, a.tw, [&](int j, int, float2 y0, float2 y1) {
+                acc[2 * j] = fmaf(wl, fmaf(y0.x, y0.x, y0.y * y0.y), acc[2 * j]);
+                acc[2 * j + 1] = fmaf(wl, fmaf(y1.x, y1.x, y1.y * y1.y), acc[2 * j + 1]);
+            });
+        }
+        cluster_wait();
+        // column-major, so that the stores coalesce; transpose_add_kernel puts it in place
+        float* col = a.scratch + (size_t)x * N;
+#pragma unroll
+        for (int j = 0; j < E / 2; ++j) {
+            const int n = t + (j + r * (E / 2)) * T;
+            col[n] = acc[2 * j];
+            col[n + H2] = acc[2 * j + 1];
+        }
+    }
+}
+
+// intensity (+)= the transpose of the column-major map src, in 32 x 32 tiles through
+// shared memory (reads and writes both coalesced); n is a multiple of 32
+__global__ void __launch_bounds__(256) transpose_add_kernel(const float* __restrict__ src, float* dst, int n,
+                                                            int accumulate) {
+    __shared__ float tile[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+#pragma unroll
+    for (int k = ty; k < 32; k += 8) tile[k][tx] = src[(size_t)(x0 + k) * n + y0 + tx];   // [x][y]
+    __syncthreads();
+#pragma unroll
+    for (int k = ty; k < 32; k += 8) {
+        float* o = dst + (size_t)(y0 + k) * n + x0 + tx;
+        const float v = tile[tx][k];
+        *o = accumulate ? *o + v : v;
+    }
+}
+
 template <bool CONJ>
 cudaError_t launch_rows(const PropArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
@@ -190,10 +365,21 @@ cudaError_t launch_rows(const PropArgs& a, cudaStream_t s) {
         if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            cudaError_t e = set_smem(prop_rows_kernel<N, CONJ>, prow_smem<N>());
-            if (e != cudaSuccess) return e;
-            return launch_k(prop_rows_kernel<N, CONJ>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
-                            dim3(prow_threads<N>()), prow_smem<N>(), s, a);
+            if constexpr (pcs<N>() == 2 && !CONJ) {
+                static_assert(prow_split_smem<N>() <= kMaxSmem, "split row pass does not fit");
+                cudaError_t e = set_smem(prop_rows_split_kernel<N>, prow_split_smem<N>());
+                int nc = 0;
+                if (e == cudaSuccess)
+                    e = active_clusters(prop_rows_split_kernel<N>, 2, psplit_threads<N>(), prow_split_smem<N>(), &nc);
+                if (e != cudaSuccess) return e;
+                return launch_k(prop_rows_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()),
+                                prow_split_smem<N>(), s, a);
+            } else {
+                cudaError_t e = set_smem(prop_rows_kernel<N, CONJ>, prow_smem<N>());
+                if (e != cudaSuccess) return e;
+                return launch_k(prop_rows_kernel<N, CONJ>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
+                                dim3(prow_threads<N>()), prow_smem<N>(), s, a);
+            }
         }
     });
 }
@@ -205,10 +391,25 @@ cudaError_t launch_cols(const PropArgs& a, cudaStream_t s) {
         if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            cudaError_t e = set_smem(prop_cols_kernel<N, CONJ>, pcol_smem<N>());
-            if (e != cudaSuccess) return e;
-            return launch_k(prop_cols_kernel<N, CONJ>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
-                            dim3(pcol_threads<N>()), pcol_smem<N>(), s, a);
+            if constexpr (pcs<N>() == 2 && !CONJ) {
+                static_assert(pcol_split_smem<N>() <= kMaxSmem, "split column pass does not fit");
+                if (!a.scratch) return cudaErrorInvalidValue;
+                cudaError_t e = set_smem(prop_cols_split_kernel<N>, pcol_split_smem<N>());
+                int nc = 0;
+                if (e == cudaSuccess)
+                    e = active_clusters(prop_cols_split_kernel<N>, 2, psplit_threads<N>(), pcol_split_smem<N>(), &nc);
+                if (e != cudaSuccess) return e;
+                e = launch_k(prop_cols_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()),
+                             pcol_split_smem<N>(), s, a);
+                if (e != cudaSuccess) return e;
+                transpose_add_kernel<<<dim3(N / 32, N / 32), 256, 0, s>>>(a.scratch, a.intensity, N, a.accumulate);
+                return cudaGetLastError();
+            } else {
+                cudaError_t e = set_smem(prop_cols_kernel<N, CONJ>, pcol_smem<N>());
+                if (e != cudaSuccess) return e;
+                return launch_k(prop_cols_kernel<N, CONJ>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
+                                dim3(pcol_threads<N>()), pcol_smem<N>(), s, a);
+            }
         }
     });
 }

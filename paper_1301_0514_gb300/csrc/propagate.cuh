@@ -23,11 +23,13 @@ constexpr int kColTw = SCINT_COL_TWIDDLES;
 constexpr int kColEPT = 16;   // values per thread in the column passes
 constexpr size_t kMaxSmem = 227 * 1024;
 
-// Lines longer than one block's shared memory (N = 16384) are split over a
-// cluster of two blocks (fft.cuh, CS = 2); they read twiddles from the global
-// table.  Own-entry arrays (fixed-point phases, accumulators) hold the N/CS
-// entries of the line that the block's threads own.
-template <int N> __host__ __device__ constexpr int pcs() { return N >= 16384 ? 2 : 1; }
+// Lines longer than one block's shared memory (N = 16384) go to a cluster of two
+// blocks.  The transfer-function passes split them by one radix-2 step on each
+// side (prop_*_split_kernel, propagate.cu); the one-FFT mode and the adjoint split
+// every FFT stage (fft.cuh, CS = 2), reading twiddles from the global table, with
+// own-entry arrays (fixed-point phases, accumulators) holding the N/CS entries of
+// the line that the block's threads own.
+template <int N> __host__ __device__ constexpr int pcs() { return N >= kSplitN ? 2 : 1; }
 template <int N> __host__ __device__ constexpr int prow_twm() { return pcs<N>() == 2 ? 0 : kRowTw; }
 template <int N> __host__ __device__ constexpr int pcol_twm();   // below: depends on the shared-memory budget
 

@@ -5,7 +5,8 @@ At this size the oracle cannot run the whole map in seconds, so the checks are
 identities that hold at any size:
   * line FFTs vs numpy on whole 16384-point lines (FP32 and FP64);
   * screen pixels vs the oracle's direct double sum over all 2.7e8 bins;
-  * a sinusoidal phase grating vs its Jacobi-Anger closed form;
+  * sinusoidal phase gratings (along x, y and obliquely) vs the Jacobi-Anger closed form;
+  * a two-wavelength passband split into groups and accumulated vs its single-wavelength maps;
   * cosine eigenfunctions of the disk filter vs quadrature;
   * the full pipeline (beta in {3.3, 3.67, 3.9}, point and disk source):
     energy conservation of the periodic propagation (mean I = <SF^2>^2) and
@@ -55,23 +56,45 @@ def test_screen_16384_sampled_pixels():
     assert np.abs(ref).max() > 1.0
 
 
-def test_grating_16384_closed_form():
-    """phi = a sin(2 pi x / p) on 16384^2, untapered: Jacobi-Anger closed form (orders |m| <= 20)."""
+@pytest.mark.parametrize("fx,fy", [(64, 0), (0, 48), (40, -24)])
+def test_grating_16384_closed_form(fx, fy):
+    """phi = a sin(2 pi (fx x + fy y) / L) on 16384^2, untapered: Jacobi-Anger closed form
+    (orders |m| <= 20); fy != 0 puts the column pass (its split radix-2 steps) to work."""
     pix_km, a, lam, lam_ref, z = 5.0, 1.7, 500.0, 550.0, 160.0
     L = N * pix_km
-    per = L / 64.0
-    x = (np.arange(N) + 0.5) * pix_km
-    row = a * np.sin(2.0 * np.pi * x / per)
-    phi = torch.from_numpy(row).cuda().repeat(N, 1).contiguous()
+    c = (torch.arange(N, dtype=torch.float64, device="cuda") + 0.5) * pix_km
+    phi = a * torch.sin(2.0 * np.pi * (fx * c[None, :] + fy * c[:, None]) / L)
     p = S.params(n=N, pixel_km=pix_km, r_diff_km=100.0, lambda_nm=lam, lambda_ref_nm=lam_ref, z_pc=z, margin_km=0.0)
-    I = S.propagate(p, phi)
+    I = S.propagate(p, phi.contiguous())
     s = lam_ref / lam
     lz = lam * O.KM_PER_NM * z * O.KM_PER_PC
-    amp = sum(special.jv(m, a * s) * np.exp(2j * np.pi * m * x / per) * np.exp(-1j * np.pi * lz * m * m / per ** 2)
-              for m in range(-20, 21))
-    ref = np.abs(amp) ** 2
-    for y in (0, 4097, 16383):
-        assert np.abs(I[y].cpu().numpy() - ref).max() <= I_TOL
+    k2 = (fx * fx + fy * fy) / L ** 2
+    x = (np.arange(N) + 0.5) * pix_km
+    for y in (0, 4097, 8192, 16383):
+        u = 2.0 * np.pi * (fx * x + fy * x[y]) / L
+        amp = sum(special.jv(m, a * s) * np.exp(1j * m * u) * np.exp(-1j * np.pi * lz * m * m * k2) for m in range(-20, 21))
+        assert np.abs(I[y].cpu().numpy() - np.abs(amp) ** 2).max() <= I_TOL
+    # a column as well (the transposed write of the column pass)
+    xc = 12345
+    u = 2.0 * np.pi * (fx * x[xc] + fy * x) / L
+    amp = sum(special.jv(m, a * s) * np.exp(1j * m * u) * np.exp(-1j * np.pi * lz * m * m * k2) for m in range(-20, 21))
+    assert np.abs(I[:, xc].cpu().numpy() - np.abs(amp) ** 2).max() <= I_TOL
+
+
+def test_passband_16384_groups_accumulate():
+    """Two wavelengths in two groups (the workspace holds one) added onto a prior map equal
+    the weighted single-wavelength maps: the accumulating transposed write of the column pass."""
+    it = W.config4(beta=3.67, disk=False)
+    p = gpu_params(it)
+    phi = S.make_screen(p)
+    lams, wts = (480.0, 530.0), (0.3, 0.7)
+    ws = torch.empty(S.workspace_bytes(p, 1), dtype=torch.uint8, device="cuda")
+    out = torch.full((N, N), 0.25, device="cuda")
+    S.sum_passband(p, phi, lams, wts, out=out, accumulate=True, workspace=ws)
+    want = 0.25 + wts[0] * S.sum_passband(p, phi, lams[:1], workspace=ws).double()
+    want += wts[1] * S.sum_passband(p, phi, lams[1:], workspace=ws).double()
+    for y in (0, 7, 8191, 8192, 16383):
+        assert (out[y].double() - want[y]).abs().max().item() <= 1e-5
 
 
 def test_disk_filter_16384_eigenfunction():
