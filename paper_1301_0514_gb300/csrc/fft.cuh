@@ -395,4 +395,44 @@ SCINT_DEV void fft_line_tr(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const Twid
     fft_stage<C, N, DIR, EPT, LW, 2, CS, 0>(v, buf, t, nullptr, &tr);
 }
 
+// ---- lines split by one radix-2 step over a two-block cluster ------------------
+// Block r of the cluster holds the parity-r half-problem of an N-point line as a
+// whole N/2 = H2-point line in its own shared memory.  After the inverse
+// transforms of the halves (A' in block 0, B' in block 1, at n = t + m T), the
+// decimation-in-time step y_n = A'_n + W^{-n} B'_n, y_{n+H2} = A'_n - W^{-n} B'_n
+// (W = exp(-2 pi i / N), tw[j] = W^j) needs the other block's half: each block
+// publishes its values in its buffer and fetches, for its quarter of the outputs
+// (block 0: n < H2/2, block 1: n >= H2/2), the partner's.  emit(j, n, y_n, y_{n+H2})
+// for n = t + (j + r E/2) T, j < E/2.  Ends with a cluster arrive: the caller
+// waits (cluster_wait) before it next writes buf.
+template <typename C, int H2, typename Emit>
+SCINT_DEV void split_combine(C (&v)[FftPlan<H2>::E], C* buf, int t, int r, const C* __restrict__ tw, Emit&& emit) {
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E;
+    static_assert(T % 16 == 0, "pad16(t + j T) = pad16(t) + j T 17/16");
+#pragma unroll
+    for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = v[m];
+    line_sync<2>();
+    const unsigned pb = cluster_addr(buf, (unsigned)(r ^ 1)) + (unsigned)(pad16(t + r * (E / 2) * T) * sizeof(C));
+    C q[E / 2];
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) q[j] = ld_cluster<C>(pb + (unsigned)(j * (T + T / 16) * sizeof(C)));
+    cluster_arrive();    // done with the partner's buffer
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) {
+        const int n = t + (j + r * (E / 2)) * T;
+        const C own = r == 0 ? v[j] : v[j + E / 2];
+        const C A = r == 0 ? own : q[j], B = r == 0 ? q[j] : own;
+        const C bw = cmulc(B, ld_tw(tw + n));
+        emit(j, n, A + bw, A - bw);
+    }
+}
+
+// Decimation in frequency for the forward transform: the parity-r half-problem's
+// input, a_n = x_n + x_{n+H2} (r = 0) or b_n = (x_n - x_{n+H2}) W^n (r = 1).
+template <typename C>
+SCINT_DEV C split_dif(C x0, C x1, int r, int n, const C* __restrict__ tw) {
+    return r == 0 ? x0 + x1 : cmul(x0 - x1, ld_tw(tw + n));
+}
+
 }  // namespace scint

@@ -207,32 +207,6 @@ template <int N> constexpr size_t pcol_split_smem() {
     return (size_t)(FftPlan<N / 2>::BUF + FftPlan<N / 2>::TWS) * sizeof(float2);
 }
 
-// publish this block's half (A' or B') and combine it with the partner's: emit(j, n,
-// y_n, y_{n+N/2}) for n = t + (j + r E/2) T, j < E/2
-template <int H2, typename Emit>
-SCINT_DEV void split_combine(float2 (&v)[FftPlan<H2>::E], float2* buf, int t, int r, const float2* __restrict__ tw,
-                             Emit&& emit) {
-    using Pl = FftPlan<H2>;
-    constexpr int T = Pl::T, E = Pl::E;
-    static_assert(T % 16 == 0, "pad16(t + j T) = pad16(t) + j T 17/16");
-#pragma unroll
-    for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = v[m];
-    line_sync<2>();
-    const unsigned pb = cluster_addr(buf, (unsigned)(r ^ 1)) + (unsigned)(pad16(t + r * (E / 2) * T) * sizeof(float2));
-    float2 q[E / 2];
-#pragma unroll
-    for (int j = 0; j < E / 2; ++j) q[j] = ld_cluster<float2>(pb + (unsigned)(j * (T + T / 16) * sizeof(float2)));
-    cluster_arrive();    // this block is done with the partner's buffer; waited on before the next write
-#pragma unroll
-    for (int j = 0; j < E / 2; ++j) {
-        const int n = t + (j + r * (E / 2)) * T;
-        const float2 own = r == 0 ? v[j] : v[j + E / 2];
-        const float2 A = r == 0 ? own : q[j], B = r == 0 ? q[j] : own;
-        const float2 bw = cmulc(B, __ldg(tw + n));
-        emit(j, n, A + bw, A - bw);
-    }
-}
-
 template <int N>
 __global__ void __launch_bounds__(psplit_threads<N>(), 1) prop_rows_split_kernel(PropArgs a) {
     constexpr int H2 = N / 2;
@@ -279,7 +253,7 @@ __global__ void __launch_bounds__(psplit_threads<N>(), 1) prop_rows_split_kernel
             for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, 2 * (t + m * T) + r, N));
             fft_line_tr<float2, H2, +1, 16, 1>(v, buf, t, tr);
             float2* dst = a.work + (size_t)l * N * N;
-            split_combine<H2>(v, buf, t, r, a.tw, [&](int, int n, float2 y0, float2 y1) {
+            split_combine<float2, H2>(v, buf, t, r, a.tw, [&](int, int n, float2 y0, float2 y1) {
                 dst[strip_index<W>(y, n, N)] = y0;
                 dst[strip_index<W>(y, n + H2, N)] = y1;
             });
@@ -323,7 +297,7 @@ __global__ void __launch_bounds__(psplit_threads<N>(), 1) prop_cols_split_kernel
             for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, 2 * (t + m * T) + r, N));
             fft_line<float2, H2, +1, 16, 1, 1, 1>(v, buf, t, tws);
             const float wl = a.lam.weight[l];
-            split_combine<H2>(v, buf, t, r, a.tw, [&](int j, int, float2 y0, float2 y1) {
+            split_combine<float2, H2>(v, buf, t, r, a.tw, [&](int j, int, float2 y0, float2 y1) {
                 acc[2 * j] = fmaf(wl, fmaf(y0.x, y0.x, y0.y * y0.y), acc[2 * j]);
                 acc[2 * j + 1] = fmaf(wl, fmaf(y1.x, y1.x, y1.y * y1.y), acc[2 * j + 1]);
             });

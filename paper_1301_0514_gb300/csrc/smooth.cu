@@ -12,8 +12,8 @@
 
 namespace scint {
 
-// N = 16384 lines are split over a cluster of two blocks (fft.cuh, CS = 2)
-template <int N> __host__ __device__ constexpr int scs() { return N >= 16384 ? 2 : 1; }
+// N = 16384 lines go to a cluster of two blocks (the split kernels below)
+template <int N> __host__ __device__ constexpr int scs() { return N >= kSplitN ? 2 : 1; }
 template <int N> __host__ __device__ constexpr int scol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N / 2 ? kTileCol32 / N : N / 2); }
 template <int N> __host__ __device__ constexpr int scol_threads() { return scol_lines<N>() * FftPlan<N>::T / scs<N>(); }
 template <int N> __host__ __device__ constexpr int srow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N / 2 ? kTileRow32 / N : N / 2); }
@@ -160,6 +160,138 @@ smooth_inv_cols_kernel(SmoothArgs a) {
     if constexpr (CS == 2) line_sync<CS>();
 }
 
+// ---- N = 16384: lines split by one radix-2 step over a two-block cluster --------------
+// Block r of a cluster transforms the parity-r half of every line as a whole 8192-point
+// line in its own shared memory (fft.cuh: split_dif, split_combine):
+//   forward column pass: the frequencies f = 2k + r of the packed column pair, by
+//     decimation in frequency from both halves of the columns (both blocks read them);
+//     Z(N - f) has the parity of f, so the half-spectrum split stays in the block;
+//   row pass: decimation in frequency from the whole row, K at the frequencies 2k + r,
+//     inverse, decimation in time through the partner's buffer, written in place
+//     (the partner read the row before it reached the exchange);
+//   inverse column pass: block r reads the spectrum rows of its parity, inverse,
+//     decimation in time.
+// Grids are persistent: as many clusters as fit, each looping over lines.
+template <int N> __host__ __device__ constexpr int ssplit_threads() { return FftPlan<N / 2>::T; }
+template <int N> constexpr size_t ssplit_smem() {
+    return (size_t)(FftPlan<N / 2>::BUF + FftPlan<N / 2>::TWS) * sizeof(float2);
+}
+
+template <int N>
+__global__ void __launch_bounds__(ssplit_threads<N>(), 1) smooth_fwd_cols_split_kernel(SmoothArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E;
+    extern __shared__ float2 smem32[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    float2* buf = smem32;
+    float2* tws = smem32 + Pl::BUF;
+    fill_twiddle_table<float2, H2>(tws, a.tw, t, T, 2);
+    __syncthreads();
+#pragma unroll 1
+    for (int xa = (blockIdx.x / 2) * 2; xa < N; xa += gridDim.x) {
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int e = t + m * T;
+            const float2 z0 = *reinterpret_cast<const float2*>(a.intensity + (size_t)e * N + xa);
+            const float2 z1 = *reinterpret_cast<const float2*>(a.intensity + (size_t)(e + H2) * N + xa);
+            v[m] = split_dif(z0, z1, r, e, a.tw);
+        }
+        fft_line<float2, H2, -1, 16, 1, 1, 1>(v, buf, t, tws);     // v[m] = Z(2k + r), k = t + m T
+#pragma unroll
+        for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = v[m];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int k = t + m * T, f = 2 * k + r;
+            if (f <= N / 2) {
+                const float2 z = v[m];
+                const float2 zc = conjc(buf[pad16((H2 - r - k) & (H2 - 1))]);   // conj Z(N - f)
+                // X_a = (Z + conj Z(-f))/2, X_b = (Z - conj Z(-f))/(2i)
+                *reinterpret_cast<float4*>(a.spec + (size_t)f * N + xa) =
+                    make_float4(0.5f * (z.x + zc.x), 0.5f * (z.y + zc.y), 0.5f * (z.y - zc.y), -0.5f * (z.x - zc.x));
+            }
+        }
+        __syncthreads();    // the next pair's first stage rewrites buf
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(ssplit_threads<N>(), 1) smooth_rows_split_kernel(SmoothArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E;
+    extern __shared__ float2 smem32[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    float2* buf = smem32;
+    float2* tws = smem32 + Pl::BUF;
+    fill_twiddle_table<float2, H2>(tws, a.tw, t, T, 2);
+    const float inv = 1.0f / ((float)N * (float)N);
+    const float twopi_r = (float)(2.0 * kPi * a.radius_over_L);
+    cluster_arrive();    // the first wait also publishes the twiddle table to the block
+#pragma unroll 1
+    for (int ky = blockIdx.x / 2; ky <= N / 2; ky += gridDim.x / 2) {
+        float2* row = a.spec + (size_t)ky * N;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = split_dif(row[t + m * T], row[t + m * T + H2], r, t + m * T, a.tw);
+        cluster_wait();
+        fft_line<float2, H2, -1, 16, 1, 1, 1>(v, buf, t, tws);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int kx = 2 * (t + m * T) + r;
+            const int mx = kx < N / 2 ? kx : kx - N;
+            const float u = twopi_r * sqrtf((float)(mx * mx + ky * ky));
+            const float K = u > 0.0f ? 2.0f * j1f(u) / u : 1.0f;
+            v[m] = v[m] * (K * inv);
+        }
+        fft_line<float2, H2, +1, 16, 1, 1, 1>(v, buf, t, tws);
+        split_combine<float2, H2>(v, buf, t, r, a.tw, [&](int, int n, float2 y0, float2 y1) {
+            row[n] = y0;
+            row[n + H2] = y1;
+        });
+    }
+    cluster_wait();
+}
+
+template <int N>
+__global__ void __launch_bounds__(ssplit_threads<N>(), 1) smooth_inv_cols_split_kernel(SmoothArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E;
+    extern __shared__ float2 smem32[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    float2* buf = smem32;
+    float2* tws = smem32 + Pl::BUF;
+    fill_twiddle_table<float2, H2>(tws, a.tw, t, T, 2);
+    cluster_arrive();
+#pragma unroll 1
+    for (int xa = (blockIdx.x / 2) * 2; xa < N; xa += gridDim.x) {
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int f = 2 * (t + m * T) + r;
+            const bool lo = f <= N / 2;
+            const float4 q = *reinterpret_cast<const float4*>(a.spec + (size_t)(lo ? f : N - f) * N + xa);
+            // X(f) for f > N/2 is conj X(N-f) (real columns); Z = X_a + i X_b
+            const float2 Xa = lo ? make_float2(q.x, q.y) : make_float2(q.x, -q.y);
+            const float2 Xb = lo ? make_float2(q.z, q.w) : make_float2(q.z, -q.w);
+            v[m] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);
+        }
+        cluster_wait();
+        fft_line<float2, H2, +1, 16, 1, 1, 1>(v, buf, t, tws);
+        split_combine<float2, H2>(v, buf, t, r, a.tw, [&](int, int n, float2 y0, float2 y1) {
+            *reinterpret_cast<float2*>(a.intensity + (size_t)n * N + xa) = y0;
+            *reinterpret_cast<float2*>(a.intensity + (size_t)(n + H2) * N + xa) = y1;
+        });
+    }
+    cluster_wait();
+}
+
 template <int N> constexpr size_t scol_smem() { return (size_t)scol_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>() + stws_bytes<N>(); }
 template <int N> constexpr size_t srow_smem() { return (size_t)srow_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / scs<N>(); }
 
@@ -172,6 +304,16 @@ cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {
         } else {
             constexpr int CS = scs<N>();
             cudaError_t e;
+            if constexpr (CS == 2) {
+                static_assert(ssplit_smem<N>() <= 227 * 1024, "split smoothing pass does not fit");
+                auto k = which == 0 ? smooth_fwd_cols_split_kernel<N>
+                                    : (which == 1 ? smooth_rows_split_kernel<N> : smooth_inv_cols_split_kernel<N>);
+                int nc = 0;
+                if ((e = set_smem(k, ssplit_smem<N>())) != cudaSuccess) return e;
+                if ((e = active_clusters(k, 2, ssplit_threads<N>(), ssplit_smem<N>(), &nc)) != cudaSuccess) return e;
+                const int lines = which == 1 ? N / 2 + 1 : N / 2;
+                return launch_k(k, 2, dim3(2 * std::min(nc, lines)), dim3(ssplit_threads<N>()), ssplit_smem<N>(), s, a);
+            } else {
             // every block (cluster) of the column passes holds W line pairs = 2W real columns
             const int col_blocks = N / (2 * scol_lines<N>()) * CS;
             if (which == 0) {
@@ -185,6 +327,7 @@ cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {
             } else {
                 if ((e = set_smem(smooth_inv_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
                 return launch_k(smooth_inv_cols_kernel<N>, CS, dim3(col_blocks), dim3(scol_threads<N>()), scol_smem<N>(), s, a);
+            }
             }
         }
     });

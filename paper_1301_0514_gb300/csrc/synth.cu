@@ -62,9 +62,9 @@ cudaError_t launch_twiddles64(double2* tw, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Lines per block (all transformed together); N = 16384 lines (256 KB in FP64)
-// are split over a cluster of two blocks (fft.cuh, CS = 2).
-template <int N> __host__ __device__ constexpr int synth_cs() { return N >= 16384 ? 2 : 1; }
+// Lines per block (all transformed together); N = 16384 lines (256 KB in
+// double-float) go to a cluster of two blocks (the split kernels below).
+template <int N> __host__ __device__ constexpr int synth_cs() { return N >= kSplitN ? 2 : 1; }
 template <int N> __host__ __device__ constexpr int synth_lines() { return N >= kTile64 ? 1 : (kTile64 / N < N ? kTile64 / N : N); }
 template <int N> __host__ __device__ constexpr int synth_threads() { return synth_lines<N>() * FftPlan<N>::T / synth_cs<N>(); }
 // column pass: complex lines (each two real output columns) per block, at most N/2
@@ -143,6 +143,79 @@ synth_cols_kernel(SynthArgs a) {
     if constexpr (CS == 2) line_sync<CS>();
 }
 
+// ---- N = 16384: lines split by one radix-2 step over a two-block cluster --------------
+// Both passes are inverse transforms, so each block r of a cluster takes the spectral
+// values of parity r (f = 2k + r), inverse-transforms them as a whole 8192-point line in
+// its own shared memory, and the decimation-in-time step combines the two halves through
+// the partner's buffer (fft.cuh, split_combine): no value is generated or read twice.
+// Twiddles come from the N-point double-float table at even indices.  Persistent grids.
+template <int N> __host__ __device__ constexpr int synth_split_threads() { return FftPlan<N / 2>::T; }
+template <int N> constexpr size_t synth_split_smem() { return (size_t)FftPlan<N / 2>::BUF * sizeof(dfc); }
+
+template <int N>
+__global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_rows_split_kernel(SynthArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E;
+    extern __shared__ dfc smem_df[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    dfc* buf = smem_df;
+    cluster_arrive();
+#pragma unroll 1
+    for (int ky = blockIdx.x / 2; ky <= N / 2; ky += gridDim.x / 2) {
+        dfc v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = hermitian_bin(a, 2 * (t + m * T) + r, ky);
+        cluster_wait();
+        fft_line<dfc, H2, +1, 16, 1, 0, 1, 2>(v, buf, t, a.tw);
+        dfc* row = a.work + (size_t)ky * N;
+        split_combine<dfc, H2>(v, buf, t, r, a.tw, [&](int, int n, dfc y0, dfc y1) {
+            row[n] = y0;
+            row[n + H2] = y1;
+        });
+    }
+    cluster_wait();
+}
+
+// two real output columns (xa, xa + 1) per complex line
+template <int N>
+__global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_cols_split_kernel(SynthArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E;
+    extern __shared__ dfc smem_df[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    dfc* buf = smem_df;
+    cluster_arrive();
+#pragma unroll 1
+    for (int xa = (blockIdx.x / 2) * 2; xa < N; xa += gridDim.x) {
+        dfc v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int ky = 2 * (t + m * T) + r;
+            const bool lo = ky <= N / 2;
+            const dfc* g = a.work + (size_t)(lo ? ky : N - ky) * N + xa;
+            const dfc ga = g[0], gb = g[1];
+            // G(ky) = conj G(N - ky) above N/2; Z = G_a + i G_b
+            const dfc za = lo ? ga : conjc(ga), zb = lo ? gb : conjc(gb);
+            v[m] = dfc{za.x - zb.y, za.y + zb.x};
+        }
+        cluster_wait();
+        fft_line<dfc, H2, +1, 16, 1, 0, 1, 2>(v, buf, t, a.tw);
+        split_combine<dfc, H2>(v, buf, t, r, a.tw, [&](int, int n, dfc y0, dfc y1) {
+            double* o = a.phi + (size_t)n * N + xa;
+            o[0] = a.out_scale * to_double(y0.x);
+            o[1] = a.out_scale * to_double(y0.y);
+            o = a.phi + (size_t)(n + H2) * N + xa;
+            o[0] = a.out_scale * to_double(y1.x);
+            o[1] = a.out_scale * to_double(y1.y);
+        });
+    }
+    cluster_wait();
+}
+
 template <bool ROWS>
 cudaError_t launch_synth_pass(const SynthArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
@@ -152,7 +225,17 @@ cudaError_t launch_synth_pass(const SynthArgs& a, cudaStream_t s) {
         } else {
             constexpr int CS = synth_cs<N>();
             cudaError_t e;
-            if (ROWS) {
+            if constexpr (CS == 2) {
+                static_assert(synth_split_smem<N>() <= 227 * 1024, "split synthesis pass does not fit");
+                auto k = ROWS ? synth_rows_split_kernel<N> : synth_cols_split_kernel<N>;
+                int nc = 0;
+                if ((e = set_smem(k, synth_split_smem<N>())) != cudaSuccess) return e;
+                if ((e = active_clusters(k, 2, synth_split_threads<N>(), synth_split_smem<N>(), &nc)) != cudaSuccess)
+                    return e;
+                const int lines = ROWS ? N / 2 + 1 : N / 2;
+                return launch_k(k, 2, dim3(2 * std::min(nc, lines)), dim3(synth_split_threads<N>()),
+                                synth_split_smem<N>(), s, a);
+            } else if (ROWS) {
                 if ((e = set_smem(synth_rows_kernel<N>, synth_smem<N>())) != cudaSuccess) return e;
                 const int rows = N / 2 + 1;
                 return launch_k(synth_rows_kernel<N>, CS, dim3((rows + synth_lines<N>() - 1) / synth_lines<N>() * CS),

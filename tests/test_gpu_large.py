@@ -7,7 +7,7 @@ identities that hold at any size:
   * screen pixels vs the oracle's direct double sum over all 2.7e8 bins;
   * sinusoidal phase gratings (along x, y and obliquely) vs the Jacobi-Anger closed form;
   * a two-wavelength passband split into groups and accumulated vs its single-wavelength maps;
-  * cosine eigenfunctions of the disk filter vs quadrature;
+  * cosine eigenfunctions of the disk filter (along x, y and obliquely) vs quadrature;
   * the full pipeline (beta in {3.3, 3.67, 3.9}, point and disk source):
     energy conservation of the periodic propagation (mean I = <SF^2>^2) and
     of the disk filter (mean preserved).
@@ -97,19 +97,24 @@ def test_passband_16384_groups_accumulate():
         assert (out[y].double() - want[y]).abs().max().item() <= 1e-5
 
 
-def test_disk_filter_16384_eigenfunction():
+@pytest.mark.parametrize("mx,my", [(1, 0), (9, 0), (0, 7), (5, -3)])
+def test_disk_filter_16384_eigenfunction(mx, my):
+    """cos(2 pi (mx x + my y) / L) is an eigenfunction of the periodic disk filter with
+    eigenvalue K(q) = 2 J1(2 pi q R)/(2 pi q R), q = |m|/L (K by quadrature here); my != 0
+    puts the column passes (their split radix-2 steps) to work."""
     pix_km, R = 5.0, 24686.0
     L = N * pix_km
+    c = (torch.arange(N, dtype=torch.float64, device="cuda") + 0.5) * pix_km
+    I = (1.0 + 0.25 * torch.cos(2.0 * np.pi * (mx * c[None, :] + my * c[:, None]) / L)).float().contiguous()
+    S.smooth_source(S.params(n=N, pixel_km=pix_km, r_diff_km=100.0, source_radius_km=R), I)
+    u = 2.0 * np.pi * math.hypot(mx, my) / L * R
+    K = integrate.quad(lambda t: 2.0 * math.sqrt(1 - t * t) * math.cos(u * t), -1, 1, limit=200)[0] / math.pi
     x = (np.arange(N) + 0.5) * pix_km
-    for mode in (1, 9):
-        row = 1.0 + 0.25 * np.cos(2.0 * np.pi * mode * x / L)
-        I = torch.from_numpy(row.astype(np.float32)).cuda().repeat(N, 1).contiguous()
-        S.smooth_source(S.params(n=N, pixel_km=pix_km, r_diff_km=100.0, source_radius_km=R), I)
-        u = 2.0 * np.pi * (mode / L) * R
-        K = integrate.quad(lambda t: 2.0 * math.sqrt(1 - t * t) * math.cos(u * t), -1, 1, limit=200)[0] / math.pi
-        ref = 1.0 + 0.25 * K * np.cos(2.0 * np.pi * mode * x / L)
-        for y in (0, 9000):
-            assert np.abs(I[y].cpu().numpy() - ref).max() <= I_TOL
+    for y in (0, 9000, 16383):
+        ref = 1.0 + 0.25 * K * np.cos(2.0 * np.pi * (mx * x + my * x[y]) / L)
+        assert np.abs(I[y].cpu().numpy() - ref).max() <= I_TOL
+    ref = 1.0 + 0.25 * K * np.cos(2.0 * np.pi * (mx * x[4321] + my * x) / L)
+    assert np.abs(I[:, 4321].cpu().numpy() - ref).max() <= I_TOL
 
 
 @pytest.mark.parametrize("beta", [3.3, 3.67, 3.9])
