@@ -291,14 +291,22 @@ SCINT_DEV dfc ld_cluster<dfc>(unsigned addr) {
     return dfc{dfl(a, b), dfl(c, d)};
 }
 
-template <typename C, int N, int DIR, int EPT, int LW, int TWM, int CS, int S, int TS = 1>
+// PP (ping-pong, CS = 1 only): stage s writes buffer s mod 2 (buf, buf1) and stage s + 1
+// reads it, so a stage's reads and the next stage's writes touch different buffers
+// and one barrier per stage suffices (in place: two).  The last stage reads buffer
+// NSTAGE - 2; when that is buf, the next transform's first stage would overwrite it,
+// so that case keeps a barrier after the reads.
+template <typename C, int N, int DIR, int EPT, int LW, int TWM, int CS, int S, int TS = 1, bool PP = false>
 SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw,
-                         const TwiddleRegs<C, N, EPT>* tr) {
+                         const TwiddleRegs<C, N, EPT>* tr, C* buf1 = nullptr) {
     using Pl = FftPlan<N, EPT>;
     constexpr int E = Pl::E, T = Pl::T;
     constexpr int R = Pl::radix(S), P = Pl::span(S), NB = E / R;
     constexpr bool FIRST = (S == 0), LAST = (S == Pl::NSTAGE - 1);
     constexpr int HALF = N / 2;
+    static_assert(!PP || CS == 1, "ping-pong buffers are for unsplit lines");
+    C* const rbuf = PP && (S % 2 == 0) ? buf1 : buf;    // written by stage S - 1
+    C* const wbuf = PP && (S % 2 == 1) ? buf1 : buf;    // written by stage S
     C u[E];
     if constexpr (FIRST) {
         // butterfly b takes positions t + b T + r N/R = t + (b + r NB) T
@@ -311,9 +319,9 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
         for (int b = 0; b < NB; ++b) {
             // N/R is a multiple of 16 here, so pad16(i + r N/R) = pad16(i) + r (N/R)(17/16).
 #pragma unroll
-            for (int r = 0; r < R; ++r) u[b * R + r] = buf[pad16(t + b * T) * LW + r * ((N / R) + (N / R) / 16) * LW];
+            for (int r = 0; r < R; ++r) u[b * R + r] = rbuf[pad16(t + b * T) * LW + r * ((N / R) + (N / R) / 16) * LW];
         }
-        __syncthreads();
+        if constexpr (!PP || (LAST && (Pl::NSTAGE - 2) % 2 == 0)) __syncthreads();
     } else {
         // Split line: i < N/R <= N/2, so element i + r N/R is in the upper half
         // (rank 1's buffer, local index i + (r - R/2) N/R) iff r >= R/2.
@@ -369,12 +377,12 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
             int j = (i - k) * R + k;
             if constexpr (CS == 2) j &= HALF - 1;
             // P >= 16: pad16(j + r P) = pad16(j) + r P (17/16); P == 1: j = i R and r < R <= 16
-            C* dst = buf + pad16(j) * LW;
+            C* dst = wbuf + pad16(j) * LW;
 #pragma unroll
             for (int r = 0; r < R; ++r) dst[(P >= 16 ? r * (P + P / 16) : r) * LW] = u[b * R + r];
         }
         line_sync<CS>();
-        fft_stage<C, N, DIR, EPT, LW, TWM, CS, S + 1, TS>(v, buf, t, tw, tr);
+        fft_stage<C, N, DIR, EPT, LW, TWM, CS, S + 1, TS, PP>(v, buf, t, tw, tr, buf1);
     }
 }
 
@@ -393,6 +401,19 @@ template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int CS = 1>
 SCINT_DEV void fft_line_tr(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const TwiddleRegs<C, N, EPT>& tr) {
     static_assert(CS == 1 || (CS == 2 && FftPlan<N, EPT>::NSTAGE > 1 && N >= 512), "split lines need N >= 512");
     fft_stage<C, N, DIR, EPT, LW, 2, CS, 0>(v, buf, t, nullptr, &tr);
+}
+
+// Ping-pong forms (unsplit lines): buf1 is a second buffer laid out like buf.  Between
+// two ping-pong transforms of the same buffers no barrier is needed; any other write
+// to either buffer after one needs a __syncthreads first.
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0>
+SCINT_DEV void fft_line_pp(C (&v)[FftPlan<N, EPT>::E], C* buf, C* buf1, int t, const C* __restrict__ tw) {
+    static_assert(TWM != 2, "register twiddles: use fft_line_tr_pp");
+    fft_stage<C, N, DIR, EPT, LW, TWM, 1, 0, 1, true>(v, buf, t, tw, nullptr, buf1);
+}
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1>
+SCINT_DEV void fft_line_tr_pp(C (&v)[FftPlan<N, EPT>::E], C* buf, C* buf1, int t, const TwiddleRegs<C, N, EPT>& tr) {
+    fft_stage<C, N, DIR, EPT, LW, 2, 1, 0, 1, true>(v, buf, t, nullptr, &tr, buf1);
 }
 
 // ---- lines split by one radix-2 step over a two-block cluster ------------------

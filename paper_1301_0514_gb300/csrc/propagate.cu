@@ -70,6 +70,8 @@ prop_rows_kernel(PropArgs a) {
     long long* P = reinterpret_cast<long long*>(smem32 + B * BUFL) + team * NL + tl;
     float2* tws = smem32 + B * BUFL + B * NL;   // shared twiddle table (after P, 8 B per entry)
     const float2* twp = TWM == 1 ? tws : a.tw;
+    constexpr bool PP = ppp_row<N>();            // second line buffers after the table
+    float2* buf1 = smem32 + B * BUFL + B * NL + (TWM == 1 ? Pl::TWS : 0) + team * BUFL;
     TwiddleRegs<float2, N, 16> tr;
     if constexpr (TWM == 2) tr.load(a.tw, t);
     else if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
@@ -95,13 +97,17 @@ prop_rows_kernel(PropArgs a) {
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = unit_phasor(P[m * TL], S) * (sfy * __ldg(sf + t + m * T));
         }
-        if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
+        if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, -1, 16, 1>(v, buf, buf1, t, tr);
+        else if constexpr (PP) fft_line_pp<float2, N, -1, 16, 1, TWM>(v, buf, buf1, t, twp);
+        else if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
         else fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, twp);
         if constexpr (!CONJ) {
             const unsigned long long hc = a.lam.h_fx[l];
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
-            if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
+            if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, +1, 16, 1>(v, buf, buf1, t, tr);
+            else if constexpr (PP) fft_line_pp<float2, N, +1, 16, 1, TWM>(v, buf, buf1, t, twp);
+            else if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
             else fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, twp);
         }
         float2* dst = a.work + (size_t)l * N * N;
@@ -130,6 +136,8 @@ prop_cols_kernel(PropArgs a) {
     float acc[E];
     float2* tws = smem32 + W * BUFL;   // shared twiddle table (after the line buffers)
     const float2* twp = TWM == 1 ? tws : a.tw;
+    constexpr bool PP = ppp_col<N>();   // second line buffers after the table
+    float2* buf1 = smem32 + W * BUFL + (TWM == 1 ? Pl::TWS : 0) + w;
     TwiddleRegs<float2, N, kColEPT> tr;
     if constexpr (TWM == 2) tr.load(a.tw, t);
     else if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
@@ -142,7 +150,9 @@ prop_cols_kernel(PropArgs a) {
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * WL + w];
-        if constexpr (TWM == 2) fft_line_tr<float2, N, -1, kColEPT, W>(v, buf, t, tr);
+        if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, -1, kColEPT, W>(v, buf, buf1, t, tr);
+        else if constexpr (PP) fft_line_pp<float2, N, -1, kColEPT, W, TWM>(v, buf, buf1, t, twp);
+        else if constexpr (TWM == 2) fft_line_tr<float2, N, -1, kColEPT, W>(v, buf, t, tr);
         else fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
         if constexpr (CONJ) {
             // h = (Delta^2 / lambda z)^2 |FT G|^2 on the pattern grid of this wavelength (Eq. intens)
@@ -162,7 +172,9 @@ prop_cols_kernel(PropArgs a) {
             const unsigned long long hc = a.lam.h_fx[l];
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
-            if constexpr (TWM == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
+            if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, +1, kColEPT, W>(v, buf, buf1, t, tr);
+            else if constexpr (PP) fft_line_pp<float2, N, +1, kColEPT, W, TWM>(v, buf, buf1, t, twp);
+            else if constexpr (TWM == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
             else fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);
         }
         const float wl = a.lam.weight[l];

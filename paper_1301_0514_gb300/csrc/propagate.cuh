@@ -18,6 +18,14 @@
 
 namespace scint {
 
+// Ping-pong FFT buffers in the propagation passes (fft.cuh: one barrier per stage
+// instead of two) for lines that fit one block; measured on GB300 with 32
+// wavelengths: rows 1.4 % (4096) to 10 % (1024) faster, columns 1-4.5 % faster below
+// 4096 and 1.5 % slower at 4096 (172 KB of shared memory per block), which keeps one.
+#ifndef SCINT_PROP_PINGPONG
+#define SCINT_PROP_PINGPONG 1
+#endif
+
 constexpr int kRowTw = SCINT_ROW_TWIDDLES;
 constexpr int kColTw = SCINT_COL_TWIDDLES;
 constexpr int kColEPT = 16;   // values per thread in the column passes
@@ -30,6 +38,8 @@ constexpr size_t kMaxSmem = 227 * 1024;
 // own-entry arrays (fixed-point phases, accumulators) holding the N/CS entries of
 // the line that the block's threads own.
 template <int N> __host__ __device__ constexpr int pcs() { return N >= kSplitN ? 2 : 1; }
+template <int N> __host__ __device__ constexpr bool ppp_row() { return SCINT_PROP_PINGPONG && pcs<N>() == 1; }
+template <int N> __host__ __device__ constexpr bool ppp_col() { return SCINT_PROP_PINGPONG && N < 4096; }
 template <int N> __host__ __device__ constexpr int prow_twm() { return pcs<N>() == 2 ? 0 : kRowTw; }
 template <int N> __host__ __device__ constexpr int pcol_twm();   // below: depends on the shared-memory budget
 
@@ -52,7 +62,8 @@ template <int N> __host__ __device__ constexpr int pstrip() { return pcol_lines<
 
 template <int N> constexpr size_t ptws_bytes(int twm) { return twm == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0; }
 template <int N> constexpr size_t prow_smem() {
-    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) / pcs<N>() +
+    return (size_t)prow_lines<N>() * ((ppp_row<N>() ? 2 : 1) * FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) /
+               pcs<N>() +
            ptws_bytes<N>(prow_twm<N>());
 }
 // column pass: line buffers and (when it fits) the twiddle table
@@ -61,9 +72,12 @@ template <int N> __host__ __device__ constexpr size_t pcol_base_bytes() {
 }
 template <int N> __host__ __device__ constexpr int pcol_twm() {
     return pcs<N>() == 2 ? 0
-         : (kColTw == 1 && pcol_base_bytes<N>() + (size_t)FftPlan<N>::TWS * sizeof(float2) > kMaxSmem ? 2 : kColTw);
+         : (kColTw == 1 && pcol_base_bytes<N>() * (ppp_col<N>() ? 2 : 1) + (size_t)FftPlan<N>::TWS * sizeof(float2) > kMaxSmem
+                ? 2 : kColTw);
 }
-template <int N> constexpr size_t pcol_smem() { return pcol_base_bytes<N>() + ptws_bytes<N>(pcol_twm<N>()); }
+template <int N> constexpr size_t pcol_smem() {
+    return pcol_base_bytes<N>() * (ppp_col<N>() ? 2 : 1) + ptws_bytes<N>(pcol_twm<N>());
+}
 
 // rank of this block in its line's cluster (0 when lines are not split)
 template <int CS> SCINT_DEV int line_rank() {
