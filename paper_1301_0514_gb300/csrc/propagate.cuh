@@ -19,11 +19,13 @@
 namespace scint {
 
 // Ping-pong FFT buffers in the propagation passes (fft.cuh: one barrier per stage
-// instead of two) for lines that fit one block; measured on GB300 with 32
-// wavelengths: rows 1.4 % (4096) to 10 % (1024) faster, columns 1-4.5 % faster below
-// 4096 and 1.5 % slower at 4096 (172 KB of shared memory per block), which keeps one.
+// instead of two), off by default.  Measured on GB300 with 32 wavelengths, each pass
+// alone is faster with them (rows 1.4 % at 4096 to 10 % at 1024, columns 1-4.5 %
+// below 4096; 1.5 % slower at 4096, which would keep one buffer), but the batched
+// step on four lanes is 7.6 % slower (123.1 -> 132.5 ms): at 102 KB per row block two
+// blocks fill an SM's shared memory and the other lanes' kernels no longer share it.
 #ifndef SCINT_PROP_PINGPONG
-#define SCINT_PROP_PINGPONG 1
+#define SCINT_PROP_PINGPONG 0
 #endif
 
 constexpr int kRowTw = SCINT_ROW_TWIDDLES;
