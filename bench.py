@@ -63,20 +63,20 @@ def _peaks():
 def _workload(name: str, rank: int):
     from paper_1301_0514_gb300 import workloads as W
     if name == "batched":
-        items = W.config3()
+        items = W.batched_polychromatic()
         desc = ("batched: 48 screens (16 each of 1024^2, 2048^2, 4096^2, 10 km pixels, R_diff U[30,300] km) "
                 "x 32 wavelengths 400-700 nm, disk sources U[0.1,2] R_ref, 8 tracks/screen")
     elif name == "profile":
-        items = [x for x in W.config3() if x["n"] == 4096][:1]
+        items = [x for x in W.batched_polychromatic() if x["n"] == 4096][:1]
         items[0]["lambdas_nm"] = items[0]["lambdas_nm"][::4]
         desc = ("profiling case: one 4096^2 screen of the batched workload x 8 wavelengths "
                 "(~1.2 GB on the device, above the L2 size)")
-    elif name == "config4":
-        items = [W.config4(beta=11.0 / 3.0, disk=True)]
+    elif name == "large16384":
+        items = [W.large_screen_16384(beta=11.0 / 3.0, disk=True)]
         desc = ("one 16384^2 screen (lines split over two-block clusters), 5 km pixels, R_diff 100 km, "
                 "Kolmogorov, 500 nm, disk of one R_ref")
     else:
-        items = W.config2(r_diffs=(100.0,))
+        items = W.single_screens_4096(r_diffs=(100.0,))
         items[0]["lambdas_nm"] = np.array([500.0])
         desc = "single 4096^2 screen, 10 km pixels, R_diff 100 km, 500 nm, point source, 64 tracks"
     for it in items:
@@ -938,7 +938,7 @@ def run_gradient(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    items = W.config5()
+    items = W.gradient_batch_2048()
     for it in items:
         it["seed"] += 100000 * rank
     P = [S.params(**{k: it[k] for k in PARAM_KEYS}) for it in items]
@@ -1046,7 +1046,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "config4", "screen_check", "conjugate",
+    ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "large16384", "screen_check", "conjugate",
                                                               "m_sweep", "timeseries", "gradient"])
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
     ap.add_argument("--conj-n", type=int, default=4096, help="grid of the one-FFT workload")

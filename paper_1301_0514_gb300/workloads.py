@@ -8,7 +8,7 @@ inputs from here, so the CUDA path and the oracle see identical inputs.
 The shapes follow the paper's workloads (Sect. 3, Figs. 3-5): strong
 scintillation (R_diff < R_F), z0 = 160 pc, Kolmogorov and non-Kolmogorov
 screens, point and extended sources, optical/NIR passbands, long straight
-tracks.  Seeds are 20130514 + 1000 * config + item.
+tracks.  Seeds are 20130514 + 1000 * k + item, k = 1..5 for the five workloads below in order.
 """
 from __future__ import annotations
 
@@ -44,13 +44,13 @@ def random_tracks(rng: np.random.Generator, n: int, count: int, ds: float) -> np
     return np.stack([x0, y0, th, np.full(count, ds)], axis=1)
 
 
-def config1() -> List[Dict]:
+def small_screen_256() -> List[Dict]:
     """256^2 Kolmogorov screen, 20 km pixels, R_diff = 100 km, 500 nm, 160 pc, point source,
     one horizontal track through row 128 (1 px steps, 256 samples)."""
     return [_item(256, 20.0, 100.0, seed=SEED_BASE + 1000, tracks=[(0.0, 128.0, 0.0, 1.0)], n_samples=256)]
 
 
-def config2(r_diffs=(30.0, 100.0, 300.0), n: int = 4096) -> List[Dict]:
+def single_screens_4096(r_diffs=(30.0, 100.0, 300.0), n: int = 4096) -> List[Dict]:
     """4096^2 screens, 10 km pixels, R_diff in {30, 100, 300} km, 500 nm, point source,
     64 tracks at random angles (1 px steps, 2048 samples)."""
     out = []
@@ -65,7 +65,7 @@ def passband_400_700(count: int = 32) -> np.ndarray:
     return np.linspace(400.0, 700.0, count)
 
 
-def config3(sizes=(1024, 2048, 4096), per_size: int = 16, n_lambda: int = 32, tracks_per_screen: int = 8) -> List[Dict]:
+def batched_polychromatic(sizes=(1024, 2048, 4096), per_size: int = 16, n_lambda: int = 32, tracks_per_screen: int = 8) -> List[Dict]:
     """Batched polychromatic extended sources: per_size screens of each size, 10 km pixels,
     R_diff ~ U[30, 300] km at lambda_ref = 550 nm, 32 wavelengths in 400-700 nm (flat),
     projected disk radius ~ U[0.1, 2] x R_ref(lambda_ref), R_ref = lambda_ref z / R_diff."""
@@ -86,7 +86,7 @@ def config3(sizes=(1024, 2048, 4096), per_size: int = 16, n_lambda: int = 32, tr
     return out
 
 
-def config4(beta: float, disk: bool, n: int = 16384) -> Dict:
+def large_screen_16384(beta: float, disk: bool, n: int = 16384) -> Dict:
     """16384^2 screen, 5 km pixels, R_diff = 100 km, non-Kolmogorov beta, 500 nm; point source
     or a disk of one R_ref = lambda z / R_diff."""
     r_ref = 500.0 * KM_PER_NM * 160.0 * KM_PER_PC / 100.0
@@ -96,7 +96,7 @@ def config4(beta: float, disk: bool, n: int = 16384) -> Dict:
                  n_samples=n // 2)
 
 
-def config5(batch: int = 8, n: int = 2048) -> List[Dict]:
+def gradient_batch_2048(batch: int = 8, n: int = 2048) -> List[Dict]:
     """Differentiation: batch of 2048^2 screens, R_diff = 100 km, 500 nm; one track of 10^4
     samples at 0.2 px steps; the target curve comes from the screen of seed + 500."""
     out = []

@@ -103,13 +103,13 @@ def test_workspace_too_small_rejected(lib):
 
 def test_workloads_are_seeded_and_shaped():
     from paper_1301_0514_gb300 import workloads as W
-    c3 = W.config3()
+    c3 = W.batched_polychromatic()
     assert len(c3) == 48 and sorted({it["n"] for it in c3}) == [1024, 2048, 4096]
     assert all(len(it["lambdas_nm"]) == 32 for it in c3)
     assert all(30.0 <= it["r_diff_km"] <= 300.0 for it in c3)
-    again = W.config3()
+    again = W.batched_polychromatic()
     assert all(a["seed"] == b["seed"] and a["r_diff_km"] == b["r_diff_km"] for a, b in zip(c3, again))
-    c2 = W.config2()
+    c2 = W.single_screens_4096()
     assert [it["r_diff_km"] for it in c2] == [30.0, 100.0, 300.0] and c2[0]["tracks"].shape == (64, 4)
 
 

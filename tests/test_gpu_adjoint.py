@@ -82,9 +82,9 @@ def test_autograd_phi_and_rdiff():
     assert r.grad.item() == pytest.approx(gr_o, rel=1e-3)
 
 
-def test_config5_gradient_full_size():
+def test_gradient_batch_2048_full_size():
     """2048^2, R_diff = 100 km, 500 nm, one track of 10^4 samples at 0.2 px: GPU vs oracle gradient."""
-    it = W.config5(batch=1)[0]
+    it = W.gradient_batch_2048(batch=1)[0]
     p_g, p_o = gpu_params(it), oracle_params(it)
     phi = O.make_screen(p_o)
     gc, target = _oracle_gc(it, p_o, phi)

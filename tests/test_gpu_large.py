@@ -46,7 +46,7 @@ def test_fft_lines_16384(dtype, tol, direction):
 
 
 def test_screen_16384_sampled_pixels():
-    it = W.config4(beta=3.67, disk=False)
+    it = W.large_screen_16384(beta=3.67, disk=False)
     p_g, p_o = gpu_params(it), oracle_params(it)
     phi = S.make_screen(p_g)
     pix = [(0, 0), (1, 8191), (8192, 8192), (16383, 1), (5000, 12345), (12001, 777)]
@@ -84,7 +84,7 @@ def test_grating_16384_closed_form(fx, fy):
 def test_passband_16384_groups_accumulate():
     """Two wavelengths in two groups (the workspace holds one) added onto a prior map equal
     the weighted single-wavelength maps: the accumulating transposed write of the column pass."""
-    it = W.config4(beta=3.67, disk=False)
+    it = W.large_screen_16384(beta=3.67, disk=False)
     p = gpu_params(it)
     phi = S.make_screen(p)
     lams, wts = (480.0, 530.0), (0.3, 0.7)
@@ -119,8 +119,8 @@ def test_disk_filter_16384_eigenfunction(mx, my):
 
 @pytest.mark.parametrize("beta", [3.3, 3.67, 3.9])
 @pytest.mark.parametrize("disk", [False, True])
-def test_config4_pipeline_identities(beta, disk):
-    it = W.config4(beta=beta, disk=disk)
+def test_large_16384_pipeline_identities(beta, disk):
+    it = W.large_screen_16384(beta=beta, disk=disk)
     p = gpu_params(it)
     phi = S.make_screen(p)
     I = S.propagate(p, phi)

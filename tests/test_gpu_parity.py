@@ -100,9 +100,9 @@ def _intensity_case(it, lam=None):
     return I_g, I_o
 
 
-def test_config1_full_path():
+def test_small_screen_256_full_path():
     """256^2, 20 km, R_diff = 100 km, 500 nm, 160 pc: GPU screen + propagation + track vs oracle."""
-    it = W.config1()[0]
+    it = W.small_screen_256()[0]
     p_g, p_o = gpu_params(it), oracle_params(it)
     phi_t = S.make_screen(p_g)
     I_g = S.propagate(p_g, phi_t)
@@ -216,9 +216,9 @@ def test_modulation_index_fiducial_zone():
 
 
 # ---------------------------------------------------------------------------
-def test_config2_full_size_one_screen():
+def test_single_4096_full_size_one_screen():
     """4096^2, 10 km, R_diff = 300 km: whole intensity map and the 64 tracks vs the oracle."""
-    it = W.config2(r_diffs=(300.0,))[0]
+    it = W.single_screens_4096(r_diffs=(300.0,))[0]
     p_g, p_o = gpu_params(it), oracle_params(it)
     phi_g = S.make_screen(p_g)
     phi_o = O.make_screen(p_o)
@@ -239,7 +239,7 @@ def test_config2_full_size_one_screen():
 
 def test_largest_phase_screen_full_path():
     """R_diff = 30 km (phase rms ~ 60 rad, peaks ~ 300 rad), 2048^2: screen, intensity, m vs oracle."""
-    it = W.config2(r_diffs=(30.0,), n=2048)[0]
+    it = W.single_screens_4096(r_diffs=(30.0,), n=2048)[0]
     p_g, p_o = gpu_params(it), oracle_params(it)
     phi_g = S.make_screen(p_g)
     phi_o = O.make_screen(p_o)
@@ -251,9 +251,9 @@ def test_largest_phase_screen_full_path():
     assert S.modulation_index(p_g, I_g).cpu().numpy()[0] == pytest.approx(O.modulation_index_map(I_o, p_o), rel=M_TOL)
 
 
-def test_config3_like_screen_passband_and_disk():
+def test_batched_polychromatic_screen_passband_and_disk():
     """One 1024^2 screen of the batched workload: 32 wavelengths, disk source, tracks."""
-    it = [x for x in W.config3() if x["n"] == 1024][0]
+    it = [x for x in W.batched_polychromatic() if x["n"] == 1024][0]
     p_g, p_o = gpu_params(it), oracle_params(it)
     phi_g = S.make_screen(p_g)
     I_g = S.sum_passband(p_g, phi_g, it["lambdas_nm"])

@@ -88,7 +88,7 @@ def test_modulation_index_closed_form():
 
 
 def test_fiducial_zone():
-    # config-2-like, R_diff = 30 km: margin exceeds L/2 -> whole map, flagged
+    # like the 4096^2 single screens, R_diff = 30 km: margin exceeds L/2 -> whole map, flagged
     p = O.ScreenParams(n=4096, pixel_km=10.0, r_diff_km=30.0)
     assert O.fiducial_slice(p) == (0, 4096, True)
     p = O.ScreenParams(n=4096, pixel_km=10.0, r_diff_km=300.0)
