@@ -96,6 +96,24 @@ int scint_version(void);
 /* Message describing the last error on the calling thread ("" if none). */
 const char* scint_last_error(void);
 
+/*
+ * Sampling condition of Sect. 3.2.2: the pixel must resolve the screen's phase
+ * variations, pixel_km < R_diff(lambda)/2, with R_diff(lambda) =
+ * r_diff_km (lambda / lambda_ref_nm)^(2/(beta-2)) (the phase scales as
+ * lambda_ref/lambda, Sect. 3.2.4).  Returns the worst ratio
+ * 2 pixel_km / R_diff(lambda) over lambdas_nm[0..n_lambda) (host array; NULL or
+ * n_lambda <= 0: p->lambda_nm), >= 1 meaning violated; -1 on invalid arguments
+ * (scint_last_error() says why).  Host only.
+ */
+double scint_sampling_ratio(const scint_params* p, const double* lambdas_nm, int n_lambda);
+
+/* Warning left by the last propagating call on the calling thread
+ * (scint_propagate*, scint_sum_passband*, scint_lightcurve_adjoint,
+ * scint_run_batch): "" when its parameters meet the sampling condition above,
+ * else a message naming the wavelength (and, for a batch, the first item) that
+ * violates it.  Such a call still runs and returns SCINT_OK. */
+const char* scint_last_warning(void);
+
 /* Device scratch bytes that the calls below need for grid p->n when a passband
  * of n_lambda wavelengths is processed in one group (n_lambda >= 1). */
 size_t scint_workspace_bytes(const scint_params* p, int n_lambda);

@@ -10,6 +10,7 @@ from ._lib import (  # noqa: F401
     BatchItem,
     batch_items,
     batch_workspace_bytes,
+    SamplingWarning,
     ScintError,
     ScintParams,
     conjugate_pixel_km,
@@ -18,6 +19,7 @@ from ._lib import (  # noqa: F401
     curve_power_spectrum,
     fft_lines,
     fiducial_zone,
+    last_warning,
     lib,
     lightcurve,
     lightcurve_adjoint,
@@ -34,6 +36,7 @@ from ._lib import (  # noqa: F401
     rdiff_gradient,
     release,
     run_batch,
+    sampling_ratio,
     smooth_source,
     spectrum_rec,
     structure_function_rec,

@@ -9,6 +9,7 @@ call raises: there is no fallback implementation.
 from __future__ import annotations
 
 import ctypes
+import warnings
 import os
 from typing import Optional, Sequence
 
@@ -108,6 +109,8 @@ def lib() -> ctypes.CDLL:
     sig = {
         "scint_version": ([], _i),
         "scint_last_error": ([], ctypes.c_char_p),
+        "scint_last_warning": ([], ctypes.c_char_p),
+        "scint_sampling_ratio": ([_P, _vp, _i], ctypes.c_double),
         "scint_workspace_bytes": ([_P, _i], _sz),
         "scint_make_screen": ([_P, _vp, _vp, _sz, _vp], _i),
         "scint_propagate": ([_P, _vp, _vp, _vp, _sz, _vp], _i),
@@ -151,6 +154,35 @@ def _check(rc: int):
         raise ScintError(rc, lib().scint_last_error().decode())
 
 
+class SamplingWarning(UserWarning):
+    """The pixel does not resolve the screen's phase variations (Sect. 3.2.2:
+    pixel < R_diff(lambda)/2); the call still ran."""
+
+
+def _check_warn(rc: int):
+    """_check, then the library's sampling warning (if any) as a SamplingWarning."""
+    _check(rc)
+    msg = lib().scint_last_warning().decode()
+    if msg:
+        warnings.warn(msg, SamplingWarning, stacklevel=3)
+
+
+def last_warning() -> str:
+    return lib().scint_last_warning().decode()
+
+
+def sampling_ratio(p: "ScintParams", lambdas_nm=None) -> float:
+    """Worst 2 pixel / R_diff(lambda) over the wavelengths (>= 1 violates Sect. 3.2.2)."""
+    if lambdas_nm is None:
+        r = lib().scint_sampling_ratio(ctypes.byref(p), None, 0)
+    else:
+        lam = np.ascontiguousarray(lambdas_nm, dtype=np.float64)
+        r = lib().scint_sampling_ratio(ctypes.byref(p), lam.ctypes.data_as(ctypes.c_void_p), len(lam))
+    if r < 0:
+        raise ScintError(1, lib().scint_last_error().decode())   # SCINT_EINVAL
+    return r
+
+
 def _stream(stream) -> int:
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -189,7 +221,7 @@ def propagate(p: ScintParams, phi: torch.Tensor, out: Optional[torch.Tensor] = N
     if out is None:
         out = torch.empty((p.n, p.n), dtype=torch.float32, device=phi.device)
     ws, wp, wb = _workspace(p, 1, workspace, phi.device)
-    _check(lib().scint_propagate(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
+    _check_warn(lib().scint_propagate(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
                                  _dev(out, torch.float32, p.n * p.n, "intensity"), wp, wb, _stream(stream)))
     return out
 
@@ -204,7 +236,7 @@ def sum_passband(p: ScintParams, phi: torch.Tensor, lambdas_nm: Sequence[float],
     if out is None:
         out = torch.empty((p.n, p.n), dtype=torch.float32, device=phi.device)
     ws, wp, wb = _workspace(p, len(lam), workspace, phi.device)
-    _check(lib().scint_sum_passband(
+    _check_warn(lib().scint_sum_passband(
         ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
         lam.ctypes.data_as(ctypes.c_void_p), None if w is None else w.ctypes.data_as(ctypes.c_void_p),
         len(lam), _dev(out, torch.float32, p.n * p.n, "intensity"), int(bool(accumulate)), wp, wb,
@@ -269,7 +301,7 @@ def propagate_conjugate(p: ScintParams, phi: torch.Tensor, out: Optional[torch.T
     if out is None:
         out = torch.empty((p.n, p.n), dtype=torch.float32, device=phi.device)
     ws, wp, wb = _workspace(p, 1, workspace, phi.device)
-    _check(lib().scint_propagate_conjugate(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
+    _check_warn(lib().scint_propagate_conjugate(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
                                            _dev(out, torch.float32, p.n * p.n, "intensity"), wp, wb,
                                            _stream(stream)))
     return out
@@ -289,7 +321,7 @@ def sum_passband_conjugate(p: ScintParams, phi: torch.Tensor, lambdas_nm: Sequen
         wp, wb = None, 0
     else:
         wp, wb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
-    _check(lib().scint_sum_passband_conjugate(
+    _check_warn(lib().scint_sum_passband_conjugate(
         ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
         lam.ctypes.data_as(ctypes.c_void_p), None if w is None else w.ctypes.data_as(ctypes.c_void_p),
         len(lam), _dev(out, torch.float32, p.n * p.n, "intensity"), int(bool(accumulate)), wp, wb,
@@ -346,7 +378,7 @@ def lightcurve_adjoint(p: ScintParams, phi: torch.Tensor, lambdas_nm, tracks, n_
     if out is None:
         out = torch.empty((p.n, p.n), dtype=torch.float64, device=phi.device)
     ws, wp, wb = _workspace(p, len(lam), workspace, phi.device)
-    _check(lib().scint_lightcurve_adjoint(
+    _check_warn(lib().scint_lightcurve_adjoint(
         ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"), lam.ctypes.data_as(ctypes.c_void_p),
         None if w is None else w.ctypes.data_as(ctypes.c_void_p), len(lam),
         tr.ctypes.data_as(ctypes.c_void_p), tr.shape[0], n_samples,
@@ -414,7 +446,7 @@ def run_batch(items, lambdas_nm, weights=None, n_lanes: int = 0, workspace: Opti
         if not (workspace.is_cuda and workspace.is_contiguous()):
             raise ValueError("workspace must be a contiguous CUDA tensor")
         wp, wb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
-    _check(lib().scint_run_batch(arr, len(arr), lam.ctypes.data_as(ctypes.c_void_p),
+    _check_warn(lib().scint_run_batch(arr, len(arr), lam.ctypes.data_as(ctypes.c_void_p),
                                  None if w is None else w.ctypes.data_as(ctypes.c_void_p), len(lam),
                                  int(n_lanes), wp, wb, _stream(stream)))
     return arr

@@ -27,6 +27,7 @@ using namespace scint;
 namespace {
 
 thread_local std::string g_error;
+thread_local std::string g_warning;
 
 int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -83,6 +84,29 @@ double taper_margin(const scint_params* p, double lambda_nm) {
 }
 double diffraction_radius(const scint_params* p, double lambda_nm) {
     return p->r_diff_km * std::pow(lambda_nm / p->lambda_ref_nm, 2.0 / (p->beta - 2.0));
+}
+// Sampling condition of Sect. 3.2.2: the pixel must resolve the phase variations,
+// Delta < R_diff(lambda) / 2.  Worst ratio 2 Delta / R_diff(lambda) over the wavelengths
+// (the smallest wavelength has the smallest R_diff); >= 1 violates it.
+double sampling_ratio(const scint_params* p, const double* lambdas, int n_lambda) {
+    double worst = 0.0;
+    for (int i = 0; i < n_lambda; ++i) worst = std::fmax(worst, 2.0 * p->pixel_km / diffraction_radius(p, lambdas[i]));
+    return worst;
+}
+// Record a warning (the call still succeeds) when the condition is violated.
+void note_sampling(const scint_params* p, const double* lambdas, int n_lambda, int item = -1) {
+    int worst = 0;
+    for (int i = 1; i < n_lambda; ++i)
+        if (diffraction_radius(p, lambdas[i]) < diffraction_radius(p, lambdas[worst])) worst = i;
+    const double rd = diffraction_radius(p, lambdas[worst]);
+    if (2.0 * p->pixel_km < rd) return;
+    char buf[320];
+    snprintf(buf, sizeof buf,
+             "%spixel %.6g km >= R_diff/2 = %.6g km at %.6g nm: the screen does not resolve its phase "
+             "variations (Sect. 3.2.2 needs pixel < R_diff/2)",
+             item >= 0 ? (std::string("item ") + std::to_string(item) + ": ").c_str() : "", p->pixel_km, 0.5 * rd,
+             lambdas[worst]);
+    g_warning = buf;
 }
 double refraction_radius(const scint_params* p, double lambda_nm) {
     return lz_km2(lambda_nm, p->z_pc) / diffraction_radius(p, lambda_nm);
@@ -375,6 +399,8 @@ int passband_impl(const scint_params* p, const double* phi, const double* lambda
     int rc = check_passband(p, lambdas, weights, n_lambda);
     if (rc) return rc;
     if (!phi || !intensity) return fail(SCINT_EINVAL, "phi and intensity must be device pointers");
+    g_warning.clear();
+    note_sampling(p, lambdas, n_lambda);
     std::vector<double> w(n_lambda, 1.0 / n_lambda);
     if (weights) w.assign(weights, weights + n_lambda);
     const int n = p->n;
@@ -410,6 +436,8 @@ int conj_impl(const scint_params* p, const double* phi, const double* lambdas, c
     int rc = check_passband(p, lambdas, weights, n_lambda);
     if (rc) return rc;
     if (!phi || !intensity) return fail(SCINT_EINVAL, "phi and intensity must be device pointers");
+    g_warning.clear();
+    note_sampling(p, lambdas, n_lambda);
     const int n = p->n;
     std::vector<double> w(n_lambda, 1.0 / n_lambda);
     if (weights) w.assign(weights, weights + n_lambda);
@@ -523,6 +551,10 @@ namespace scint {
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 int clear_error() { return ok(); }
 const char* last_error() { return g_error.c_str(); }
+void sampling_warning(const scint_params* p, const double* lambdas, int n_lambda, int item, bool clear) {
+    if (clear) g_warning.clear();
+    if (g_warning.empty()) note_sampling(p, lambdas, n_lambda, item);
+}
 int validate_params(const scint_params* p) { return check_params(p); }
 int validate_passband(const scint_params* p, const double* lambdas, const double* weights, int n_lambda) {
     return check_passband(p, lambdas, weights, n_lambda);
@@ -574,6 +606,20 @@ extern "C" {
 int scint_version(void) { return 100; }
 
 const char* scint_last_error(void) { return g_error.c_str(); }
+
+const char* scint_last_warning(void) { return g_warning.c_str(); }
+
+double scint_sampling_ratio(const scint_params* p, const double* lambdas_nm, int n_lambda) {
+    if (check_params(p)) return -1.0;
+    if (!lambdas_nm || n_lambda <= 0) return sampling_ratio(p, &p->lambda_nm, 1);
+    for (int i = 0; i < n_lambda; ++i)
+        if (!(lambdas_nm[i] > 0) || !std::isfinite(lambdas_nm[i])) {
+            fail(SCINT_EINVAL, "lambda %d must be > 0", i);
+            return -1.0;
+        }
+    ok();
+    return sampling_ratio(p, lambdas_nm, n_lambda);
+}
 
 size_t scint_workspace_bytes(const scint_params* p, int n_lambda) {
     if (check_params(p) || n_lambda < 1) return 0;
@@ -817,6 +863,8 @@ int scint_lightcurve_adjoint(const scint_params* p, const double* phi, const dou
         if (taper_margin(p, lambdas_nm[i]) > 0.5 * screen_len(p))
             return fail(SCINT_EINVAL, "taper margin exceeds half the screen");
     }
+    g_warning.clear();
+    note_sampling(p, lambdas_nm, n_lambda);
     const int n = p->n;
     int g = n_lambda;
     if (workspace) {

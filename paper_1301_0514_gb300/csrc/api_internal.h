@@ -16,6 +16,9 @@ int set_error(int code, const char* msg);
 // Clear the calling thread's last-error message; returns SCINT_OK.
 int clear_error();
 const char* last_error();
+// The sampling warning of Sect. 3.2.2 (pixel >= R_diff(lambda)/2) for one screen,
+// "item i: ..." for i >= 0; clear = start over, else keep the first warning.
+void sampling_warning(const scint_params* p, const double* lambdas, int n_lambda, int item, bool clear);
 
 // Host checks of one screen's parameters, and of a passband for it (the same
 // checks, with the same messages, as the single-screen entry points).

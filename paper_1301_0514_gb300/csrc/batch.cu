@@ -252,6 +252,8 @@ int scint_run_batch(const scint_batch_item* items, int n_items, const double* la
         }
     }
     if (first_rc) return set_error(first_rc, first_msg.c_str());
+    // the items' own calls each replaced the warning; report the first item that warns
+    for (int i = 0; i < n_items; ++i) scint::sampling_warning(&items[i].params, lambdas_nm, n_lambda, i, i == 0);
     return scint::clear_error();
 }
 

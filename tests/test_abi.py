@@ -232,3 +232,22 @@ def test_wavelength_count_limits(lib):
     nan_w = (ctypes.c_double * 2)(0.5, float("nan"))
     assert lib.scint_sum_passband(ctypes.byref(p), ctypes.c_void_p(16), lam, nan_w, 2, ctypes.c_void_p(16), 0,
                                   None, 0, None) == 1
+
+
+def test_sampling_ratio_closed_form(lib):
+    """Sect. 3.2.2 asks pixel < R_diff(lambda)/2, R_diff(lambda) = R_diff (lambda/lambda_ref)^(2/(beta-2))
+    (phase ~ lambda_ref/lambda; Kolmogorov R_diff ~ lambda^(6/5)); the ratio is checked on the host."""
+    p = S.params(n=256, pixel_km=20.0, r_diff_km=100.0, lambda_nm=500.0, lambda_ref_nm=500.0)
+    assert S.sampling_ratio(p) == pytest.approx(0.4, rel=1e-15)
+    q = S.params(n=256, pixel_km=20.0, r_diff_km=100.0, beta=11.0 / 3.0, lambda_nm=550.0, lambda_ref_nm=550.0)
+    want = 40.0 / (100.0 * (400.0 / 550.0) ** 1.2)           # the shortest wavelength has the smallest R_diff
+    assert S.sampling_ratio(q, [700.0, 400.0, 550.0]) == pytest.approx(want, rel=1e-13)
+    b = S.params(n=256, pixel_km=20.0, r_diff_km=100.0, beta=3.1, lambda_nm=550.0, lambda_ref_nm=550.0)
+    assert S.sampling_ratio(b, [800.0]) == pytest.approx(40.0 / (100.0 * (800.0 / 550.0) ** (2.0 / 1.1)), rel=1e-13)
+    # pixel = R_diff/2 exactly is on the violating side
+    assert S.sampling_ratio(S.params(n=256, pixel_km=50.0, r_diff_km=100.0)) == pytest.approx(1.0, rel=1e-15)
+    with pytest.raises(S.ScintError):
+        S.sampling_ratio(S.params(n=256, pixel_km=-1.0, r_diff_km=100.0))
+    with pytest.raises(S.ScintError):
+        S.sampling_ratio(p, [500.0, -3.0])
+    assert S.last_warning() == ""     # nothing propagated on this thread
