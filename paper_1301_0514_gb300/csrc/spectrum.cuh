@@ -45,8 +45,31 @@ struct BinValue {
     double2 d;
     float2 f;
 };
+SCINT_DEV u32x4 bin_words(const SynthArgs& a, int kx, int ky) {
+    return philox4x32_10(u32x4{(uint32_t)kx, (uint32_t)ky, a.screen_id, 0u}, a.key0, a.key1);
+}
+// amplitude sqrt(L^2 S(q)) (with the 1/sqrt(2)) from m2 = mx^2 + my^2 > 0, in each precision
+SCINT_DEV double amplitude_low(const SynthArgs& a, int m2) { return a.amp * pow((double)m2, a.neg_beta_4); }
+SCINT_DEV float amplitude_high(const SynthArgs& a, int m2) { return a.amp32 * powf((float)m2, a.neg_beta_4_32); }
+// sig (g_re + i g_im) from a bin's Philox words, Box-Muller in FP64 ...
+SCINT_DEV double2 shaped_low(const u32x4& w, double sig) {
+    const double ub = uniform53(w.w, w.z);
+    const double r = sqrt(2.0 * neg_log_ua64(w));
+    double sn, cs;
+    sincospi(2.0 * ub, &sn, &cs);
+    return make_double2(sig * r * cs, sig * r * sn);
+}
+// ... and in FP32 with the same 53-bit uniforms, each rounded once to float
+SCINT_DEV float2 shaped_high(const u32x4& w, float sig) {
+    const float r = sqrtf(2.0f * neg_log_ua32(w));
+    const float tb = fmaf((float)(w.z >> 11), 0x1.0p-52f, (float)w.w * 0x1.0p-31f) + 0x1.0p-53f;  // 2 u_b
+    float sn, cs;
+    sincospif(tb, &sn, &cs);
+    return make_float2(sig * r * cs, sig * r * sn);
+}
+
 SCINT_DEV BinValue spectrum_value(const SynthArgs& a, int kx, int ky) {
-    const u32x4 w = philox4x32_10(u32x4{(uint32_t)kx, (uint32_t)ky, a.screen_id, 0u}, a.key0, a.key1);
+    const u32x4 w = bin_words(a, kx, ky);
     const int mx = signed_freq(kx, a.n), my = signed_freq(ky, a.n);
     const int m2 = mx * mx + my * my;
     BinValue v;
@@ -55,22 +78,11 @@ SCINT_DEV BinValue spectrum_value(const SynthArgs& a, int kx, int ky) {
     v.f = make_float2(0.0f, 0.0f);
     if (m2 == 0) return v;
     if (abs(mx) <= kLowK && abs(my) <= kLowK) {
-        const double ub = uniform53(w.w, w.z);
-        const double r = sqrt(2.0 * neg_log_ua64(w));
-        double sn, cs;
-        sincospi(2.0 * ub, &sn, &cs);
-        const double sig = a.amp * pow((double)m2, a.neg_beta_4);
-        v.d = make_double2(sig * r * cs, sig * r * sn);
+        v.d = shaped_low(w, amplitude_low(a, m2));
         return v;
     }
-    // FP32 with the same 53-bit uniforms, each rounded once to float
-    const float r = sqrtf(2.0f * neg_log_ua32(w));
-    const float tb = fmaf((float)(w.z >> 11), 0x1.0p-52f, (float)w.w * 0x1.0p-31f) + 0x1.0p-53f;  // 2 u_b
-    float sn, cs;
-    sincospif(tb, &sn, &cs);
-    const float sig = a.amp32 * powf((float)m2, a.neg_beta_4_32);
     v.low = false;
-    v.f = make_float2(sig * r * cs, sig * r * sn);
+    v.f = shaped_high(w, amplitude_high(a, m2));
     return v;
 }
 
@@ -88,17 +100,40 @@ SCINT_DEV dfc spectrum_bin_df(const SynthArgs& a, int kx, int ky) {
     return dfc{dfl(v.f.x, 0.0f), dfl(v.f.y, 0.0f)};
 }
 
+// F at (kx, ky) and at the mirror bin (-kx, -ky) mod n, as double-floats: the same values
+// as two spectrum_bin_df calls, with the amplitude (which depends on |k| only, and so is the
+// same for both) computed once.
+SCINT_DEV void spectrum_pair_df(const SynthArgs& a, int kx, int ky, dfc& f, dfc& g) {
+    const int n = a.n;
+    const u32x4 w1 = bin_words(a, kx, ky), w2 = bin_words(a, (n - kx) & (n - 1), (n - ky) & (n - 1));
+    const int mx = signed_freq(kx, n), my = signed_freq(ky, n);
+    const int m2 = mx * mx + my * my;
+    if (m2 == 0) {
+        f = g = dfc{dfl(0.0f, 0.0f), dfl(0.0f, 0.0f)};
+    } else if (abs(mx) <= kLowK && abs(my) <= kLowK) {
+        const double sig = amplitude_low(a, m2);
+        const double2 d1 = shaped_low(w1, sig), d2 = shaped_low(w2, sig);
+        f = dfc{dfl(d1.x), dfl(d1.y)};
+        g = dfc{dfl(d2.x), dfl(d2.y)};
+    } else {
+        const float sig = amplitude_high(a, m2);
+        const float2 v1 = shaped_high(w1, sig), v2 = shaped_high(w2, sig);
+        f = dfc{dfl(v1.x, 0.0f), dfl(v1.y, 0.0f)};
+        g = dfc{dfl(v2.x, 0.0f), dfl(v2.y, 0.0f)};
+    }
+}
+
 // |F[ky][kx]|^2 = sigma^2 (g_re^2 + g_im^2) / 2 = sigma^2 (-2 ln u_a) / 2 of a
 // bin with Philox words w and m2 = mx^2 + my^2 > 0 (the Box-Muller angle
 // cancels), in the precision spectrum_bin uses for it: FP64 for the low bins
 // (|mx|, |my| <= kLowK), FP32 for the others.
 SCINT_DEV bool low_bin(int mx, int my) { return abs(mx) <= kLowK && abs(my) <= kLowK; }
 SCINT_DEV double power_low(const SynthArgs& a, const u32x4& w, int m2) {
-    const double sig = a.amp * pow((double)m2, a.neg_beta_4);
+    const double sig = amplitude_low(a, m2);
     return sig * sig * (2.0 * neg_log_ua64(w));
 }
 SCINT_DEV float power_high(const SynthArgs& a, const u32x4& w, int m2) {
-    const float sig = a.amp32 * powf((float)m2, a.neg_beta_4_32);
+    const float sig = amplitude_high(a, m2);
     return sig * sig * (2.0f * neg_log_ua32(w));
 }
 

@@ -81,9 +81,8 @@ template <int CS> SCINT_DEV int synth_rank() {
 // F_h(ky, kx) = (F(ky, kx) + conj F(-ky, -kx)) / 2 (the halving is exact)
 SCINT_DEV dfl half(dfl v) { return dfl(0.5f * v.hi, 0.5f * v.lo); }
 SCINT_DEV dfc hermitian_bin(const SynthArgs& a, int kx, int ky) {
-    const int n = a.n;
-    const dfc f = spectrum_bin_df(a, kx, ky);
-    const dfc g = spectrum_bin_df(a, (n - kx) & (n - 1), (n - ky) & (n - 1));
+    dfc f, g;
+    spectrum_pair_df(a, kx, ky, f, g);
     return dfc{half(f.x + g.x), half(f.y - g.y)};
 }
 
