@@ -41,6 +41,15 @@ int scint_noise_spectrum(const scint_params* p, double* F, void* stream);
 int scint_fft_lines32(int n, int dir, float* data, int n_lines, void* stream);
 int scint_fft_lines64(int n, int dir, double* data, int n_lines, void* stream);
 
+/*
+ * The propagation passes' fixed-point phase (exact mod 2 pi reduction, Sect. 3.2.4
+ * phi_lambda = phi lambda_ref / lambda): P_i = round(phi_i 2^32 / 2 pi) as the row
+ * passes compute it: one FP64 product, rounded to the nearest integer (clamped to the
+ * int64 range).
+ *   phi  device, n doubles;  P  device, n int64.  n >= 0.
+ */
+int scint_phase_fixed(const double* phi, int64_t* P, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,7 @@ from ._lib import (  # noqa: F401
     noise_spectrum,
     noise_words,
     params,
+    phase_fixed,
     profile_enable,
     profile_read,
     propagate,

@@ -124,6 +124,7 @@ def lib() -> ctypes.CDLL:
         "scint_noise_words": ([_P, _vp, _vp], _i),
         "scint_noise_spectrum": ([_P, _vp, _vp], _i),
         "scint_fft_lines32": ([_i, _i, _vp, _i, _vp], _i),
+        "scint_phase_fixed": ([_vp, _vp, ctypes.c_int64, _vp], _i),
         "scint_fft_lines64": ([_i, _i, _vp, _i, _vp], _i),
         "scint_lightcurve_adjoint": ([_P, _vp, _vp, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp, _sz, _vp], _i),
         "scint_rdiff_gradient": ([_P, _vp, _vp, _vp, _vp, _sz, _vp], _i),
@@ -509,6 +510,17 @@ def noise_words(p: ScintParams, stream=None, device="cuda") -> torch.Tensor:
 def noise_spectrum(p: ScintParams, stream=None, device="cuda") -> torch.Tensor:
     out = torch.empty((p.n, p.n), dtype=torch.complex128, device=device)
     _check(lib().scint_noise_spectrum(ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def phase_fixed(phi: torch.Tensor, stream=None) -> torch.Tensor:
+    """The propagation passes' fixed-point phase round(phi 2^32 / 2 pi) (int64) of a CUDA
+    float64 tensor (test hook)."""
+    if not (phi.is_cuda and phi.is_contiguous() and phi.dtype == torch.float64):
+        raise ValueError("phi must be a contiguous float64 CUDA tensor")
+    out = torch.empty(phi.shape, dtype=torch.int64, device=phi.device)
+    _check(lib().scint_phase_fixed(ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                   phi.numel(), _stream(stream)))
     return out
 
 

@@ -190,11 +190,25 @@ cudaError_t launch_adj_rows(const AdjArgs& a, cudaStream_t s) {
 }
 
 // ---- dL/dR_diff = ((2 - beta) / (2 R_diff)) sum phi g_phi (FP64) ----------------------
+// Block partials of sum a_i b_i, each thread over a fixed strided set of i with four loads
+// of each array in flight (one dependent load-FMA chain per thread left the loop latency-bound).
 __global__ void __launch_bounds__(256) dot_partial_kernel(const double* a, const double* b, long long n,
                                                           double* partial) {
-    double s = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        s = fma(a[i], b[i], s);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        const double a0 = __ldg(a + i), a1 = __ldg(a + i + stride), a2 = __ldg(a + i + 2 * stride),
+                     a3 = __ldg(a + i + 3 * stride);
+        const double b0 = __ldg(b + i), b1 = __ldg(b + i + stride), b2 = __ldg(b + i + 2 * stride),
+                     b3 = __ldg(b + i + 3 * stride);
+        s0 = fma(a0, b0, s0);
+        s1 = fma(a1, b1, s1);
+        s2 = fma(a2, b2, s2);
+        s3 = fma(a3, b3, s3);
+    }
+    for (; i < n; i += stride) s0 = fma(__ldg(a + i), __ldg(b + i), s0);
+    double s = (s0 + s1) + (s2 + s3);
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     __shared__ double sw[8];
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;

@@ -20,6 +20,7 @@
 namespace scint {
 cudaError_t launch_fft_lines32(int n, int dir, float2* data, int n_lines, const float2* tw, cudaStream_t s);
 cudaError_t launch_fft_lines64(int n, int dir, double2* data, int n_lines, const double2* tw, cudaStream_t s);
+cudaError_t launch_phase_fixed(const double* phi, long long* P, long long n, cudaStream_t s);
 }
 
 using namespace scint;
@@ -1107,6 +1108,13 @@ int scint_noise_spectrum(const scint_params* p, double* F, void* stream) {
     if (!F) return fail(SCINT_EINVAL, "F must be a device pointer");
     SCINT_CUDA(launch_noise_spectrum(synth_args(p), reinterpret_cast<double2*>(F),
                                      static_cast<cudaStream_t>(stream)));
+    return ok();
+}
+
+int scint_phase_fixed(const double* phi, int64_t* P, int64_t n, void* stream) {
+    if (n < 0) return fail(SCINT_EINVAL, "n=%lld must be >= 0", (long long)n);
+    if (n > 0 && (!phi || !P)) return fail(SCINT_EINVAL, "phi and P must be device pointers");
+    SCINT_CUDA(launch_phase_fixed(phi, reinterpret_cast<long long*>(P), (long long)n, static_cast<cudaStream_t>(stream)));
     return ok();
 }
 

@@ -1,8 +1,11 @@
 // Standalone line FFTs for the inspection entry points (same device code as the
 // propagation and synthesis passes).
+#include <algorithm>
+
 #include "dispatch.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "propagate.cuh"
 
 namespace scint {
 
@@ -68,6 +71,17 @@ cudaError_t launch_fft_lines32(int n, int dir, float2* data, int n_lines, const 
 }
 cudaError_t launch_fft_lines64(int n, int dir, double2* data, int n_lines, const double2* tw, cudaStream_t s) {
     return launch_fft_lines<double2>(n, dir, data, n_lines, tw, s);
+}
+
+__global__ void phase_fixed_kernel(const double* phi, long long* P, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        P[i] = phase_fixed(phi[i]);
+}
+cudaError_t launch_phase_fixed(const double* phi, long long* P, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    phase_fixed_kernel<<<(unsigned)blocks, 256, 0, s>>>(phi, P, n);
+    return cudaGetLastError();
 }
 
 }  // namespace scint
