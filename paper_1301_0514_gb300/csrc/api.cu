@@ -486,6 +486,7 @@ int conj_impl(const scint_params* p, const double* phi, const double* lambdas, c
         ta.sf = cg.take<float>((size_t)gg * n * 4);
         pa.sf = ta.sf;
         pa.work = cg.take<float2>((size_t)gg * n * n * 8);
+        pa.scratch = n >= kSplitN ? cg.take<float>((size_t)n * n * 4) : nullptr;
         pa.intensity = intensity;
         pa.accumulate = accumulate || l0 > 0;
         pa.conj.direct = direct ? 1 : 0;

@@ -326,6 +326,110 @@ __global__ void __launch_bounds__(psplit_threads<N>(), 1) prop_cols_split_kernel
     }
 }
 
+// One-FFT mode (Eq. intens, Eq. Gxy) at N = 16384: forward transforms only, so the
+// decimation-in-frequency split alone divides them (block r makes the frequencies
+// 2k + r).  The row pass copies the partner's half of the row's phases once per row
+// (split arrive/wait around the next row's fill) and writes X(2k + r); the column pass
+// needs nothing from its partner: both blocks read the whole column (the second read
+// from L2) and each writes its parity's pattern rows, column-major.
+template <int N>
+__global__ void __launch_bounds__(psplit_threads<N>(), 1) conj_rows_split_kernel(PropArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E, W = pstrip<N>();
+    extern __shared__ float2 smem32[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    float2* buf = smem32;
+    long long* P = reinterpret_cast<long long*>(smem32 + Pl::BUF);
+    TwiddleRegs<float2, H2, 16> tr;
+    tr.load(a.tw, t, 2);
+    bool first = true;
+#pragma unroll 1
+    for (int y = blockIdx.x / 2; y < N; y += gridDim.x / 2) {
+        if (!first) cluster_wait();     // the partner has copied this block's previous phases
+        first = false;
+        const double* phi = a.phi + (size_t)y * N + r * H2;
+#pragma unroll
+        for (int m = 0; m < E; ++m) P[r * H2 + t + m * T] = phase_fixed(phi[t + m * T]);
+        line_sync<2>();
+        const unsigned pp = cluster_addr(P, (unsigned)(r ^ 1)) + (unsigned)(((r ^ 1) * H2 + t) * sizeof(long long));
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            P[(r ^ 1) * H2 + t + m * T] = ld_cluster<long long>(pp + (unsigned)(m * T * sizeof(long long)));
+        cluster_arrive();
+#pragma unroll 1
+        for (int l = 0; l < a.lam.count; ++l) {
+            const unsigned long long S = a.lam.scale_fx[l], C = a.conj.chirp_fx[l];
+            const float* sf = a.sf + (size_t)l * N;
+            const float sfy = sf[y];
+            const unsigned long long cy = chirp_turns(C, y, N);
+            float2 v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = t + m * T;
+                // G = SF SF exp(i (phi s + |x_1|^2 / 2 R_F^2)) (-1)^(x + y), Eq. Gxy
+                const float2 x0 = unit_phasor(P[e], S, cy + chirp_turns(C, e, N)) * (sfy * __ldg(sf + e));
+                const float2 x1 = unit_phasor(P[e + H2], S, cy + chirp_turns(C, e + H2, N)) * (sfy * __ldg(sf + e + H2));
+                v[m] = split_dif(x0, x1, r, e, a.tw);
+            }
+            fft_line_tr<float2, H2, -1, 16, 1>(v, buf, t, tr);
+            float2* dst = a.work + (size_t)l * N * N;
+#pragma unroll
+            for (int m = 0; m < E; ++m) dst[strip_index<W>(y, 2 * (t + m * T) + r, N)] = v[m];
+        }
+    }
+    if (!first) cluster_wait();
+}
+
+template <int N>
+__global__ void __launch_bounds__(psplit_threads<N>(), 1) conj_cols_split_kernel(PropArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E, WL = pstrip<N>();
+    extern __shared__ float2 smem32[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    float2* buf = smem32;
+    float2* tws = smem32 + Pl::BUF;
+    fill_twiddle_table<float2, H2>(tws, a.tw, t, T, 2);
+    __syncthreads();
+#pragma unroll 1
+    for (int x = blockIdx.x / 2; x < N; x += gridDim.x / 2) {
+        float acc[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) acc[m] = 0.0f;
+#pragma unroll 1
+        for (int l = 0; l < a.lam.count; ++l) {
+            const float2* src = a.work + (size_t)l * N * N + (size_t)(x / WL) * N * WL + (x % WL);
+            float2 v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = t + m * T;
+                v[m] = split_dif(src[(size_t)e * WL], src[(size_t)(e + H2) * WL], r, e, a.tw);
+            }
+            fft_line<float2, H2, -1, 16, 1, 1, 1>(v, buf, t, tws);
+            // h = (Delta^2 / lambda z)^2 |FT G|^2 on the pattern grid of this wavelength (Eq. intens)
+            const float nrm = a.conj.norm[l];
+            if (a.conj.direct) {
+                const float wn = a.lam.weight[l] * nrm;
+#pragma unroll
+                for (int m = 0; m < E; ++m) acc[m] = fmaf(wn, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m]);
+            } else {
+                float* pat = a.conj.pattern + (size_t)l * N * N + (size_t)x * N;
+#pragma unroll
+                for (int m = 0; m < E; ++m) pat[2 * (t + m * T) + r] = nrm * fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
+            }
+        }
+        if (a.conj.direct) {
+            // column-major, transposed into place by transpose_add_kernel
+            float* col = a.scratch + (size_t)x * N;
+#pragma unroll
+            for (int m = 0; m < E; ++m) col[2 * (t + m * T) + r] = acc[m];
+        }
+    }
+}
+
 // intensity (+)= the transpose of the column-major map src, in 32 x 32 tiles through
 // shared memory (reads and writes both coalesced); n is a multiple of 32
 __global__ void __launch_bounds__(256) transpose_add_kernel(const float* __restrict__ src, float* dst, int n,
@@ -351,15 +455,14 @@ cudaError_t launch_rows(const PropArgs& a, cudaStream_t s) {
         if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            if constexpr (pcs<N>() == 2 && !CONJ) {
+            if constexpr (pcs<N>() == 2) {
                 static_assert(prow_split_smem<N>() <= kMaxSmem, "split row pass does not fit");
-                cudaError_t e = set_smem(prop_rows_split_kernel<N>, prow_split_smem<N>());
+                auto k = CONJ ? conj_rows_split_kernel<N> : prop_rows_split_kernel<N>;
+                cudaError_t e = set_smem(k, prow_split_smem<N>());
                 int nc = 0;
-                if (e == cudaSuccess)
-                    e = active_clusters(prop_rows_split_kernel<N>, 2, psplit_threads<N>(), prow_split_smem<N>(), &nc);
+                if (e == cudaSuccess) e = active_clusters(k, 2, psplit_threads<N>(), prow_split_smem<N>(), &nc);
                 if (e != cudaSuccess) return e;
-                return launch_k(prop_rows_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()),
-                                prow_split_smem<N>(), s, a);
+                return launch_k(k, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()), prow_split_smem<N>(), s, a);
             } else {
                 cudaError_t e = set_smem(prop_rows_kernel<N, CONJ>, prow_smem<N>());
                 if (e != cudaSuccess) return e;
@@ -377,17 +480,17 @@ cudaError_t launch_cols(const PropArgs& a, cudaStream_t s) {
         if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            if constexpr (pcs<N>() == 2 && !CONJ) {
+            if constexpr (pcs<N>() == 2) {
                 static_assert(pcol_split_smem<N>() <= kMaxSmem, "split column pass does not fit");
-                if (!a.scratch) return cudaErrorInvalidValue;
-                cudaError_t e = set_smem(prop_cols_split_kernel<N>, pcol_split_smem<N>());
+                const bool to_scratch = !CONJ || a.conj.direct;    // intensity through the transpose
+                if (to_scratch && !a.scratch) return cudaErrorInvalidValue;
+                auto k = CONJ ? conj_cols_split_kernel<N> : prop_cols_split_kernel<N>;
+                cudaError_t e = set_smem(k, pcol_split_smem<N>());
                 int nc = 0;
-                if (e == cudaSuccess)
-                    e = active_clusters(prop_cols_split_kernel<N>, 2, psplit_threads<N>(), pcol_split_smem<N>(), &nc);
+                if (e == cudaSuccess) e = active_clusters(k, 2, psplit_threads<N>(), pcol_split_smem<N>(), &nc);
                 if (e != cudaSuccess) return e;
-                e = launch_k(prop_cols_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()),
-                             pcol_split_smem<N>(), s, a);
-                if (e != cudaSuccess) return e;
+                e = launch_k(k, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()), pcol_split_smem<N>(), s, a);
+                if (e != cudaSuccess || !to_scratch) return e;
                 transpose_add_kernel<<<dim3(N / 32, N / 32), 256, 0, s>>>(a.scratch, a.intensity, N, a.accumulate);
                 return cudaGetLastError();
             } else {

@@ -68,6 +68,20 @@ def test_conjugate_16384_split_lines_at_critical_sampling():
     assert abs(h.double().mean().item() - I.double().mean().item()) < 1e-5
 
 
+def test_conjugate_16384_pattern_mode_equals_direct():
+    """Two copies of the grid wavelength go through the stored patterns and the resampling
+    (ratio 1: the identity) and must give the direct single-wavelength pattern."""
+    n = 16384
+    pix = _critical_pixel(n, lam=500.0)
+    pg = S.params(n=n, pixel_km=pix, r_diff_km=4.0 * pix, lambda_nm=500.0, seed=20130514 + 9320)
+    phi = S.make_screen(pg)
+    h = S.propagate_conjugate(pg, phi)
+    two = S.sum_passband_conjugate(pg, phi, [500.0, 500.0], [0.5, 0.5])
+    for y in (0, 5, 8191, 8192, 16383):
+        assert (two[y] - h[y]).abs().max().item() <= 1e-6 * max(1.0, h[y].max().item())
+    assert (two[:, 777] - h[:, 777]).abs().max().item() <= 1e-6 * max(1.0, h[:, 777].max().item())
+
+
 @pytest.mark.parametrize("lams,weights", [((550.0,), None), ((480.0, 550.0, 640.0), None),
                                           ((450.0, 520.0, 600.0, 700.0), (0.1, 0.2, 0.3, 0.4))])
 def test_conjugate_passband_matches_oracle(lams, weights):
