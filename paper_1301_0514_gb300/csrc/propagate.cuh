@@ -34,11 +34,11 @@ constexpr int kColEPT = 16;   // values per thread in the column passes
 constexpr size_t kMaxSmem = 227 * 1024;
 
 // Lines longer than one block's shared memory (N = 16384) go to a cluster of two
-// blocks.  The transfer-function passes split them by one radix-2 step on each
-// side (prop_*_split_kernel, propagate.cu); the one-FFT mode and the adjoint split
-// every FFT stage (fft.cuh, CS = 2), reading twiddles from the global table, with
-// own-entry arrays (fixed-point phases, accumulators) holding the N/CS entries of
-// the line that the block's threads own.
+// blocks.  The transfer-function and one-FFT passes split them by one radix-2 step
+// (prop_*_split_kernel, conj_*_split_kernel, propagate.cu); the adjoint splits every
+// FFT stage (fft.cuh, CS = 2), reading twiddles from the global table, with own-entry
+// arrays (fixed-point phases, accumulators) holding the N/CS entries of the line that
+// the block's threads own.
 template <int N> __host__ __device__ constexpr int pcs() { return N >= kSplitN ? 2 : 1; }
 template <int N> __host__ __device__ constexpr bool ppp_row() { return SCINT_PROP_PINGPONG && pcs<N>() == 1; }
 template <int N> __host__ __device__ constexpr bool ppp_col() { return SCINT_PROP_PINGPONG && N < 4096; }
