@@ -15,6 +15,8 @@
 //   adjoint row pass:    FFT_x conj(H_x) IFFT_x -> G_in; A_in recomputed from
 //                        the fixed-point phase; g_phi accumulated over the group.
 // The forward fields are recomputed, never stored.
+#include <algorithm>
+
 #include "dispatch.cuh"
 #include "propagate.cuh"
 
@@ -161,16 +163,184 @@ adj_rows_kernel(AdjArgs a) {
     if constexpr (CS == 2) line_sync<CS>();
 }
 
+// ---- N = 16384: the adjoint passes on the radix-2 cluster split --------------------
+// Block r of a cluster transforms the parity-r half of every line as a whole 8192-point
+// line in its own shared memory (fft.cuh: split_dif, split_combine), as the forward
+// passes do.  The column pass chains two transform pairs per wavelength: after the first
+// (A_out) each block holds G_out at its quarter of the outputs, n and n + N/2, i.e. both
+// halves of the decimation-in-frequency pairs for those n; it keeps its parity's a_n or
+// b_n and hands the other to its partner through shared memory.  Grids are persistent.
+template <int N> __host__ __device__ constexpr int asplit_threads() { return FftPlan<N / 2>::T; }
+template <int N> constexpr size_t asplit_col_smem() {
+    return (size_t)(FftPlan<N / 2>::BUF + FftPlan<N / 2>::TWS) * sizeof(float2);
+}
+template <int N> constexpr size_t asplit_row_smem() {
+    return (size_t)FftPlan<N / 2>::BUF * sizeof(float2) + (size_t)N * sizeof(long long);
+}
+
+template <int N>
+__global__ void __launch_bounds__(asplit_threads<N>(), 1) adj_cols_split_kernel(AdjArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E, WL = pstrip<N>();
+    extern __shared__ float2 smem32[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    float2* buf = smem32;
+    float2* tws = smem32 + Pl::BUF;
+    fill_twiddle_table<float2, H2>(tws, a.tw, t, T, 2);
+    cluster_arrive();    // the first wait also publishes the twiddle table to the block
+#pragma unroll 1
+    for (int x = blockIdx.x / 2; x < N; x += gridDim.x / 2) {
+        float gi[E];     // g_I at this block's outputs: n (2j) and n + N/2 (2j + 1), n = t + (j + r E/2) T
+#pragma unroll
+        for (int j = 0; j < E / 2; ++j) {
+            const int n = t + (j + r * (E / 2)) * T;
+            gi[2 * j] = a.grad_map[(size_t)n * N + x];
+            gi[2 * j + 1] = a.grad_map[(size_t)(n + H2) * N + x];
+        }
+#pragma unroll 1
+        for (int l = 0; l < a.lam.count; ++l) {
+            float2* f = a.work + (size_t)l * N * N + (size_t)(x / WL) * N * WL + (x % WL);
+            const unsigned long long hc = a.lam.h_fx[l];    // H_y from its fixed-point phase
+            float2 v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = t + m * T;
+                v[m] = split_dif(f[(size_t)e * WL], f[(size_t)(e + H2) * WL], r, e, a.tw);
+            }
+            cluster_wait();
+            fft_line<float2, H2, -1, 16, 1, 1, 1>(v, buf, t, tws);
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, 2 * (t + m * T) + r, N));
+            fft_line<float2, H2, +1, 16, 1, 1, 1>(v, buf, t, tws);
+            const float c2w = 2.0f * a.lam.weight[l];
+            float2 gq[E];                                    // G_out at n and n + N/2
+            split_combine<float2, H2>(v, buf, t, r, a.tw, [&](int j, int, float2 y0, float2 y1) {
+                gq[2 * j] = y0 * (c2w * gi[2 * j]);
+                gq[2 * j + 1] = y1 * (c2w * gi[2 * j + 1]);
+            });
+            // decimation in frequency of G_out: keep this block's parity, hand over the other
+            cluster_wait();                                  // the partner has read this block's buffer
+#pragma unroll
+            for (int j = 0; j < E / 2; ++j) {
+                const int e = t + (j + r * (E / 2)) * T;
+                const float2 own = split_dif(gq[2 * j], gq[2 * j + 1], r, e, a.tw);
+                buf[pad16(e)] = split_dif(gq[2 * j], gq[2 * j + 1], r ^ 1, e, a.tw);
+                if (r == 0) v[j] = own;
+                else v[j + E / 2] = own;
+            }
+            line_sync<2>();
+            const unsigned pb = cluster_addr(buf, (unsigned)(r ^ 1)) +
+                                (unsigned)(pad16(t + (r ^ 1) * (E / 2) * T) * sizeof(float2));
+#pragma unroll
+            for (int j = 0; j < E / 2; ++j) {
+                const float2 q = ld_cluster<float2>(pb + (unsigned)(j * (T + T / 16) * sizeof(float2)));
+                if (r == 0) v[j + E / 2] = q;
+                else v[j] = q;
+            }
+            line_sync<2>();                                  // the partner is done with this block's buffer
+            fft_line<float2, H2, -1, 16, 1, 1, 1>(v, buf, t, tws);
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], transfer_at(hc, 2 * (t + m * T) + r, N));
+            fft_line<float2, H2, +1, 16, 1, 1, 1>(v, buf, t, tws);
+            // P_y^H G_out over the field (the partner read this column before its first exchange)
+            split_combine<float2, H2>(v, buf, t, r, a.tw, [&](int, int n, float2 y0, float2 y1) {
+                f[(size_t)n * WL] = y0;
+                f[(size_t)(n + H2) * WL] = y1;
+            });
+        }
+    }
+    cluster_wait();
+}
+
+template <int N>
+__global__ void __launch_bounds__(asplit_threads<N>(), 1) adj_rows_split_kernel(AdjArgs a) {
+    constexpr int H2 = N / 2;
+    using Pl = FftPlan<H2>;
+    constexpr int T = Pl::T, E = Pl::E, WL = pstrip<N>();
+    extern __shared__ float2 smem32[];
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int t = threadIdx.x;
+    float2* buf = smem32;
+    // the whole row's fixed-point phases (each thread reads back only the entries it wrote)
+    long long* P = reinterpret_cast<long long*>(smem32 + Pl::BUF);
+    TwiddleRegs<float2, H2, 16> tr;
+    tr.load(a.tw, t, 2);
+#pragma unroll 1
+    for (int y = blockIdx.x / 2; y < N; y += gridDim.x / 2) {
+        const double* phi = a.phi + (size_t)y * N + r * H2;
+#pragma unroll
+        for (int m = 0; m < E; ++m) P[r * H2 + t + m * T] = phase_fixed(phi[t + m * T]);
+        line_sync<2>();
+        const unsigned pp = cluster_addr(P, (unsigned)(r ^ 1)) + (unsigned)(((r ^ 1) * H2 + t) * sizeof(long long));
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            P[(r ^ 1) * H2 + t + m * T] = ld_cluster<long long>(pp + (unsigned)(m * T * sizeof(long long)));
+        cluster_arrive();
+        float acc[E];    // g_phi at n (2j) and n + N/2 (2j + 1), n = t + (j + r E/2) T
+#pragma unroll
+        for (int m = 0; m < E; ++m) acc[m] = 0.0f;
+#pragma unroll 1
+        for (int l = 0; l < a.lam.count; ++l) {
+            const float2* f = a.work + (size_t)l * N * N;
+            const unsigned long long hc = a.lam.h_fx[l];    // H_x from its fixed-point phase
+            float2 v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = t + m * T;
+                v[m] = split_dif(f[strip_index<WL>(y, e, N)], f[strip_index<WL>(y, e + H2, N)], r, e, a.tw);
+            }
+            cluster_wait();
+            fft_line_tr<float2, H2, -1, 16, 1>(v, buf, t, tr);
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], transfer_at(hc, 2 * (t + m * T) + r, N));
+            fft_line_tr<float2, H2, +1, 16, 1>(v, buf, t, tr);     // G_in of this row
+            const unsigned long long S = a.lam.scale_fx[l];
+            const float s_l = a.lam.scale[l];
+            const float* sf = a.sf + (size_t)l * N;
+            const float sfy = sf[y];
+            split_combine<float2, H2>(v, buf, t, r, a.tw, [&](int j, int n, float2 g0, float2 g1) {
+                // s Im(conj(A_in) G_in), A_in recomputed from the fixed-point phase
+                const float2 A0 = unit_phasor(P[n], S) * (sfy * __ldg(sf + n));
+                const float2 A1 = unit_phasor(P[n + H2], S) * (sfy * __ldg(sf + n + H2));
+                acc[2 * j] = fmaf(s_l, A0.x * g0.y - A0.y * g0.x, acc[2 * j]);
+                acc[2 * j + 1] = fmaf(s_l, A1.x * g1.y - A1.y * g1.x, acc[2 * j + 1]);
+            });
+        }
+        cluster_wait();
+#pragma unroll
+        for (int j = 0; j < E / 2; ++j) {
+            const int n = t + (j + r * (E / 2)) * T;
+            double* o0 = a.grad_phi + (size_t)y * N + n;
+            double* o1 = o0 + H2;
+            *o0 = a.accumulate ? *o0 + (double)acc[2 * j] : (double)acc[2 * j];
+            *o1 = a.accumulate ? *o1 + (double)acc[2 * j + 1] : (double)acc[2 * j + 1];
+        }
+    }
+}
+
 cudaError_t launch_adj_cols(const AdjArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
         if constexpr (acol_smem<N>() > kMaxSmem || arow_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            cudaError_t e = set_smem(adj_cols_kernel<N>, acol_smem<N>());
-            if (e != cudaSuccess) return e;
-            return launch_k(adj_cols_kernel<N>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
-                            dim3(pcol_threads<N>()), acol_smem<N>(), s, a);
+            if constexpr (pcs<N>() == 2) {
+                static_assert(asplit_col_smem<N>() <= kMaxSmem, "split adjoint column pass does not fit");
+                cudaError_t e = set_smem(adj_cols_split_kernel<N>, asplit_col_smem<N>());
+                int nc = 0;
+                if (e == cudaSuccess)
+                    e = active_clusters(adj_cols_split_kernel<N>, 2, asplit_threads<N>(), asplit_col_smem<N>(), &nc);
+                if (e != cudaSuccess) return e;
+                return launch_k(adj_cols_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(asplit_threads<N>()),
+                                asplit_col_smem<N>(), s, a);
+            } else {
+                cudaError_t e = set_smem(adj_cols_kernel<N>, acol_smem<N>());
+                if (e != cudaSuccess) return e;
+                return launch_k(adj_cols_kernel<N>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
+                                dim3(pcol_threads<N>()), acol_smem<N>(), s, a);
+            }
         }
     });
 }
@@ -181,10 +351,21 @@ cudaError_t launch_adj_rows(const AdjArgs& a, cudaStream_t s) {
         if constexpr (acol_smem<N>() > kMaxSmem || arow_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            cudaError_t e = set_smem(adj_rows_kernel<N>, arow_smem<N>());
-            if (e != cudaSuccess) return e;
-            return launch_k(adj_rows_kernel<N>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
-                            dim3(prow_threads<N>()), arow_smem<N>(), s, a);
+            if constexpr (pcs<N>() == 2) {
+                static_assert(asplit_row_smem<N>() <= kMaxSmem, "split adjoint row pass does not fit");
+                cudaError_t e = set_smem(adj_rows_split_kernel<N>, asplit_row_smem<N>());
+                int nc = 0;
+                if (e == cudaSuccess)
+                    e = active_clusters(adj_rows_split_kernel<N>, 2, asplit_threads<N>(), asplit_row_smem<N>(), &nc);
+                if (e != cudaSuccess) return e;
+                return launch_k(adj_rows_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(asplit_threads<N>()),
+                                asplit_row_smem<N>(), s, a);
+            } else {
+                cudaError_t e = set_smem(adj_rows_kernel<N>, arow_smem<N>());
+                if (e != cudaSuccess) return e;
+                return launch_k(adj_rows_kernel<N>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
+                                dim3(prow_threads<N>()), arow_smem<N>(), s, a);
+            }
         }
     });
 }
