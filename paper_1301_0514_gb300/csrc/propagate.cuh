@@ -34,11 +34,9 @@ constexpr int kColEPT = 16;   // values per thread in the column passes
 constexpr size_t kMaxSmem = 227 * 1024;
 
 // Lines longer than one block's shared memory (N = 16384) go to a cluster of two
-// blocks.  The transfer-function and one-FFT passes split them by one radix-2 step
-// (prop_*_split_kernel, conj_*_split_kernel, propagate.cu); the adjoint splits every
-// FFT stage (fft.cuh, CS = 2), reading twiddles from the global table, with own-entry
-// arrays (fixed-point phases, accumulators) holding the N/CS entries of the line that
-// the block's threads own.
+// blocks, split by one radix-2 step (prop_*_split_kernel and conj_*_split_kernel in
+// propagate.cu, adj_*_split_kernel in adjoint.cu): each block transforms one parity
+// as a whole N/2-point line.  The kernels below are the unsplit passes.
 template <int N> __host__ __device__ constexpr int pcs() { return N >= kSplitN ? 2 : 1; }
 template <int N> __host__ __device__ constexpr bool ppp_row() { return SCINT_PROP_PINGPONG && pcs<N>() == 1; }
 template <int N> __host__ __device__ constexpr bool ppp_col() { return SCINT_PROP_PINGPONG && N < 4096; }
