@@ -55,21 +55,18 @@ cudaError_t launch_lightcurve_adjoint(const CurveAdjArgs& a, cudaStream_t s) {
 // ---- adjoint column pass ----------------------------------------------------------
 // buffers, the g_I columns (in place of the accumulator) and the twiddle table
 template <int N> constexpr size_t acol_smem() {
-    return (size_t)pcol_lines<N>() * FftPlan<N, kColEPT>::BUF * sizeof(float2) / pcs<N>() +
-           (pcs<N>() == 2 ? 0 : (size_t)FftPlan<N>::TWS * sizeof(float2));
+    return (size_t)pcol_lines<N>() * FftPlan<N, kColEPT>::BUF * sizeof(float2) + (size_t)FftPlan<N>::TWS * sizeof(float2);
 }
 
 template <int N>
 __global__ void __launch_bounds__(pcol_threads<N>(), (pcol_threads<N>() <= 256 ? 2 : 1))
 adj_cols_kernel(AdjArgs a) {
     using Pl = FftPlan<N, kColEPT>;
-    constexpr int CS = pcs<N>(), TWM = pcs<N>() == 2 ? 0 : 1;   // shared twiddle table unless split
-    constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
-    constexpr int TL = T / CS, BUFL = Pl::BUF / CS;
+    constexpr int TWM = 1;   // the shared twiddle table
+    constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>(), BUFL = Pl::BUF;
     extern __shared__ float2 smem32[];
-    const int w = threadIdx.x % W, tl = threadIdx.x / W;
-    const int t = line_rank<CS>() * TL + tl;
-    const int x0 = (blockIdx.x / CS) * W;
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int x0 = blockIdx.x * W;
     const int x = x0 + w;
     float2* buf = smem32 + w;
     float gi[E];                                  // g_I of this column (own entries), in registers
@@ -78,7 +75,7 @@ adj_cols_kernel(AdjArgs a) {
     if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
     for (int m = 0; m < E; ++m) gi[m] = a.grad_map[(size_t)(t + m * T) * N + x];
-    line_sync<CS>();
+    __syncthreads();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         float2* f = a.work + (size_t)l * N * N + (size_t)(x0 / WL) * N * WL + (x0 % WL);
@@ -86,52 +83,47 @@ adj_cols_kernel(AdjArgs a) {
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = f[(size_t)(t + m * T) * WL + w];
-        fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
+        fft_line<float2, N, -1, kColEPT, W, TWM>(v, buf, t, twp);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
-        fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);          // A_out of this column
+        fft_line<float2, N, +1, kColEPT, W, TWM>(v, buf, t, twp);          // A_out of this column
         const float c2w = 2.0f * a.lam.weight[l];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = v[m] * (c2w * gi[m]);          // G_out
-        fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
+        fft_line<float2, N, -1, kColEPT, W, TWM>(v, buf, t, twp);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], transfer_at(hc, t + m * T, N));
-        fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);          // P_y^H G_out
+        fft_line<float2, N, +1, kColEPT, W, TWM>(v, buf, t, twp);          // P_y^H G_out
 #pragma unroll
         for (int m = 0; m < E; ++m) f[(size_t)(t + m * T) * WL + w] = v[m];
     }
-    if constexpr (CS == 2) line_sync<CS>();
 }
 
 // ---- adjoint row pass --------------------------------------------------------------
-// buffers and fixed-point phases (the g_phi sums live in registers; the twiddle
-// bases in registers too unless the line is split, which uses the global table)
+// buffers and fixed-point phases (the g_phi sums and the twiddle bases live in registers)
 template <int N> constexpr size_t arow_smem() {
-    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) / pcs<N>();
+    return (size_t)prow_lines<N>() * (FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long));
 }
 
 template <int N>
 __global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
 adj_rows_kernel(AdjArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int CS = pcs<N>(), TWM = pcs<N>() == 2 ? 0 : 2;   // register twiddle bases unless split
-    constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), WL = pstrip<N>();
-    constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
+    constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), WL = pstrip<N>(), BUFL = Pl::BUF;
     extern __shared__ float2 smem32[];
-    const int team = threadIdx.x / TL, tl = threadIdx.x % TL;
-    const int t = line_rank<CS>() * TL + tl;
-    const int y = (blockIdx.x / CS) * B + team;
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const int y = blockIdx.x * B + team;
     float2* buf = smem32 + team * BUFL;
-    long long* P = reinterpret_cast<long long*>(smem32 + B * BUFL) + team * NL + tl;
+    long long* P = reinterpret_cast<long long*>(smem32 + B * BUFL) + team * N + t;
     float acc[E];                                 // g_phi of this row (own entries)
     TwiddleRegs<float2, N, 16> tr;
-    if constexpr (TWM == 2) tr.load(a.tw, t);
+    tr.load(a.tw, t);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-        P[m * TL] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
+        P[m * T] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
         acc[m] = 0.0f;
     }
-    line_sync<CS>();
+    __syncthreads();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         const float2* f = a.work + (size_t)l * N * N;
@@ -140,17 +132,15 @@ adj_rows_kernel(AdjArgs a) {
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = f[strip_index<WL>(y, t + m * T, N)];
-        if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
-        else fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, a.tw);
+        fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = cmulc(v[m], transfer_at(hc, t + m * T, N));
-        if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);   // G_in of this row
-        else fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, a.tw);
+        fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);   // G_in of this row
         const unsigned long long S = a.lam.scale_fx[l];
         const float s_l = a.lam.scale[l], sfy = sf[y];
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-            const float2 A = unit_phasor(P[m * TL], S) * (sfy * __ldg(sf + t + m * T));
+            const float2 A = unit_phasor(P[m * T], S) * (sfy * __ldg(sf + t + m * T));
             // s Im(conj(A_in) G_in)
             acc[m] = fmaf(s_l, A.x * v[m].y - A.y * v[m].x, acc[m]);
         }
@@ -160,7 +150,6 @@ adj_rows_kernel(AdjArgs a) {
         double* o = a.grad_phi + (size_t)y * N + t + m * T;
         *o = a.accumulate ? *o + (double)acc[m] : (double)acc[m];
     }
-    if constexpr (CS == 2) line_sync<CS>();
 }
 
 // ---- N = 16384: the adjoint passes on the radix-2 cluster split --------------------
@@ -323,24 +312,22 @@ __global__ void __launch_bounds__(asplit_threads<N>(), 1) adj_rows_split_kernel(
 cudaError_t launch_adj_cols(const AdjArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
-        if constexpr (acol_smem<N>() > kMaxSmem || arow_smem<N>() > kMaxSmem) {
+        if constexpr (pcs<N>() == 2) {
+            static_assert(asplit_col_smem<N>() <= kMaxSmem, "split adjoint pass does not fit");
+            cudaError_t e = set_smem(adj_cols_split_kernel<N>, asplit_col_smem<N>());
+            int nc = 0;
+            if (e == cudaSuccess)
+                e = active_clusters(adj_cols_split_kernel<N>, 2, asplit_threads<N>(), asplit_col_smem<N>(), &nc);
+            if (e != cudaSuccess) return e;
+            return launch_k(adj_cols_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(asplit_threads<N>()),
+                            asplit_col_smem<N>(), s, a);
+        } else if constexpr (acol_smem<N>() > kMaxSmem || arow_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            if constexpr (pcs<N>() == 2) {
-                static_assert(asplit_col_smem<N>() <= kMaxSmem, "split adjoint column pass does not fit");
-                cudaError_t e = set_smem(adj_cols_split_kernel<N>, asplit_col_smem<N>());
-                int nc = 0;
-                if (e == cudaSuccess)
-                    e = active_clusters(adj_cols_split_kernel<N>, 2, asplit_threads<N>(), asplit_col_smem<N>(), &nc);
-                if (e != cudaSuccess) return e;
-                return launch_k(adj_cols_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(asplit_threads<N>()),
-                                asplit_col_smem<N>(), s, a);
-            } else {
-                cudaError_t e = set_smem(adj_cols_kernel<N>, acol_smem<N>());
-                if (e != cudaSuccess) return e;
-                return launch_k(adj_cols_kernel<N>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
-                                dim3(pcol_threads<N>()), acol_smem<N>(), s, a);
-            }
+            cudaError_t e = set_smem(adj_cols_kernel<N>, acol_smem<N>());
+            if (e != cudaSuccess) return e;
+            adj_cols_kernel<N><<<N / pcol_lines<N>(), pcol_threads<N>(), acol_smem<N>(), s>>>(a);
+            return cudaGetLastError();
         }
     });
 }
@@ -348,24 +335,22 @@ cudaError_t launch_adj_cols(const AdjArgs& a, cudaStream_t s) {
 cudaError_t launch_adj_rows(const AdjArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
-        if constexpr (acol_smem<N>() > kMaxSmem || arow_smem<N>() > kMaxSmem) {
+        if constexpr (pcs<N>() == 2) {
+            static_assert(asplit_row_smem<N>() <= kMaxSmem, "split adjoint pass does not fit");
+            cudaError_t e = set_smem(adj_rows_split_kernel<N>, asplit_row_smem<N>());
+            int nc = 0;
+            if (e == cudaSuccess)
+                e = active_clusters(adj_rows_split_kernel<N>, 2, asplit_threads<N>(), asplit_row_smem<N>(), &nc);
+            if (e != cudaSuccess) return e;
+            return launch_k(adj_rows_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(asplit_threads<N>()),
+                            asplit_row_smem<N>(), s, a);
+        } else if constexpr (acol_smem<N>() > kMaxSmem || arow_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            if constexpr (pcs<N>() == 2) {
-                static_assert(asplit_row_smem<N>() <= kMaxSmem, "split adjoint row pass does not fit");
-                cudaError_t e = set_smem(adj_rows_split_kernel<N>, asplit_row_smem<N>());
-                int nc = 0;
-                if (e == cudaSuccess)
-                    e = active_clusters(adj_rows_split_kernel<N>, 2, asplit_threads<N>(), asplit_row_smem<N>(), &nc);
-                if (e != cudaSuccess) return e;
-                return launch_k(adj_rows_split_kernel<N>, 2, dim3(2 * std::min(nc, N)), dim3(asplit_threads<N>()),
-                                asplit_row_smem<N>(), s, a);
-            } else {
-                cudaError_t e = set_smem(adj_rows_kernel<N>, arow_smem<N>());
-                if (e != cudaSuccess) return e;
-                return launch_k(adj_rows_kernel<N>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
-                                dim3(prow_threads<N>()), arow_smem<N>(), s, a);
-            }
+            cudaError_t e = set_smem(adj_rows_kernel<N>, arow_smem<N>());
+            if (e != cudaSuccess) return e;
+            adj_rows_kernel<N><<<N / prow_lines<N>(), prow_threads<N>(), arow_smem<N>(), s>>>(a);
+            return cudaGetLastError();
         }
     });
 }

@@ -57,27 +57,25 @@ template <int N, bool CONJ>
 __global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
 prop_rows_kernel(PropArgs a) {
     using Pl = FftPlan<N>;
-    constexpr int CS = pcs<N>(), TWM = prow_twm<N>();
-    constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), W = pstrip<N>();
-    constexpr int TL = T / CS, BUFL = Pl::BUF / CS, NL = N / CS;
+    constexpr int TWM = prow_twm<N>();
+    constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), W = pstrip<N>(), BUFL = Pl::BUF;
     extern __shared__ float2 smem32[];
-    const int team = threadIdx.x / TL, tl = threadIdx.x % TL;
-    const int t = line_rank<CS>() * TL + tl;     // index in the line's team
-    const int y = (blockIdx.x / CS) * B + team;
+    const int team = threadIdx.x / T, t = threadIdx.x % T;    // line of the block, index in its team
+    const int y = blockIdx.x * B + team;
     float2* buf = smem32 + team * BUFL;
     // fixed-point phase of this thread's pixels, kept in shared memory across the
     // wavelength loop (each thread reads back only the entries it wrote)
-    long long* P = reinterpret_cast<long long*>(smem32 + B * BUFL) + team * NL + tl;
-    float2* tws = smem32 + B * BUFL + B * NL;   // shared twiddle table (after P, 8 B per entry)
+    long long* P = reinterpret_cast<long long*>(smem32 + B * BUFL) + team * N + t;
+    float2* tws = smem32 + B * BUFL + B * N;    // shared twiddle table (after P, 8 B per entry)
     const float2* twp = TWM == 1 ? tws : a.tw;
     constexpr bool PP = ppp_row<N>();            // second line buffers after the table
-    float2* buf1 = smem32 + B * BUFL + B * NL + (TWM == 1 ? Pl::TWS : 0) + team * BUFL;
+    float2* buf1 = smem32 + B * BUFL + B * N + (TWM == 1 ? Pl::TWS : 0) + team * BUFL;
     TwiddleRegs<float2, N, 16> tr;
     if constexpr (TWM == 2) tr.load(a.tw, t);
     else if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
-    for (int m = 0; m < E; ++m) P[m * TL] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
-    line_sync<CS>();
+    for (int m = 0; m < E; ++m) P[m * T] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
+    __syncthreads();
 
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
@@ -92,15 +90,15 @@ prop_rows_kernel(PropArgs a) {
             const unsigned long long cy = chirp_turns(C, y, N);
 #pragma unroll
             for (int m = 0; m < E; ++m)
-                v[m] = unit_phasor(P[m * TL], S, cy + chirp_turns(C, t + m * T, N)) * (sfy * __ldg(sf + t + m * T));
+                v[m] = unit_phasor(P[m * T], S, cy + chirp_turns(C, t + m * T, N)) * (sfy * __ldg(sf + t + m * T));
         } else {
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = unit_phasor(P[m * TL], S) * (sfy * __ldg(sf + t + m * T));
+            for (int m = 0; m < E; ++m) v[m] = unit_phasor(P[m * T], S) * (sfy * __ldg(sf + t + m * T));
         }
         if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, -1, 16, 1>(v, buf, buf1, t, tr);
         else if constexpr (PP) fft_line_pp<float2, N, -1, 16, 1, TWM>(v, buf, buf1, t, twp);
         else if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
-        else fft_line<float2, N, -1, 16, 1, TWM, CS>(v, buf, t, twp);
+        else fft_line<float2, N, -1, 16, 1, TWM>(v, buf, t, twp);
         if constexpr (!CONJ) {
             const unsigned long long hc = a.lam.h_fx[l];
 #pragma unroll
@@ -108,13 +106,12 @@ prop_rows_kernel(PropArgs a) {
             if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, +1, 16, 1>(v, buf, buf1, t, tr);
             else if constexpr (PP) fft_line_pp<float2, N, +1, 16, 1, TWM>(v, buf, buf1, t, twp);
             else if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
-            else fft_line<float2, N, +1, 16, 1, TWM, CS>(v, buf, t, twp);
+            else fft_line<float2, N, +1, 16, 1, TWM>(v, buf, t, twp);
         }
         float2* dst = a.work + (size_t)l * N * N;
 #pragma unroll
         for (int m = 0; m < E; ++m) dst[strip_index<W>(y, t + m * T, N)] = v[m];
     }
-    if constexpr (CS == 2) line_sync<CS>();   // no block leaves while its partner may still read its buffer
 }
 
 // ---- column pass ---------------------------------------------------------------
@@ -122,13 +119,11 @@ template <int N, bool CONJ>
 __global__ void __launch_bounds__(pcol_threads<N>(), (pcol_threads<N>() <= 256 ? 2 : 1))
 prop_cols_kernel(PropArgs a) {
     using Pl = FftPlan<N, kColEPT>;
-    constexpr int CS = pcs<N>(), TWM = pcol_twm<N>();
-    constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>();
-    constexpr int TL = T / CS, BUFL = Pl::BUF / CS;
+    constexpr int TWM = pcol_twm<N>();
+    constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>(), BUFL = Pl::BUF;
     extern __shared__ float2 smem32[];
-    const int w = threadIdx.x % W, tl = threadIdx.x / W;
-    const int t = line_rank<CS>() * TL + tl;
-    const int x0 = (blockIdx.x / CS) * W;    // first column of the block: strip x0 / WL, offset x0 % WL
+    const int w = threadIdx.x % W, t = threadIdx.x / W;
+    const int x0 = blockIdx.x * W;    // first column of the block: strip x0 / WL, offset x0 % WL
     const int x = x0 + w;
     float2* buf = smem32 + w;     // W lines interleaved: element e of line w at pad16(e) * W + w
     // passband accumulator of this thread's pixels, in registers (a shared-memory
@@ -143,7 +138,7 @@ prop_cols_kernel(PropArgs a) {
     else if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
 #pragma unroll
     for (int m = 0; m < E; ++m) acc[m] = 0.0f;
-    line_sync<CS>();
+    __syncthreads();
 #pragma unroll 1
     for (int l = 0; l < a.lam.count; ++l) {
         const float2* src = a.work + (size_t)l * N * N + (size_t)(x0 / WL) * N * WL + (x0 % WL);
@@ -153,7 +148,7 @@ prop_cols_kernel(PropArgs a) {
         if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, -1, kColEPT, W>(v, buf, buf1, t, tr);
         else if constexpr (PP) fft_line_pp<float2, N, -1, kColEPT, W, TWM>(v, buf, buf1, t, twp);
         else if constexpr (TWM == 2) fft_line_tr<float2, N, -1, kColEPT, W>(v, buf, t, tr);
-        else fft_line<float2, N, -1, kColEPT, W, TWM, CS>(v, buf, t, twp);
+        else fft_line<float2, N, -1, kColEPT, W, TWM>(v, buf, t, twp);
         if constexpr (CONJ) {
             // h = (Delta^2 / lambda z)^2 |FT G|^2 on the pattern grid of this wavelength (Eq. intens)
             const float nrm = a.conj.norm[l];
@@ -175,24 +170,20 @@ prop_cols_kernel(PropArgs a) {
             if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, +1, kColEPT, W>(v, buf, buf1, t, tr);
             else if constexpr (PP) fft_line_pp<float2, N, +1, kColEPT, W, TWM>(v, buf, buf1, t, twp);
             else if constexpr (TWM == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
-            else fft_line<float2, N, +1, kColEPT, W, TWM, CS>(v, buf, t, twp);
+            else fft_line<float2, N, +1, kColEPT, W, TWM>(v, buf, t, twp);
         }
         const float wl = a.lam.weight[l];
 #pragma unroll
         for (int m = 0; m < E; ++m) acc[m] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m]);
     }
     if constexpr (CONJ) {
-        if (!a.conj.direct) {
-            if constexpr (CS == 2) line_sync<CS>();
-            return;
-        }
+        if (!a.conj.direct) return;
     }
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         float* o = a.intensity + (size_t)(t + m * T) * N + x;
         *o = a.accumulate ? *o + acc[m] : acc[m];
     }
-    if constexpr (CS == 2) line_sync<CS>();
 }
 
 // ---- lines split over a two-block cluster (N = 16384) -------------------------------
@@ -452,23 +443,21 @@ template <bool CONJ>
 cudaError_t launch_rows(const PropArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
-        if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
+        if constexpr (pcs<N>() == 2) {
+            static_assert(prow_split_smem<N>() <= kMaxSmem, "split row pass does not fit");
+            auto k = CONJ ? conj_rows_split_kernel<N> : prop_rows_split_kernel<N>;
+            cudaError_t e = set_smem(k, prow_split_smem<N>());
+            int nc = 0;
+            if (e == cudaSuccess) e = active_clusters(k, 2, psplit_threads<N>(), prow_split_smem<N>(), &nc);
+            if (e != cudaSuccess) return e;
+            return launch_k(k, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()), prow_split_smem<N>(), s, a);
+        } else if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            if constexpr (pcs<N>() == 2) {
-                static_assert(prow_split_smem<N>() <= kMaxSmem, "split row pass does not fit");
-                auto k = CONJ ? conj_rows_split_kernel<N> : prop_rows_split_kernel<N>;
-                cudaError_t e = set_smem(k, prow_split_smem<N>());
-                int nc = 0;
-                if (e == cudaSuccess) e = active_clusters(k, 2, psplit_threads<N>(), prow_split_smem<N>(), &nc);
-                if (e != cudaSuccess) return e;
-                return launch_k(k, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()), prow_split_smem<N>(), s, a);
-            } else {
-                cudaError_t e = set_smem(prop_rows_kernel<N, CONJ>, prow_smem<N>());
-                if (e != cudaSuccess) return e;
-                return launch_k(prop_rows_kernel<N, CONJ>, pcs<N>(), dim3(N / prow_lines<N>() * pcs<N>()),
-                                dim3(prow_threads<N>()), prow_smem<N>(), s, a);
-            }
+            cudaError_t e = set_smem(prop_rows_kernel<N, CONJ>, prow_smem<N>());
+            if (e != cudaSuccess) return e;
+            prop_rows_kernel<N, CONJ><<<N / prow_lines<N>(), prow_threads<N>(), prow_smem<N>(), s>>>(a);
+            return cudaGetLastError();
         }
     });
 }
@@ -477,28 +466,26 @@ template <bool CONJ>
 cudaError_t launch_cols(const PropArgs& a, cudaStream_t s) {
     return dispatch_n(a.n, [&](auto nc) -> cudaError_t {
         constexpr int N = decltype(nc)::value;
-        if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
+        if constexpr (pcs<N>() == 2) {
+            static_assert(pcol_split_smem<N>() <= kMaxSmem, "split column pass does not fit");
+            const bool to_scratch = !CONJ || a.conj.direct;    // intensity through the transpose
+            if (to_scratch && !a.scratch) return cudaErrorInvalidValue;
+            auto k = CONJ ? conj_cols_split_kernel<N> : prop_cols_split_kernel<N>;
+            cudaError_t e = set_smem(k, pcol_split_smem<N>());
+            int nc = 0;
+            if (e == cudaSuccess) e = active_clusters(k, 2, psplit_threads<N>(), pcol_split_smem<N>(), &nc);
+            if (e != cudaSuccess) return e;
+            e = launch_k(k, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()), pcol_split_smem<N>(), s, a);
+            if (e != cudaSuccess || !to_scratch) return e;
+            transpose_add_kernel<<<dim3(N / 32, N / 32), 256, 0, s>>>(a.scratch, a.intensity, N, a.accumulate);
+            return cudaGetLastError();
+        } else if constexpr (prow_smem<N>() > kMaxSmem || pcol_smem<N>() > kMaxSmem) {
             return cudaErrorNotSupported;
         } else {
-            if constexpr (pcs<N>() == 2) {
-                static_assert(pcol_split_smem<N>() <= kMaxSmem, "split column pass does not fit");
-                const bool to_scratch = !CONJ || a.conj.direct;    // intensity through the transpose
-                if (to_scratch && !a.scratch) return cudaErrorInvalidValue;
-                auto k = CONJ ? conj_cols_split_kernel<N> : prop_cols_split_kernel<N>;
-                cudaError_t e = set_smem(k, pcol_split_smem<N>());
-                int nc = 0;
-                if (e == cudaSuccess) e = active_clusters(k, 2, psplit_threads<N>(), pcol_split_smem<N>(), &nc);
-                if (e != cudaSuccess) return e;
-                e = launch_k(k, 2, dim3(2 * std::min(nc, N)), dim3(psplit_threads<N>()), pcol_split_smem<N>(), s, a);
-                if (e != cudaSuccess || !to_scratch) return e;
-                transpose_add_kernel<<<dim3(N / 32, N / 32), 256, 0, s>>>(a.scratch, a.intensity, N, a.accumulate);
-                return cudaGetLastError();
-            } else {
-                cudaError_t e = set_smem(prop_cols_kernel<N, CONJ>, pcol_smem<N>());
-                if (e != cudaSuccess) return e;
-                return launch_k(prop_cols_kernel<N, CONJ>, pcs<N>(), dim3(N / pcol_lines<N>() * pcs<N>()),
-                                dim3(pcol_threads<N>()), pcol_smem<N>(), s, a);
-            }
+            cudaError_t e = set_smem(prop_cols_kernel<N, CONJ>, pcol_smem<N>());
+            if (e != cudaSuccess) return e;
+            prop_cols_kernel<N, CONJ><<<N / pcol_lines<N>(), pcol_threads<N>(), pcol_smem<N>(), s>>>(a);
+            return cudaGetLastError();
         }
     });
 }

@@ -38,15 +38,15 @@ constexpr size_t kMaxSmem = 227 * 1024;
 // propagate.cu, adj_*_split_kernel in adjoint.cu): each block transforms one parity
 // as a whole N/2-point line.  The kernels below are the unsplit passes.
 template <int N> __host__ __device__ constexpr int pcs() { return N >= kSplitN ? 2 : 1; }
-template <int N> __host__ __device__ constexpr bool ppp_row() { return SCINT_PROP_PINGPONG && pcs<N>() == 1; }
+template <int N> __host__ __device__ constexpr bool ppp_row() { return SCINT_PROP_PINGPONG; }
 template <int N> __host__ __device__ constexpr bool ppp_col() { return SCINT_PROP_PINGPONG && N < 4096; }
-template <int N> __host__ __device__ constexpr int prow_twm() { return pcs<N>() == 2 ? 0 : kRowTw; }
+template <int N> __host__ __device__ constexpr int prow_twm() { return kRowTw; }
 template <int N> __host__ __device__ constexpr int pcol_twm();   // below: depends on the shared-memory budget
 
 // rows per row-pass block, columns per column-pass block (all lines of a block
 // are transformed together); threads are per block
 template <int N> __host__ __device__ constexpr int prow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N ? kTileRow32 / N : N); }
-template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T / pcs<N>(); }
+template <int N> __host__ __device__ constexpr int prow_threads() { return prow_lines<N>() * FftPlan<N>::T; }
 // Column-pass blocks take 256 threads (two blocks per SM, so a stage barrier idles
 // half the SM, not all of it) wherever a block still holds two or more columns of
 // a strip; at N = 4096 that would leave one column (a quarter of every 32-byte
@@ -54,7 +54,7 @@ template <int N> __host__ __device__ constexpr int prow_threads() { return prow_
 template <int N> __host__ __device__ constexpr int pcol_lines() {
     return N >= 8192 ? 1 : (N >= 4096 ? 2 : (4096 / N < N ? 4096 / N : N));
 }
-template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_lines<N>() * FftPlan<N, kColEPT>::T / pcs<N>(); }
+template <int N> __host__ __device__ constexpr int pcol_threads() { return pcol_lines<N>() * FftPlan<N, kColEPT>::T; }
 // Strip width of the intermediate: at least 4 columns, so that every row of the
 // row pass writes whole 32-byte sectors; a column block then reads its
 // pcol_lines() columns out of one strip (sibling blocks share the sectors in L2).
@@ -62,27 +62,19 @@ template <int N> __host__ __device__ constexpr int pstrip() { return pcol_lines<
 
 template <int N> constexpr size_t ptws_bytes(int twm) { return twm == 1 ? (size_t)FftPlan<N>::TWS * sizeof(float2) : 0; }
 template <int N> constexpr size_t prow_smem() {
-    return (size_t)prow_lines<N>() * ((ppp_row<N>() ? 2 : 1) * FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) /
-               pcs<N>() +
+    return (size_t)prow_lines<N>() * ((ppp_row<N>() ? 2 : 1) * FftPlan<N>::BUF * sizeof(float2) + N * sizeof(long long)) +
            ptws_bytes<N>(prow_twm<N>());
 }
 // column pass: line buffers and (when it fits) the twiddle table
 template <int N> __host__ __device__ constexpr size_t pcol_base_bytes() {
-    return (size_t)pcol_lines<N>() * FftPlan<N>::BUF * sizeof(float2) / pcs<N>();
+    return (size_t)pcol_lines<N>() * FftPlan<N>::BUF * sizeof(float2);
 }
 template <int N> __host__ __device__ constexpr int pcol_twm() {
-    return pcs<N>() == 2 ? 0
-         : (kColTw == 1 && pcol_base_bytes<N>() * (ppp_col<N>() ? 2 : 1) + (size_t)FftPlan<N>::TWS * sizeof(float2) > kMaxSmem
+    return (kColTw == 1 && pcol_base_bytes<N>() * (ppp_col<N>() ? 2 : 1) + (size_t)FftPlan<N>::TWS * sizeof(float2) > kMaxSmem
                 ? 2 : kColTw);
 }
 template <int N> constexpr size_t pcol_smem() {
     return pcol_base_bytes<N>() * (ppp_col<N>() ? 2 : 1) + ptws_bytes<N>(pcol_twm<N>());
-}
-
-// rank of this block in its line's cluster (0 when lines are not split)
-template <int CS> SCINT_DEV int line_rank() {
-    if constexpr (CS == 1) return 0;
-    else return (int)cooperative_groups::this_cluster().block_rank();
 }
 
 // signed FFT frequency index of bin i
