@@ -8,7 +8,7 @@ projected stellar disk of U[0.1, 2] R_ref and sampled along 8 straight tracks,
 with the modulation index of the map and of every curve.  A step is one pass of
 the whole hot path over the batch: synthesis -> passband propagation ->
 smoothing -> light curves -> modulation indices, issued by scint_run_batch on
-four internal streams and replayed as one CUDA graph.
+eight internal streams and replayed as one CUDA graph.
 
 Metric: Fresnel-propagated pixels per second, sum over screens of N^2 x
 N_lambda per step / step time.  Timing: CUDA events on the launching stream,
@@ -1092,7 +1092,7 @@ def main():
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
     ap.add_argument("--conj-n", type=int, default=4096, help="grid of the one-FFT workload")
     ap.add_argument("--sweep-n", type=int, default=8192, help="grid of the m-sweep workload")
-    ap.add_argument("--lanes", type=int, default=4, help="streams the batch is scheduled on (1..8)")
+    ap.add_argument("--lanes", type=int, default=8, help="streams the batch is scheduled on (1..8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload == "screen_check" and args.impl != "reference":

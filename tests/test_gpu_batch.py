@@ -120,3 +120,19 @@ def test_batch_graph_capture_replays():
     torch.cuda.synchronize()
     for a, b in zip(outs, eager):
         _same(a, b, ("phi", "intensity", "curves", "m_map", "m_curves"))
+
+
+def test_batch_with_a_16384_screen_equals_single_calls():
+    """A 16384^2 screen (persistent two-block-cluster kernels sized to the whole GPU) on one lane
+    while the other lanes run small screens: the same bits as the single-screen calls."""
+    lams = np.array([500.0, 560.0])
+    big = W.large_screen_16384(beta=3.67, disk=True)
+    big["tracks"], big["n_samples"] = big["tracks"][:4], 2048
+    items = [big] + _items((256, 128, 512))
+    for it in items:
+        it["lambdas_nm"] = lams
+    outs = [_outputs(it) for it in items]
+    S.run_batch(outs, lams, n_lanes=3)
+    torch.cuda.synchronize()
+    for it, o in zip(items, outs):
+        _same(o, _single(it), ("phi", "intensity", "curves", "m_map", "m_curves"))
