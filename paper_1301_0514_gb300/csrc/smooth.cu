@@ -14,7 +14,12 @@ namespace scint {
 
 // N = 16384 lines go to a cluster of two blocks (the split kernels below)
 template <int N> __host__ __device__ constexpr int scs() { return N >= kSplitN ? 2 : 1; }
-template <int N> __host__ __device__ constexpr int scol_lines() { return N >= kTileCol32 ? 1 : (kTileCol32 / N < N / 2 ? kTileCol32 / N : N / 2); }
+// column passes: packed column pairs per block, 16384 / N below N = 8192 (1024 threads), so that
+// a block's row accesses are whole 32-byte sectors (four pairs at 4096): the passes are bound by
+// scattered sector requests, not latency (two 512-thread blocks per SM were slower).  Measured
+// against two pairs per block: 4096^2 forward 79 -> 66 us, inverse 91 -> 62 us; 2048^2 19 -> 16,
+// 18.5 -> 15 us.
+template <int N> __host__ __device__ constexpr int scol_lines() { return N >= 8192 ? 1 : (16384 / N < N / 2 ? 16384 / N : N / 2); }
 template <int N> __host__ __device__ constexpr int scol_threads() { return scol_lines<N>() * FftPlan<N>::T / scs<N>(); }
 template <int N> __host__ __device__ constexpr int srow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N / 2 ? kTileRow32 / N : N / 2); }
 template <int N> __host__ __device__ constexpr int srow_threads() { return srow_lines<N>() * FftPlan<N>::T / scs<N>(); }
