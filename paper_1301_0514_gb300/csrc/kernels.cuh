@@ -15,8 +15,7 @@ constexpr int kMaxLambda = 128;
 // Line-tile sizes (complex elements staged in shared memory per block).
 constexpr int kTileRow32 = 4096;    // FP32 line passes over rows
 constexpr int kSplitN = 16384;      // lines this long are split over a two-block cluster
-constexpr int kTileCol32 = 8192;    // FP32 line passes over columns
-constexpr int kTile64 = 4096;       // FP64 synthesis passes
+constexpr int kTile64 = 4096;       // double-float synthesis passes
 
 // Intermediates between a row pass and a column pass use the "strip layout":
 // element (y, x) of an N x N field sits at (x / W) * N * W + y * W + x % W, so
