@@ -420,9 +420,9 @@ def propagate_conjugate(phi, p: ScreenParams, lambda_nm: float | None = None):
 def sum_passband_conjugate(phi, p: ScreenParams, lambdas_nm, weights=None):
     """Passband co-addition (Sect. 3.2.4) of one-FFT patterns, whose pixels differ per
     wavelength (Delta_0 proportional to lambda).  Every pattern is resampled onto the grid of
-    p.lambda_nm about the optical axis, which is a pixel centre of every grid (Sect. 3.2.1:
-    integer pixel centres "to allow simple combinations of illumination patterns with different
-    pixel sizes"): output pixel k samples pattern l at u = (k - N/2) lambda_grid/lambda_l + N/2
+    p.lambda_nm about the optical axis, which is a pixel centre of every grid (Sect. 3.2.1 puts
+    pixel centres at integers so that patterns of different pixel sizes combine simply): output
+    pixel k samples pattern l at u = (k - N/2) lambda_grid/lambda_l + N/2
     (pattern pixels), bilinearly, periodic like the discrete transform (Reading R16).
     """
     lambdas_nm = np.asarray(lambdas_nm, dtype=np.float64)
