@@ -251,3 +251,25 @@ def test_sampling_ratio_closed_form(lib):
     with pytest.raises(S.ScintError):
         S.sampling_ratio(p, [500.0, -3.0])
     assert S.last_warning() == ""     # nothing propagated on this thread
+
+
+def test_cpu_tensors_are_refused_no_fallback(lib):
+    """The product path has no CPU fallback: the binding refuses host tensors loudly before any
+    library call (the oracle is test infrastructure, never a substitute)."""
+    import torch
+    p = S.params(n=64, pixel_km=20.0, r_diff_km=100.0)
+    phi = torch.zeros((64, 64), dtype=torch.float64)
+    I = torch.ones((64, 64), dtype=torch.float32)
+    calls = [
+        lambda: S.make_screen(p, out=phi),
+        lambda: S.propagate(p, phi),
+        lambda: S.sum_passband(p, phi, [500.0, 550.0]),
+        lambda: S.smooth_source(p, I),
+        lambda: S.lightcurve(p, I, np.array([[1.0, 2.0, 0.3, 1.0]]), 10),
+        lambda: S.propagate_conjugate(p, phi),
+        lambda: S.phase_fixed(phi.reshape(-1)),
+        lambda: S.fft_lines(torch.zeros((2, 64), dtype=torch.complex64), -1),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError):
+            call()
