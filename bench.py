@@ -39,7 +39,6 @@ METRIC = "Fresnel-propagated pixels/sec, batched FP32 vs plain, at <=2e-4 err; %
 UNIT = "pixel-wavelengths/s"
 PARAM_KEYS = ("n", "pixel_km", "r_diff_km", "beta", "lambda_nm", "lambda_ref_nm", "z_pc",
               "source_radius_km", "seed", "screen_id", "margin_km")
-SM_COUNT = 152
 CPU_SAMPLE_N = 2048       # the batch screen the oracle is timed on (about 10 s on one core)
 FP32_LANES_PER_SM = 128
 
@@ -366,6 +365,8 @@ def run_ours(args):
         else:
             S.run_batch(batch, lams, wts, n_lanes=args.lanes, workspace=ws)
 
+    # propagation plans: the autotuner times the built variants per grid size (outside capture)
+    plans = {str(n): S.tune(n, n_lam) for n in sizes}
     # warm-up outside the graph (sets kernel attributes), then capture one graph of the step
     step()
     torch.cuda.synchronize(dev)
@@ -417,14 +418,17 @@ def run_ours(args):
     kstats = S.profile_read()           # per-kernel event times of the last serial replay
     S.profile_enable(False)
 
-    # plain form: one screen and one wavelength per call, no graph, same kernels
+    # plain form: one screen and one wavelength per call, no graph, same kernels; one untimed
+    # pass, then --steps timed passes
+    step(plain=True)
     torch.cuda.synchronize(dev)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(stream)
-    step(plain=True)
+    for _ in range(args.steps):
+        step(plain=True)
     p1.record(stream)
     torch.cuda.synchronize(dev)
-    ms_plain = p0.elapsed_time(p1)
+    ms_plain = p0.elapsed_time(p1) / args.steps
 
     cufft = _cufft_comparison(items, dev) if any(it["n"] == 4096 for it in items) else None
 
@@ -433,7 +437,7 @@ def run_ours(args):
     pinned_m = torch.empty(m_map.shape, dtype=m_map.dtype, pin_memory=True)
     h2d = sum(it["tracks"].nbytes + it["lambdas_nm"].nbytes + 96 for it in items)
     d2h = sum(c.numel() * 4 for c in curves) + m_map.numel() * 8
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = args.steps
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -446,7 +450,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel (largest share of the timed step)
     hbm_peak, sm_max_mhz, peak_src = _peaks()
-    alu_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     dom_name, dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
     per_launch_ms = dom["total_ms"] / dom["launches"]   # from the serial replay
     gbs = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9
@@ -473,8 +478,22 @@ def run_ours(args):
                  "timing": f"serial one-lane replay of the step ({ms_serial:.1f} ms), CUDA events per launch",
                  "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
                  "fft_flops_per_launch": dom["flops"] / dom["launches"], "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
-                 "peak_source": f"hbm {peak_src} (MEASURED_PEAKS.json); alu = {SM_COUNT} SMs x "
+                 "peak_source": f"hbm {peak_src} (MEASURED_PEAKS.json); alu = {sm_count} SMs (device) x "
                                 f"{FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz"})
+    # the same kernel and the whole step on the planning bytes: 24 B per pixel-wavelength per
+    # propagation pass (48 for the pair), 24 B per pixel for the smoothing, 40 B per pixel for
+    # the synthesis (a three-pass design's minimal traffic)
+    px = sum(p.n * p.n for p in P)
+    survey_step_bytes = 48.0 * units + 24.0 * sum(p.n * p.n for p in P if p.source_radius_km > 0) + 40.0 * px
+    dom_px_lambda = units / max(1, dom["launches"]) if dom_name in ("prop_rows", "prop_cols") else None
+    survey = {"step_bytes": survey_step_bytes, "step_GBps": survey_step_bytes / (ms * 1e-3) / 1e9,
+              "step_frac": survey_step_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
+              "note": "planning bytes: 48 B per pixel-wavelength for propagation, 24 B/px smoothing, "
+                      "40 B/px synthesis; the two-pass kernels move 16 B per pixel-wavelength"}
+    if dom_px_lambda is not None:
+        kb = 24.0 * dom_px_lambda / (per_launch_ms * 1e-3) / 1e9
+        survey.update({"kernel_bytes_per_px_lambda": 24.0, "kernel_GBps": kb, "kernel_frac": kb / hbm_peak})
+    roof["survey_bytes_hbm"] = survey
     launches = sum(v["launches"] for v in kstats.values())
     kernels = {k: {"launches": v["launches"], "ms": v["total_ms"], "share": v["total_ms"] / ms_serial,
                    "GBps": v["bytes"] / max(v["total_ms"], 1e-9) / 1e6,
@@ -494,6 +513,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": desc, "form": f"scint_run_batch on {args.lanes} lane(s), one CUDA graph per step",
+                           "plans": plans,
                            "l2": "inputs larger than L2 (fields 32-134 MB per screen and wavelength)",
                            "parallelism": f"independent batch per GPU x{world}"},
                 "roofline": roof, "cpu_baseline": cpu,
@@ -502,8 +522,10 @@ def run_ours(args):
                 "gpu_launches": launches * args.steps, "clocks": clk,
                 "serial": {"value": units / (ms_serial * 1e-3), "ms_per_step": ms_serial,
                            "form": "the same batch on one lane (kernels in sequence), with per-launch events"},
-                "plain": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain,
-                          "form": "one screen and one wavelength per call, no graph"},
+                "plain": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain, "steps": args.steps,
+                          "form": "one screen at a time and one wavelength per call (no wavelength groups, no "
+                                  "lanes, no graph) through the same fused kernels; the unfused form is "
+                                  "cufft_comparison"},
                 "three_pass_equivalent": {
                     "bytes_per_px_lambda": 48, "GBps": value / world * 48 / 1e9,
                     "frac_of_hbm": value / world * 48 / 1e9 / hbm_peak,

@@ -125,7 +125,13 @@ size_t scint_workspace_bytes(const scint_params* p, int n_lambda);
  * seed high word) by the Box-Muller transform, forms
  *   F_k = sqrt(L^2 S_phi(q_k)) (g_re + i g_im) / sqrt(2),  F_0 = 0,
  * and writes phi_j = sqrt(2)/L^2 Re sum_k F_k exp(+2 pi i k.x_j)  (radians, at
- * lambda_ref).  The synthesis runs in FP64.
+ * lambda_ref).  Precision: the bins with |kx|, |ky| <= 32 (nearly all of the
+ * phase variance, since S ~ q^-beta) draw their normals and amplitude in FP64;
+ * every other bin draws them in FP32 from the same 53-bit uniforms.  The
+ * inverse 2D transform runs in double-float arithmetic (pairs of FP32 numbers,
+ * about 44 significant bits) and phi is written in FP64.  Against the FP64
+ * oracle the screen agrees to better than 2e-6 rad (the measured worst cases are
+ * stated with the tests of the full-size workloads).
  *   phi   device, N*N doubles, written.
  * Needs workspace (16 N^2 bytes).
  */
@@ -202,7 +208,13 @@ int scint_propagate(const scint_params* p, const double* phi, float* intensity,
  *     behind; nothing in it needs clearing between calls.  Calls whose
  *     executions overlap on the GPU (different streams, or several host
  *     threads) race on the array: serialise them.
- *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.  The
+ *     twiddle table is computed into the array on every call, with the same
+ *     kernel that fills the table scint_propagate keeps, so the two calls give
+ *     bit-identical intensities.
+ *   - The looked-up address is forgotten by scint_release; call scint_release
+ *     before a device reset (cudaDeviceReset) if this entry point is used
+ *     again afterwards.
  */
 int scint_propagate_noalloc(const scint_params* p, const double* phi, float* intensity, void* stream);
 
@@ -434,9 +446,62 @@ int scint_lightcurve_adjoint(const scint_params* p, const double* phi,
 int scint_rdiff_gradient(const scint_params* p, const double* phi, const double* grad_phi, double* out,
                          void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Propagation plans and the autotuner (build-side; the paper has no counterpart).
+ * The transfer-function passes of scint_propagate, scint_sum_passband,
+ * scint_run_batch and the batch's passbands exist in several compiled variants
+ * that compute the same intensity to FP32 rounding (they differ in the last bits):
+ *   packed        1: two wavelengths per thread (packed two-wide FP32 arithmetic),
+ *                 used for groups of >= 2 wavelengths at 64 <= N <= 8192;
+ *                 0: one wavelength per thread.
+ *   row_twiddles  FFT twiddle source of the packed row pass: 1 the block's shared
+ *                 table, 2 register bases and products.
+ *   col_twiddles  the same for the packed column pass.
+ * (the one-wavelength passes and N = 16384 have one variant each).  A plan is
+ * kept per (device, N).  Until one is set or tuned, a default built from
+ * measurements on GB300 is used.  A call that runs while the plan of its N
+ * changes may use either plan; results of one plan are reproducible bit for bit.
+ */
+typedef struct scint_plan {
+    int32_t packed;
+    int32_t row_twiddles;
+    int32_t col_twiddles;
+    int32_t tuned;      /* out: 1 if scint_tune measured this plan, 0 otherwise */
+    double  ms;         /* out: scint_tune's best time for its test passband, else 0 */
+} scint_plan;
+
+/* The plan used for grid n on the current device (SCINT_EINVAL for an invalid n). */
+int scint_get_plan(int n, scint_plan* out);
+
+/* Fix the plan of grid n on the current device.  SCINT_EUNSUPPORTED when the
+ * variant is not built for n (e.g. a shared table that does not fit in shared
+ * memory); the plan is then unchanged.  tuned and ms are ignored. */
+int scint_set_plan(int n, const scint_plan* plan);
+
+/*
+ * Autotuner: time every built variant of the propagation passes for grid n on a
+ * test passband of n_lambda wavelengths (clamped to [2, 32]) on the current
+ * device, three times each after one warm-up, with CUDA events on `stream`, and
+ * keep the fastest as the plan of n (returned in *out when out != NULL).  The
+ * test passband's fields are limited to 1 GiB (fewer wavelengths at large n).
+ * Allocates its own test buffers (a phase screen of zeros, the intensity and the
+ * workspace) with cudaMalloc and frees them before returning; synchronous.  Not
+ * allowed while `stream` is being captured (SCINT_EINVAL).
+ */
+int scint_tune(int n, int n_lambda, scint_plan* out, void* stream);
+
+/* Autotuning on first use (off by default): while on, scint_run_batch calls
+ * scint_tune for every grid size of its items that has no plan on the current
+ * device yet, before it launches anything, unless `stream` is being captured.
+ * Returns the previous setting. */
+int scint_autotune(int on);
+
 /* Release the library's internal per-device workspace pools, the twiddle tables
  * it keeps per (device, grid size) after their first use, and the batch
- * executor's streams.  Waits for the work that may still read them. */
+ * executor's streams, and forget the device addresses that
+ * scint_propagate_noalloc looked up (the next call looks them up again).  Waits
+ * for the work that may still read them.  Call it before a device reset if the
+ * library is used again afterwards. */
 void scint_release(void);
 
 /*

@@ -9,8 +9,8 @@ table or constant generator with the CUDA library and imports nothing from it.
 
 Every function states the passage of the paper it follows.  Arithmetic is
 IEEE double precision throughout; numpy's FFT serves as a library primitive
-(its sign and scaling conventions are pinned against a direct DFT in the
-tests).  Where the paper is silent or ambiguous the reading taken here is
+(its sign and scaling conventions are pinned against a direct DFT and against
+the oracle's own radix-2 transform, fft_radix2, in the tests).  Where the paper is silent or ambiguous the reading taken here is
 named in the docstring ("Reading Rn").
 
 Conventions used everywhere in this file
@@ -327,6 +327,45 @@ def taper_1d(n: int, pixel_km: float, margin_km: float):
     sf[lo] = 0.5 * (1.0 + np.sin(np.pi * x[lo] / Lm - np.pi / 2.0))
     sf[hi] = 0.5 * (1.0 + np.sin(np.pi * (x[hi] - L + Lm) / Lm + np.pi / 2.0))
     return sf
+
+
+def fft_radix2(x, inverse: bool = False):
+    """DFT of every line along the last axis by the iterative radix-2 Cooley-Tukey algorithm.
+
+    N must be a power of two.  The input is put in bit-reversed order, then log2 N
+    butterfly stages combine blocks of 2h elements: for k < h,
+    X_k = a_k + w^k b_k and X_{k+h} = a_k - w^k b_k with w = exp(-+ 2 pi i / (2h)).
+    Forward: X_k = sum_j x_j exp(-2 pi i j k / N); inverse: the + sign, no 1/N.
+    The oracle's steps use numpy's FFT as their library primitive; this is the
+    oracle's own transform, against which that primitive is pinned (with the
+    direct DFT) in the tests.
+    """
+    x = np.asarray(x, dtype=np.complex128)
+    n = x.shape[-1]
+    if n < 1 or n & (n - 1):
+        raise ValueError("length must be a power of two")
+    bits = n.bit_length() - 1
+    j = np.arange(n)
+    rev = np.zeros(n, dtype=np.int64)
+    for b in range(bits):
+        rev |= ((j >> b) & 1) << (bits - 1 - b)
+    y = x[..., rev]
+    sign = 1.0 if inverse else -1.0
+    h = 1
+    while h < n:
+        w = np.exp(sign * 1j * np.pi * np.arange(h) / h)
+        blocks = y.reshape(x.shape[:-1] + (n // (2 * h), 2, h))
+        a = blocks[..., 0, :]
+        b = blocks[..., 1, :] * w
+        y = np.stack([a + b, a - b], axis=-2).reshape(x.shape)
+        h *= 2
+    return y
+
+
+def fft2_radix2(x, inverse: bool = False):
+    """2D DFT (both axes) by fft_radix2: lines along x, then along y."""
+    y = fft_radix2(x, inverse)
+    return np.swapaxes(fft_radix2(np.swapaxes(y, -1, -2), inverse), -1, -2)
 
 
 def transfer_function(n: int, pixel_km: float, lambda_nm: float, z_pc: float):

@@ -8,6 +8,11 @@ from ._lib import (  # noqa: F401
     MAX_LAMBDA,
     MAX_LANES,
     BatchItem,
+    ScintPlan,
+    autotune,
+    get_plan,
+    set_plan,
+    tune,
     batch_items,
     batch_workspace_bytes,
     SamplingWarning,

@@ -91,6 +91,15 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
+class ScintPlan(ctypes.Structure):
+    """Mirror of struct scint_plan (include/scint.h)."""
+    _fields_ = [("packed", ctypes.c_int32), ("row_twiddles", ctypes.c_int32), ("col_twiddles", ctypes.c_int32),
+                ("tuned", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 _P = ctypes.POINTER(ScintParams)
 _vp = ctypes.c_void_p
@@ -139,6 +148,10 @@ def lib() -> ctypes.CDLL:
         "scint_sum_passband_conjugate": ([_P, _vp, _vp, _vp, _i, _vp, _i, _vp, _sz, _vp], _i),
         "scint_conjugate_pixel_km": ([_P, ctypes.c_double], ctypes.c_double),
         "scint_structure_function_rec": ([_P, _vp, _i, _vp, _i, _vp, _vp, _vp, _sz, _vp], _i),
+        "scint_get_plan": ([_i, ctypes.POINTER(ScintPlan)], _i),
+        "scint_set_plan": ([_i, ctypes.POINTER(ScintPlan)], _i),
+        "scint_tune": ([_i, _i, ctypes.POINTER(ScintPlan), _vp], _i),
+        "scint_autotune": ([_i], _i),
         "scint_profile_enable": ([_i], _i),
         "scint_profile_read": ([ctypes.POINTER(KernelStat), _i, ctypes.POINTER(_i)], _i),
     }
@@ -536,6 +549,31 @@ def fft_lines(x: torch.Tensor, direction: int, stream=None) -> torch.Tensor:
     else:
         raise ValueError("complex64 or complex128 expected")
     return x
+
+
+def get_plan(n: int) -> dict:
+    """The propagation plan of grid n on the current device (scint_get_plan)."""
+    pl = ScintPlan()
+    _check(lib().scint_get_plan(n, ctypes.byref(pl)))
+    return pl.as_dict()
+
+
+def set_plan(n: int, packed: int, row_twiddles: int = 2, col_twiddles: int = 1):
+    """Fix the propagation plan of grid n on the current device (scint_set_plan)."""
+    pl = ScintPlan(packed=packed, row_twiddles=row_twiddles, col_twiddles=col_twiddles, tuned=0, ms=0.0)
+    _check(lib().scint_set_plan(n, ctypes.byref(pl)))
+
+
+def tune(n: int, n_lambda: int = 32, stream=None) -> dict:
+    """Time the built propagation variants for grid n and keep the fastest (scint_tune)."""
+    pl = ScintPlan()
+    _check(lib().scint_tune(n, n_lambda, ctypes.byref(pl), ctypes.c_void_p(_stream(stream))))
+    return pl.as_dict()
+
+
+def autotune(on: bool = True) -> bool:
+    """Tune unplanned grid sizes on first use in run_batch (scint_autotune); returns the old setting."""
+    return bool(lib().scint_autotune(1 if on else 0))
 
 
 def release():

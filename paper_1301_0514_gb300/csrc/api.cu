@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -124,8 +125,11 @@ size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 size_t ws_synth(int n) { return up((size_t)n * 16) + up((size_t)(n / 2 + 1) * n * 16); }
 // twiddles, the taper table per wavelength, one field per wavelength of the group, and at
 // n = 16384 the column pass's column-major intensity
+// (a group of g > 1 wavelengths holds fields for g rounded up to even: the packed passes
+// process wavelengths in pairs)
+int field_slots(int g) { return g > 1 ? (g + 1) / 2 * 2 : g; }
 size_t ws_prop(int n, int g) {
-    return up((size_t)n * 8) + up((size_t)g * n * 4) + up((size_t)g * n * n * 8) +
+    return up((size_t)n * 8) + up((size_t)g * n * 4) + up((size_t)field_slots(g) * n * n * 8) +
            (n >= kSplitN ? up((size_t)n * n * 4) : 0);
 }
 size_t ws_smooth(int n) { return up((size_t)n * 8) + up((size_t)(n / 2 + 1) * n * 8); }
@@ -347,6 +351,52 @@ int check_passband(const scint_params* p, const double* lambdas, const double* w
     return SCINT_OK;
 }
 
+// ---- propagation plans (variants of the transfer-function passes) ----------------
+// Default: the one-wavelength passes (the packed ones run when a plan selects them).
+std::mutex g_plan_mu;
+std::map<std::pair<int, int>, scint_plan> g_plans;   // (device, n) -> plan
+
+scint_plan default_plan(int n) {
+    scint_plan pl{};
+    pl.packed = 0;
+    pl.row_twiddles = 2;
+    pl.col_twiddles = 1;
+    return pl;
+}
+
+int plan_for(int n, scint_plan* out) {
+    int dev = 0;
+    SCINT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    const auto it = g_plans.find(std::make_pair(dev, n));
+    *out = it != g_plans.end() ? it->second : default_plan(n);
+    return SCINT_OK;
+}
+
+bool plan_known(int n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    return g_plans.count(std::make_pair(dev, n)) > 0;
+}
+
+void erase_plan(int n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans.erase(std::make_pair(dev, n));
+}
+
+std::atomic<int> g_autotune{0};
+
+int store_plan(int n, const scint_plan& pl) {
+    int dev = 0;
+    SCINT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[std::make_pair(dev, n)] = pl;
+    return SCINT_OK;
+}
+
 // Per-wavelength scalars of the propagation passes (slot i of a group).
 void fill_lambda(LambdaSet& ls, int i, const scint_params* p, double lam, double w) {
     const double L = screen_len(p);
@@ -380,17 +430,23 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
     Carver cg = c;   // group buffers restart at the same offset for every group
     ta.sf = cg.take<float>((size_t)g * n * 4);
     pa.sf = ta.sf;
-    pa.work = cg.take<float2>((size_t)g * n * n * 8);
+    pa.work = cg.take<float2>((size_t)field_slots(g) * n * n * 8);
     pa.scratch = n >= kSplitN ? cg.take<float>((size_t)n * n * 4) : nullptr;
     pa.intensity = intensity;
     pa.accumulate = accumulate;
+    pa.one = 1.0f;
+    scint_plan pl{};
+    int rc = plan_for(n, &pl);
+    if (rc) return rc;
+    const bool packed = pl.packed && g > 1 && packed_prop_supported(n, pl.row_twiddles, pl.col_twiddles);
     const double nn = (double)n * n;
     SCINT_LAUNCH(K_PROP_TABLES, 4.0 * g * n, 0.0, s, launch_prop_tables(ta, s));
     // rows: phi read once, one complex64 field written per wavelength; FFT_x + IFFT_x per row
-    SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * g * nn, 2.0 * g * n * fft_flops(n), s, launch_prop_rows(pa, false, s));
+    SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * g * nn, 2.0 * g * n * fft_flops(n), s,
+                 packed ? launch_prop_rows2(pa, pl.row_twiddles, s) : launch_prop_rows(pa, false, s));
     // columns: fields read, intensity written once (and read when accumulating)
     SCINT_LAUNCH(K_PROP_COLS, 8.0 * g * nn + (accumulate ? 8.0 : 4.0) * nn, 2.0 * g * n * fft_flops(n), s,
-                 launch_prop_cols(pa, false, s));
+                 packed ? launch_prop_cols2(pa, pl.col_twiddles, s) : launch_prop_cols(pa, false, s));
     return SCINT_OK;
 }
 
@@ -542,6 +598,8 @@ SynthArgs synth_args(const scint_params* p) {
     a.neg_beta_4 = -beta / 4.0;
     a.amp32 = (float)a.amp;
     a.neg_beta_4_32 = (float)a.neg_beta_4;
+    a.amp_rel_lo = (float)((a.amp - (double)a.amp32) / (double)a.amp32);
+    a.neg_beta_4_lo = (float)(a.neg_beta_4 - (double)a.neg_beta_4_32);
     a.out_scale = std::sqrt(2.0) / (L * L);
     return a;
 }
@@ -566,6 +624,8 @@ size_t forward_workspace_bytes(int n, int g) {
     return std::max(std::max(ws_synth(n), ws_prop(n, g)), std::max(ws_smooth(n), ws_moments()));
 }
 int pool_workspace(size_t bytes, cudaStream_t s, void** out) { return pool_get(bytes, s, out); }
+bool autotune_on() { return g_autotune.load() != 0; }
+bool has_plan(int n) { return plan_known(n); }
 }  // namespace scint
 
 namespace {
@@ -685,6 +745,128 @@ int scint_propagate_noalloc(const scint_params* p, const double* phi, float* int
     const double lam = p->lambda_nm, w = 1.0;
     return passband_impl(p, phi, &lam, &w, 1, intensity, 0, scratch, kStaticScratchBytes,
                          static_cast<cudaStream_t>(stream), false);
+}
+
+int scint_autotune(int on) { return g_autotune.exchange(on ? 1 : 0); }
+
+int scint_get_plan(int n, scint_plan* out) {
+    if (!out) return fail(SCINT_EINVAL, "out is NULL");
+    if (!pow2(n) || n < SCINT_MIN_N || n > SCINT_MAX_N)
+        return fail(SCINT_EINVAL, "n=%d must be a power of two in [%d, %d]", n, SCINT_MIN_N, SCINT_MAX_N);
+    const int rc = plan_for(n, out);
+    return rc ? rc : ok();
+}
+
+int scint_set_plan(int n, const scint_plan* plan) {
+    if (!plan) return fail(SCINT_EINVAL, "plan is NULL");
+    if (!pow2(n) || n < SCINT_MIN_N || n > SCINT_MAX_N)
+        return fail(SCINT_EINVAL, "n=%d must be a power of two in [%d, %d]", n, SCINT_MIN_N, SCINT_MAX_N);
+    const bool tw_ok = (plan->row_twiddles == 1 || plan->row_twiddles == 2) &&
+                       (plan->col_twiddles == 1 || plan->col_twiddles == 2);
+    if ((plan->packed != 0 && plan->packed != 1) || !tw_ok)
+        return fail(SCINT_EINVAL, "packed must be 0 or 1 and the twiddle sources 1 or 2");
+    if (plan->packed && !packed_prop_supported(n, plan->row_twiddles, plan->col_twiddles))
+        return fail(SCINT_EUNSUPPORTED, "the packed passes with twiddle sources (%d, %d) are not built for n=%d",
+                    plan->row_twiddles, plan->col_twiddles, n);
+    scint_plan pl = *plan;
+    pl.tuned = 0;
+    pl.ms = 0.0;
+    const int rc = store_plan(n, pl);
+    return rc ? rc : ok();
+}
+
+int scint_tune(int n, int n_lambda, scint_plan* out, void* stream) {
+    if (!pow2(n) || n < SCINT_MIN_N || n > SCINT_MAX_N)
+        return fail(SCINT_EINVAL, "n=%d must be a power of two in [%d, %d]", n, SCINT_MIN_N, SCINT_MAX_N);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SCINT_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return fail(SCINT_EINVAL, "scint_tune cannot run during stream capture");
+    std::vector<scint_plan> cand;
+    scint_plan one_wl{};
+    one_wl.packed = 0;
+    one_wl.row_twiddles = 2;
+    one_wl.col_twiddles = 1;
+    cand.push_back(one_wl);
+    for (int r = 1; r <= 2; ++r)
+        for (int c = 1; c <= 2; ++c)
+            if (packed_prop_supported(n, r, c)) cand.push_back(scint_plan{1, r, c, 0, 0.0});
+    // test passband: n_lambda in [2, 32], fields within 1 GiB
+    int g = std::max(2, std::min(n_lambda, 32));
+    const size_t field = (size_t)n * n * 8;
+    while (g > 2 && (size_t)field_slots(g) * field > ((size_t)1 << 30)) --g;
+    scint_plan best = cand[0];
+    best.ms = 0.0;
+    const bool had = plan_known(n);
+    scint_plan prev{};
+    if (had) plan_for(n, &prev);
+    if (cand.size() > 1) {
+        const size_t wsb = ws_prop(n, g);
+        void *phi = nullptr, *inten = nullptr, *ws = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        auto cleanup = [&] {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            cudaFree(phi);
+            cudaFree(inten);
+            cudaFree(ws);
+        };
+        if (cudaMalloc(&phi, field) != cudaSuccess || cudaMalloc(&inten, (size_t)n * n * 4) != cudaSuccess ||
+            cudaMalloc(&ws, wsb) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return fail(SCINT_ENOMEM, "scint_tune: cudaMalloc of its test buffers failed");
+        }
+        if (cudaMemsetAsync(phi, 0, field, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+            cudaEventCreate(&e1) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return fail(SCINT_ECUDA, "scint_tune: setting up its test buffers failed");
+        }
+        scint_params p{};
+        p.n = n;
+        p.pixel_km = 10.0;
+        p.r_diff_km = 100.0 * n;   // resolved at every test wavelength
+        p.beta = 11.0 / 3.0;
+        p.lambda_nm = p.lambda_ref_nm = 550.0;
+        p.z_pc = 160.0;
+        p.margin_km = -1.0;
+        std::vector<double> lams(g), wts(g, 1.0 / g);
+        for (int i = 0; i < g; ++i) lams[i] = 400.0 + 300.0 * i / (g - 1);
+        double best_ms = 1e300;
+        int rc = SCINT_OK;
+        for (const scint_plan& c : cand) {
+            if ((rc = store_plan(n, c))) break;
+            double t = 1e300;
+            for (int rep = 0; rep < 4 && !rc; ++rep) {
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = fail(SCINT_ECUDA, "scint_tune: event record");
+                if (!rc) rc = passband_impl(&p, static_cast<const double*>(phi), lams.data(), wts.data(), g,
+                                            static_cast<float*>(inten), 0, ws, wsb, s);
+                if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                    rc = fail(SCINT_ECUDA, "scint_tune: timing");
+                float ms = 0.0f;
+                if (!rc && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t = std::min(t, (double)ms);
+            }
+            if (rc) break;
+            if (t < best_ms) {
+                best_ms = t;
+                best = c;
+                best.ms = t;
+            }
+        }
+        cleanup();
+        if (rc) {   // leave the plan as it was
+            if (had) store_plan(n, prev);
+            else erase_plan(n);
+            return rc;
+        }
+    }
+    best.tuned = 1;
+    const int rc = store_plan(n, best);
+    if (rc) return rc;
+    if (out) *out = best;
+    g_warning.clear();
+    return ok();
 }
 
 double scint_conjugate_pixel_km(const scint_params* p, double lambda_nm) {
@@ -1066,6 +1248,11 @@ int scint_profile_read(scint_kernel_stat* stats, int max_stats, int* n_stats) {
 
 void scint_release(void) {
     scint::release_lanes();
+    {
+        // a device reset would invalidate them; the next noalloc call looks them up again
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        g_static_addr.clear();
+    }
     {
         std::lock_guard<std::mutex> lk(g_tw.mu);
         int cur = 0;

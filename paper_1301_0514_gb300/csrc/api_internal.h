@@ -34,5 +34,8 @@ size_t forward_workspace_bytes(int n, int g);
 int pool_workspace(size_t bytes, cudaStream_t s, void** out);
 // Destroy the batch executor's streams and events (csrc/batch.cu).
 void release_lanes();
+// Autotuning on first use (scint_autotune) is on; grid n has a plan on the current device.
+bool autotune_on();
+bool has_plan(int n);
 
 }  // namespace scint

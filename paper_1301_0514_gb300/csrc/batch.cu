@@ -180,6 +180,19 @@ int scint_run_batch(const scint_batch_item* items, int n_items, const double* la
     cudaStream_t caller = static_cast<cudaStream_t>(stream);
     const Sizes z = batch_sizes(items, n_items);
 
+    // plans of grid sizes seen for the first time (scint_autotune), never while capturing
+    if (scint::autotune_on()) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(caller, &cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+        if (cs == cudaStreamCaptureStatusNone) {
+            for (int i = 0; i < n_items; ++i) {
+                const int n = items[i].params.n;
+                if (!scint::has_plan(n) && (rc = scint_tune(n, n_lambda, nullptr, caller))) return rc;
+            }
+        }
+    }
+
     // lane slices: equal parts of the workspace; the largest group that fits
     size_t slice = 0;
     if (workspace) {

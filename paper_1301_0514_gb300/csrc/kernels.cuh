@@ -35,6 +35,8 @@ struct SynthArgs {
     double amp;          // sigma(k) = amp * (mx^2 + my^2)^(-beta/4), includes 1/sqrt(2)
     double neg_beta_4;   // -beta/4
     float amp32, neg_beta_4_32;   // the same in FP32 for the high-frequency bins
+    float amp_rel_lo;             // (amp - amp32) / amp32
+    float neg_beta_4_lo;          // -beta/4 - neg_beta_4_32
     double out_scale;    // sqrt(2) / L^2
     const dfc* tw;       // double-float twiddles for n
     dfc* work;           // (n/2 + 1) x n double-float complex, row-major: rows ky = 0..n/2 after the x transform
@@ -77,6 +79,7 @@ struct PropArgs {
     float* scratch;          // n = 16384: the column pass's column-major intensity (n*n)
     LambdaSet lam;
     ConjSet conj;            // used by the one-FFT mode only
+    float one;               // 1.0f: the multiplier of the packed passes' additions (fft2.cuh)
 };
 // The taper table of a wavelength group (SF at the pixel centres, per wavelength).
 struct TableArgs {
@@ -88,6 +91,12 @@ cudaError_t launch_prop_tables(const TableArgs& a, cudaStream_t s);
 // conj = false: transfer function (FFT, H, IFFT per axis); true: one-FFT method.
 cudaError_t launch_prop_rows(const PropArgs& a, bool conj, cudaStream_t s);
 cudaError_t launch_prop_cols(const PropArgs& a, bool conj, cudaStream_t s);
+// Transfer-function passes with two wavelengths per thread (propagate2.cu): the field
+// of wavelengths 2q, 2q + 1 is one array of 16-byte pixels at work + q N^2 (as cp2);
+// twm: twiddles from register bases (2) or the block's shared table (1).
+bool packed_prop_supported(int n, int row_twm, int col_twm);
+cudaError_t launch_prop_rows2(const PropArgs& a, int twm, cudaStream_t s);
+cudaError_t launch_prop_cols2(const PropArgs& a, int twm, cudaStream_t s);
 // Passband of one-FFT patterns: intensity (+)= sum_l w_l pattern_l resampled
 // bilinearly (periodic) at (k - n/2) r_l + n/2, r_l in 32.32 fixed point.
 struct ResampleArgs {

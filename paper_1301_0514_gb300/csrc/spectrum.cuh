@@ -34,8 +34,11 @@ SCINT_DEV float neg_log_ua32(const u32x4& w) {
 // Bins with |mx| <= kLowK and |my| <= kLowK carry almost all of the phase
 // variance (S ~ q^-beta): their noise and amplitude are computed in FP64.  The
 // other bins have small amplitudes, so FP32 Box-Muller and pow give phase errors
-// of ~1e-7 of their (small) rms contribution.
-constexpr int kLowK = 32;
+// of ~1e-7 of their (small) rms contribution, which falls as kLowK^((2 - beta)/2)
+// with the square's size.  At kLowK = 32 the screens with the largest phases (rms
+// 72 rad at 4096^2, R_diff = 30 km) were 2.4e-6 rad off the FP64 oracle; 256
+// keeps them well inside 1e-6 rad for 0.1-1 % of the bins.
+constexpr int kLowK = 256;
 
 // A bin's shaped value F[ky][kx] = sqrt(L^2 S(q)) (g_re + i g_im) / sqrt(2), in the
 // precision it is computed in: FP64 for the low bins (low = true, d), FP32 for the
@@ -50,7 +53,18 @@ SCINT_DEV u32x4 bin_words(const SynthArgs& a, int kx, int ky) {
 }
 // amplitude sqrt(L^2 S(q)) (with the 1/sqrt(2)) from m2 = mx^2 + my^2 > 0, in each precision
 SCINT_DEV double amplitude_low(const SynthArgs& a, int m2) { return a.amp * pow((double)m2, a.neg_beta_4); }
-SCINT_DEV float amplitude_high(const SynthArgs& a, int m2) { return a.amp32 * powf((float)m2, a.neg_beta_4_32); }
+// FP32: amp m2^(-beta/4) with the rounding of the constants undone to first order.  amp and
+// -beta/4 are split as hi + lo (hi the FP32 value); m2 > 2^24 rounds to float as m2f, m2 = m2f + d.
+// With x = amp_hi m2f^(y_hi), the amplitude is x (1 + amp_lo/amp_hi + y_lo ln m2f + y_hi d/m2f):
+// the lo part of the exponent alone would otherwise err by up to 3e-8 ln m2 (5e-7 at m2 = 1e7),
+// the same sign for every bin.
+SCINT_DEV float amplitude_high(const SynthArgs& a, int m2) {
+    const float m2f = (float)m2;
+    const float d = (float)(m2 - (int)m2f);
+    const float x = a.amp32 * powf(m2f, a.neg_beta_4_32);
+    const float corr = fmaf(a.neg_beta_4_lo, __logf(m2f), fmaf(a.neg_beta_4_32, __fdividef(d, m2f), a.amp_rel_lo));
+    return fmaf(x, corr, x);
+}
 // sig (g_re + i g_im) from a bin's Philox words, Box-Muller in FP64 ...
 SCINT_DEV double2 shaped_low(const u32x4& w, double sig) {
     const double ub = uniform53(w.w, w.z);

@@ -133,7 +133,7 @@ def _c_layout(struct, fields):
 
 def test_struct_layouts_match_the_c_compiler():
     for struct, cls in (("scint_params", _lib.ScintParams), ("scint_batch_item", _lib.BatchItem),
-                        ("scint_kernel_stat", _lib.KernelStat)):
+                        ("scint_kernel_stat", _lib.KernelStat), ("scint_plan", _lib.ScintPlan)):
         fields = [f for f, _ in cls._fields_]
         got = _c_layout(struct, fields)
         assert got[:-1] == [getattr(cls, f).offset for f in fields], struct
@@ -273,3 +273,14 @@ def test_cpu_tensors_are_refused_no_fallback(lib):
     for call in calls:
         with pytest.raises(ValueError):
             call()
+
+
+def test_plan_host_checks(lib):
+    """Plan calls reject bad grid sizes and variants on the host (no GPU call is made)."""
+    pl = _lib.ScintPlan(packed=1, row_twiddles=3, col_twiddles=1)
+    assert lib.scint_set_plan(1024, ctypes.byref(pl)) == 1
+    assert lib.scint_set_plan(1000, ctypes.byref(pl)) == 1
+    assert lib.scint_get_plan(1000, ctypes.byref(pl)) == 1
+    assert lib.scint_get_plan(1024, None) == 1
+    assert lib.scint_tune(999, 8, None, None) == 1
+    assert lib.scint_autotune(0) in (0, 1)

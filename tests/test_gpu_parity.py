@@ -2,7 +2,7 @@
 
 Tolerances (fixed by the required accuracy of the FP32 path, not tuned):
   * Philox words: bit-exact.
-  * Shaped spectrum: bins with |mx|, |my| <= 32 are FP64 on both sides (1e-13
+  * Shaped spectrum: bins with |mx|, |my| <= 256 are FP64 on both sides (1e-13
     relative); the other bins are drawn in FP32 on the GPU (2e-6 relative).
   * Phase screen: 2e-6 rad absolute.  The screen's error is ~1e-7 of the rms
     phase carried by the FP32 bins (a few rad at most); the intensity bound
@@ -45,11 +45,12 @@ def test_noise_words_bit_exact():
 
 @pytest.mark.parametrize("beta", [11.0 / 3.0, 3.3, 3.9])
 def test_noise_spectrum(beta):
-    it = _item(n=128, pixel_km=15.0, r_diff_km=40.0, beta=beta, seed=99, screen_id=3)
+    n = 1024    # both kinds of bins: the GPU draws |mx|, |my| <= 256 in FP64, the rest in FP32
+    it = _item(n=n, pixel_km=15.0, r_diff_km=40.0, beta=beta, seed=99, screen_id=3)
     g = S.noise_spectrum(gpu_params(it)).cpu().numpy()
     o = O.noise_spectrum(oracle_params(it))
-    m = np.abs(np.fft.fftfreq(128, 1.0 / 128))
-    low = (m[:, None] <= 32) & (m[None, :] <= 32)
+    m = np.abs(np.fft.fftfreq(n, 1.0 / n))
+    low = (m[:, None] <= 256) & (m[None, :] <= 256)
     rel = np.abs(g - o) / np.maximum(np.abs(o), 1e-300)
     assert rel[low].max() <= 1e-13
     assert rel[~low].max() <= 2e-6
@@ -216,27 +217,6 @@ def test_modulation_index_fiducial_zone():
 
 
 # ---------------------------------------------------------------------------
-def test_single_4096_full_size_one_screen():
-    """4096^2, 10 km, R_diff = 300 km: whole intensity map and the 64 tracks vs the oracle."""
-    it = W.single_screens_4096(r_diffs=(300.0,))[0]
-    p_g, p_o = gpu_params(it), oracle_params(it)
-    phi_g = S.make_screen(p_g)
-    phi_o = O.make_screen(p_o)
-    assert np.abs(phi_g.cpu().numpy() - phi_o).max() <= PHI_TOL
-    I_g = S.propagate(p_g, phi_g)
-    I_o = O.intensity_mono(phi_o, p_o)
-    err = np.abs(I_g.cpu().numpy() - I_o).max()
-    assert err <= I_TOL, err
-    c_g = S.lightcurve(p_g, I_g, it["tracks"], it["n_samples"]).cpu().numpy()
-    c_o = O.lightcurves(I_o, it["tracks"], it["n_samples"])
-    assert np.abs(c_g - c_o).max() <= I_TOL
-    m_g = S.modulation_index(p_g, I_g).cpu().numpy()[0]
-    assert m_g == pytest.approx(O.modulation_index_map(I_o, p_o), rel=M_TOL)
-    cm = S.curve_modulation(torch.from_numpy(c_g).cuda()).cpu().numpy()[:, 0]
-    cm_o = np.array([O.modulation_index(c) for c in c_o])
-    np.testing.assert_allclose(cm, cm_o, rtol=M_TOL)
-
-
 def test_largest_phase_screen_full_path():
     """R_diff = 30 km (phase rms ~ 60 rad, peaks ~ 300 rad), 2048^2: screen, intensity, m vs oracle."""
     it = W.single_screens_4096(r_diffs=(30.0,), n=2048)[0]

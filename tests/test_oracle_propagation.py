@@ -25,6 +25,36 @@ def test_fft_sign_and_scale_conventions():
     assert np.sum(np.abs(np.fft.fft2(x)) ** 2) == pytest.approx(n * n * np.sum(np.abs(x) ** 2), rel=1e-13)
 
 
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 64])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_own_radix2_fft_equals_the_direct_dft(n, inverse):
+    rng = np.random.default_rng(n + 3)
+    x = rng.standard_normal((3, n)) + 1j * rng.standard_normal((3, n))
+    j = np.arange(n)
+    W = np.exp((2j if inverse else -2j) * np.pi * np.outer(j, j) / n)
+    np.testing.assert_allclose(O.fft_radix2(x, inverse), x @ W.T, atol=1e-12 * max(1, n))
+
+
+def test_numpy_fft_equals_the_own_radix2_fft():
+    """The library primitive against the oracle's own transform at sizes the direct DFT cannot reach."""
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((4, 4096)) + 1j * rng.standard_normal((4, 4096))
+    ref = O.fft_radix2(x)
+    assert np.abs(np.fft.fft(x, axis=1) - ref).max() <= 1e-11 * np.abs(ref).max()
+    x2 = rng.standard_normal((128, 128)) + 1j * rng.standard_normal((128, 128))
+    np.testing.assert_allclose(np.fft.fft2(x2), O.fft2_radix2(x2), atol=1e-10)
+    np.testing.assert_allclose(np.fft.ifft2(x2) * 128 * 128, O.fft2_radix2(x2, inverse=True), atol=1e-10)
+
+
+def test_propagation_through_the_own_fft():
+    """propagate_field (numpy's FFT) equals IDFT(DFT(A_in) H) / N^2 with the own radix-2 FFT."""
+    p = O.ScreenParams(n=64, pixel_km=10.0, r_diff_km=20.0, seed=3)
+    a_in = O.screen_field(O.make_screen(p), p, 520.0)
+    H = O.transfer_function(64, 10.0, 520.0, p.z_pc)
+    own = O.fft2_radix2(O.fft2_radix2(a_in) * H, inverse=True) / (64 * 64)
+    np.testing.assert_allclose(O.propagate_field(a_in, 10.0, 520.0, p.z_pc), own, atol=1e-12)
+
+
 def test_uniform_untapered_screen_is_exactly_one():
     p = O.ScreenParams(n=64, pixel_km=20.0, r_diff_km=100.0, margin_km=0.0)
     I = O.intensity_mono(np.zeros((64, 64)), p)

@@ -31,6 +31,10 @@ def _noalloc(p, phi, out):
 
 
 def test_noalloc_matches_propagate_on_two_calls_in_a_row():
+    """Both entry points run the same kernels on the same inputs, and the no-allocation one fills
+    its twiddle table with the same kernel as the table the other keeps: the maps are identical
+    bit for bit, on each of two calls in a row (stale scratch from the first call cannot leak
+    into the second)."""
     cases = [S.params(n=1024, pixel_km=10.0, r_diff_km=40.0, lambda_nm=620.0, lambda_ref_nm=550.0, seed=11),
              S.params(n=256, pixel_km=20.0, r_diff_km=100.0, seed=12, margin_km=0.0)]
     outs = []
@@ -41,13 +45,34 @@ def test_noalloc_matches_propagate_on_two_calls_in_a_row():
         rc = _noalloc(p, phi, out)
         assert rc == 0, S.lib().scint_last_error().decode()
         torch.cuda.synchronize()
-        err = (out - ref).abs().max().item()
-        assert err <= I_TOL, err
+        assert torch.equal(out, ref), (out - ref).abs().max().item()
+        assert (out - ref).abs().max().item() <= I_TOL
         outs.append(out)
     # the first result is unchanged by the second call (outputs are the caller's)
     p = cases[0]
     again = S.propagate(p, S.make_screen(p))
-    assert (outs[0] - again).abs().max().item() <= I_TOL
+    assert torch.equal(outs[0], again)
+
+
+def test_noalloc_allocates_no_device_memory():
+    """With the library's pool and kept tables released (scint_release), a call takes no device
+    memory: free memory is the same before and after it (the pool or a twiddle table at
+    n = 1024 would take at least 8 MiB).  One call first loads the kernels, whose code also
+    occupies device memory."""
+    p = S.params(n=1024, pixel_km=10.0, r_diff_km=40.0, seed=13)
+    phi = S.make_screen(p)
+    ref = S.propagate(p, phi)
+    out = torch.empty((p.n, p.n), dtype=torch.float32, device="cuda")
+    assert _noalloc(p, phi, out) == 0
+    torch.cuda.synchronize()
+    S.lib().scint_release()
+    free0, _ = torch.cuda.mem_get_info()
+    out.fill_(float("nan"))
+    assert _noalloc(p, phi, out) == 0, S.lib().scint_last_error().decode()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0 - free1)
+    assert torch.equal(out, ref)
 
 
 def test_noalloc_rejects_grids_beyond_its_static_scratch():
