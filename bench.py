@@ -363,10 +363,21 @@ def run_ours(args):
             for i, (p, it) in enumerate(zip(P, items)):
                 plain_screen(i, p, it)
         else:
-            S.run_batch(batch, lams, wts, n_lanes=args.lanes, workspace=ws)
+            S.run_batch(batch, lams, wts, n_lanes=lanes, workspace=ws)
 
-    # propagation plans: the autotuner times the built variants per grid size (outside capture)
-    plans = {str(n): S.tune(n, n_lam) for n in sizes}
+    # propagation plans: the autotuner times the built variants per grid size (outside capture),
+    # or a fixed choice (--plans unpacked / packed)
+    lanes = args.lanes
+    tuned_batch = None
+    if args.plans == "tune":
+        # the batch tuner times the whole batch under candidate plan sets and lane counts
+        lanes, tuned_ms = S.tune_batch(batch, lams, wts, workspace=ws)
+        tuned_batch = {"lanes": lanes, "ms": tuned_ms}
+        plans = {str(n): S.get_plan(n) for n in sizes}
+    else:
+        for n in sizes:
+            S.set_plan(n, 1 if args.plans == "packed" else 0, 2, 2 if args.plans == "packed" else 1, 16)
+        plans = {str(n): S.get_plan(n) for n in sizes}
     # warm-up outside the graph (sets kernel attributes), then capture one graph of the step
     step()
     torch.cuda.synchronize(dev)
@@ -512,8 +523,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": desc, "form": f"scint_run_batch on {args.lanes} lane(s), one CUDA graph per step",
-                           "plans": plans,
+                "config": {"workload": desc, "form": f"scint_run_batch on {lanes} lane(s), one CUDA graph per step",
+                           "plans": plans, "batch_tuner": tuned_batch,
                            "l2": "inputs larger than L2 (fields 32-134 MB per screen and wavelength)",
                            "parallelism": f"independent batch per GPU x{world}"},
                 "roofline": roof, "cpu_baseline": cpu,
@@ -1109,6 +1120,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plans", default="tune", choices=["tune", "unpacked", "packed"],
+                    help="propagation plans: autotuned per grid size, or fixed")
     ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "large16384", "screen_check", "conjugate",
                                                               "m_sweep", "timeseries", "gradient"])
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")

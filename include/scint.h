@@ -454,6 +454,8 @@ int scint_rdiff_gradient(const scint_params* p, const double* phi, const double*
  *   packed        1: two wavelengths per thread (packed two-wide FP32 arithmetic),
  *                 used for groups of >= 2 wavelengths at 64 <= N <= 8192;
  *                 0: one wavelength per thread.
+ *   points        values per thread of the packed passes: 16 (radix-16 stages) or
+ *                 8 (radix-8 stages, twice the threads per line, N >= 128).
  *   row_twiddles  FFT twiddle source of the packed row pass: 1 the block's shared
  *                 table, 2 register bases and products.
  *   col_twiddles  the same for the packed column pass.
@@ -464,9 +466,11 @@ int scint_rdiff_gradient(const scint_params* p, const double* phi, const double*
  */
 typedef struct scint_plan {
     int32_t packed;
+    int32_t points;
     int32_t row_twiddles;
     int32_t col_twiddles;
     int32_t tuned;      /* out: 1 if scint_tune measured this plan, 0 otherwise */
+    int32_t reserved;   /* 0 */
     double  ms;         /* out: scint_tune's best time for its test passband, else 0 */
 } scint_plan;
 
@@ -489,6 +493,24 @@ int scint_set_plan(int n, const scint_plan* plan);
  * allowed while `stream` is being captured (SCINT_EINVAL).
  */
 int scint_tune(int n, int n_lambda, scint_plan* out, void* stream);
+
+/*
+ * Batch autotuner: the plans that win alone are not always the fastest when
+ * several screens run at once on the batch executor's lanes (blocks that need
+ * more shared memory leave less room for the other lanes' kernels).  This times
+ * scint_run_batch on the given batch under each candidate: plan sets {the
+ * per-size winners of scint_tune, every size on the one-wavelength passes, every
+ * size on the default packed passes} x lanes {4, 8} (those the workspace holds,
+ * at most n_items), one warm-up and two timed runs each with CUDA events on
+ * `stream`, and keeps the fastest: its plans become the plans of the batch's
+ * grid sizes (tuned = 1, ms = the batch time) and its lane count is returned in
+ * *out_lanes (*out_ms: its time).  Runs the batch's whole forward path about 20
+ * times; writes the items' outputs.  Synchronous; not allowed during capture.
+ *   workspace, workspace_bytes  as for scint_run_batch (NULL: the pool).
+ */
+int scint_tune_batch(const scint_batch_item* items, int n_items, const double* lambdas_nm, const double* weights,
+                     int n_lambda, void* workspace, size_t workspace_bytes, int* out_lanes, double* out_ms,
+                     void* stream);
 
 /* Autotuning on first use (off by default): while on, scint_run_batch calls
  * scint_tune for every grid size of its items that has no plan on the current

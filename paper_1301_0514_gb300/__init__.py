@@ -13,6 +13,7 @@ from ._lib import (  # noqa: F401
     get_plan,
     set_plan,
     tune,
+    tune_batch,
     batch_items,
     batch_workspace_bytes,
     SamplingWarning,

@@ -93,11 +93,12 @@ class KernelStat(ctypes.Structure):
 
 class ScintPlan(ctypes.Structure):
     """Mirror of struct scint_plan (include/scint.h)."""
-    _fields_ = [("packed", ctypes.c_int32), ("row_twiddles", ctypes.c_int32), ("col_twiddles", ctypes.c_int32),
-                ("tuned", ctypes.c_int32), ("ms", ctypes.c_double)]
+    _fields_ = [("packed", ctypes.c_int32), ("points", ctypes.c_int32), ("row_twiddles", ctypes.c_int32),
+                ("col_twiddles", ctypes.c_int32), ("tuned", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 _lib = None
@@ -152,6 +153,8 @@ def lib() -> ctypes.CDLL:
         "scint_set_plan": ([_i, ctypes.POINTER(ScintPlan)], _i),
         "scint_tune": ([_i, _i, ctypes.POINTER(ScintPlan), _vp], _i),
         "scint_autotune": ([_i], _i),
+        "scint_tune_batch": ([ctypes.POINTER(BatchItem), _i, _vp, _vp, _i, _vp, _sz, ctypes.POINTER(_i),
+                              ctypes.POINTER(ctypes.c_double), _vp], _i),
         "scint_profile_enable": ([_i], _i),
         "scint_profile_read": ([ctypes.POINTER(KernelStat), _i, ctypes.POINTER(_i)], _i),
     }
@@ -558,9 +561,10 @@ def get_plan(n: int) -> dict:
     return pl.as_dict()
 
 
-def set_plan(n: int, packed: int, row_twiddles: int = 2, col_twiddles: int = 1):
+def set_plan(n: int, packed: int, row_twiddles: int = 2, col_twiddles: int = 1, points: int = 16):
     """Fix the propagation plan of grid n on the current device (scint_set_plan)."""
-    pl = ScintPlan(packed=packed, row_twiddles=row_twiddles, col_twiddles=col_twiddles, tuned=0, ms=0.0)
+    pl = ScintPlan(packed=packed, points=points, row_twiddles=row_twiddles, col_twiddles=col_twiddles, tuned=0,
+                   reserved=0, ms=0.0)
     _check(lib().scint_set_plan(n, ctypes.byref(pl)))
 
 
@@ -569,6 +573,21 @@ def tune(n: int, n_lambda: int = 32, stream=None) -> dict:
     pl = ScintPlan()
     _check(lib().scint_tune(n, n_lambda, ctypes.byref(pl), ctypes.c_void_p(_stream(stream))))
     return pl.as_dict()
+
+
+def tune_batch(items, lambdas_nm, weights=None, workspace: Optional[torch.Tensor] = None, stream=None):
+    """Time the batch under candidate plan sets and lane counts and keep the fastest
+    (scint_tune_batch).  Returns (lanes, ms); the plans of the batch's grid sizes are set."""
+    arr = items if isinstance(items, ctypes.Array) else batch_items(items)
+    lam = np.ascontiguousarray(lambdas_nm, dtype=np.float64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    wp, wb = (None, 0) if workspace is None else (ctypes.c_void_p(workspace.data_ptr()),
+                                                  workspace.numel() * workspace.element_size())
+    lanes, ms = _i(0), ctypes.c_double(0.0)
+    _check(lib().scint_tune_batch(arr, len(arr), lam.ctypes.data_as(ctypes.c_void_p),
+                                  None if w is None else w.ctypes.data_as(ctypes.c_void_p), len(lam), wp, wb,
+                                  ctypes.byref(lanes), ctypes.byref(ms), _stream(stream)))
+    return lanes.value, ms.value
 
 
 def autotune(on: bool = True) -> bool:

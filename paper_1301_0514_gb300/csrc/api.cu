@@ -352,15 +352,19 @@ int check_passband(const scint_params* p, const double* lambdas, const double* w
 }
 
 // ---- propagation plans (variants of the transfer-function passes) ----------------
-// Default: the one-wavelength passes (the packed ones run when a plan selects them).
+// Default, from measurements on GB300 (1024^2-8192^2, 8 and 32 wavelengths): the packed
+// passes with 16 values per thread and register twiddle bases in both passes, 1-4 %
+// faster than the one-wavelength passes; with 8 values per thread or the shared twiddle
+// table they were slower.  Grid sizes without packed passes use the one-wavelength ones.
 std::mutex g_plan_mu;
 std::map<std::pair<int, int>, scint_plan> g_plans;   // (device, n) -> plan
 
 scint_plan default_plan(int n) {
     scint_plan pl{};
-    pl.packed = 0;
+    pl.packed = packed_prop_supported(n, 16, 2, 2) ? 1 : 0;
+    pl.points = 16;
     pl.row_twiddles = 2;
-    pl.col_twiddles = 1;
+    pl.col_twiddles = pl.packed ? 2 : 1;
     return pl;
 }
 
@@ -438,15 +442,15 @@ int run_group(const scint_params* p, const double* phi, const double* lam, const
     scint_plan pl{};
     int rc = plan_for(n, &pl);
     if (rc) return rc;
-    const bool packed = pl.packed && g > 1 && packed_prop_supported(n, pl.row_twiddles, pl.col_twiddles);
+    const bool packed = pl.packed && g > 1 && packed_prop_supported(n, pl.points, pl.row_twiddles, pl.col_twiddles);
     const double nn = (double)n * n;
     SCINT_LAUNCH(K_PROP_TABLES, 4.0 * g * n, 0.0, s, launch_prop_tables(ta, s));
     // rows: phi read once, one complex64 field written per wavelength; FFT_x + IFFT_x per row
     SCINT_LAUNCH(K_PROP_ROWS, 8.0 * nn + 8.0 * g * nn, 2.0 * g * n * fft_flops(n), s,
-                 packed ? launch_prop_rows2(pa, pl.row_twiddles, s) : launch_prop_rows(pa, false, s));
+                 packed ? launch_prop_rows2(pa, pl.points, pl.row_twiddles, s) : launch_prop_rows(pa, false, s));
     // columns: fields read, intensity written once (and read when accumulating)
     SCINT_LAUNCH(K_PROP_COLS, 8.0 * g * nn + (accumulate ? 8.0 : 4.0) * nn, 2.0 * g * n * fft_flops(n), s,
-                 packed ? launch_prop_cols2(pa, pl.col_twiddles, s) : launch_prop_cols(pa, false, s));
+                 packed ? launch_prop_cols2(pa, pl.points, pl.col_twiddles, s) : launch_prop_cols(pa, false, s));
     return SCINT_OK;
 }
 
@@ -626,6 +630,20 @@ size_t forward_workspace_bytes(int n, int g) {
 int pool_workspace(size_t bytes, cudaStream_t s, void** out) { return pool_get(bytes, s, out); }
 bool autotune_on() { return g_autotune.load() != 0; }
 bool has_plan(int n) { return plan_known(n); }
+int plan_of(int n, scint_plan* out) { return plan_for(n, out); }
+int set_tuned_plan(int n, scint_plan pl, double ms) {
+    pl.tuned = 1;
+    pl.ms = ms;
+    return store_plan(n, pl);
+}
+scint_plan one_wavelength_plan() {
+    scint_plan pl{};
+    pl.points = 16;
+    pl.row_twiddles = 2;
+    pl.col_twiddles = 1;
+    return pl;
+}
+scint_plan packed_default_plan(int n) { return default_plan(n); }
 }  // namespace scint
 
 namespace {
@@ -763,11 +781,14 @@ int scint_set_plan(int n, const scint_plan* plan) {
         return fail(SCINT_EINVAL, "n=%d must be a power of two in [%d, %d]", n, SCINT_MIN_N, SCINT_MAX_N);
     const bool tw_ok = (plan->row_twiddles == 1 || plan->row_twiddles == 2) &&
                        (plan->col_twiddles == 1 || plan->col_twiddles == 2);
-    if ((plan->packed != 0 && plan->packed != 1) || !tw_ok)
-        return fail(SCINT_EINVAL, "packed must be 0 or 1 and the twiddle sources 1 or 2");
-    if (plan->packed && !packed_prop_supported(n, plan->row_twiddles, plan->col_twiddles))
-        return fail(SCINT_EUNSUPPORTED, "the packed passes with twiddle sources (%d, %d) are not built for n=%d",
-                    plan->row_twiddles, plan->col_twiddles, n);
+    if ((plan->packed != 0 && plan->packed != 1) || !tw_ok || (plan->points != 8 && plan->points != 16) ||
+        plan->reserved)
+        return fail(SCINT_EINVAL, "packed must be 0 or 1, points 8 or 16, the twiddle sources 1 or 2, "
+                                  "reserved 0");
+    if (plan->packed && !packed_prop_supported(n, plan->points, plan->row_twiddles, plan->col_twiddles))
+        return fail(SCINT_EUNSUPPORTED, "the packed passes with %d points per thread and twiddle sources (%d, %d) "
+                                        "are not built for n=%d", plan->points, plan->row_twiddles,
+                    plan->col_twiddles, n);
     scint_plan pl = *plan;
     pl.tuned = 0;
     pl.ms = 0.0;
@@ -783,14 +804,15 @@ int scint_tune(int n, int n_lambda, scint_plan* out, void* stream) {
     SCINT_CUDA(cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone) return fail(SCINT_EINVAL, "scint_tune cannot run during stream capture");
     std::vector<scint_plan> cand;
-    scint_plan one_wl{};
-    one_wl.packed = 0;
-    one_wl.row_twiddles = 2;
-    one_wl.col_twiddles = 1;
-    cand.push_back(one_wl);
-    for (int r = 1; r <= 2; ++r)
-        for (int c = 1; c <= 2; ++c)
-            if (packed_prop_supported(n, r, c)) cand.push_back(scint_plan{1, r, c, 0, 0.0});
+    scint_plan one{};
+    one.points = 16;
+    one.row_twiddles = 2;
+    one.col_twiddles = 1;
+    cand.push_back(one);     // the one-wavelength passes
+    for (int pts : {16, 8})
+        for (int r = 1; r <= 2; ++r)
+            for (int c = 1; c <= 2; ++c)
+                if (packed_prop_supported(n, pts, r, c)) cand.push_back(scint_plan{1, pts, r, c, 0, 0, 0.0});
     // test passband: n_lambda in [2, 32], fields within 1 GiB
     int g = std::max(2, std::min(n_lambda, 32));
     const size_t field = (size_t)n * n * 8;

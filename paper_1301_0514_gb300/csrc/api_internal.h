@@ -37,5 +37,10 @@ void release_lanes();
 // Autotuning on first use (scint_autotune) is on; grid n has a plan on the current device.
 bool autotune_on();
 bool has_plan(int n);
+// Plan of grid n on the current device (tuned or default), and setting it as measured (tuned = 1).
+int plan_of(int n, scint_plan* out);
+int set_tuned_plan(int n, scint_plan pl, double ms);
+scint_plan one_wavelength_plan();
+scint_plan packed_default_plan(int n);
 
 }  // namespace scint

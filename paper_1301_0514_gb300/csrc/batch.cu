@@ -270,6 +270,83 @@ int scint_run_batch(const scint_batch_item* items, int n_items, const double* la
     return scint::clear_error();
 }
 
+int scint_tune_batch(const scint_batch_item* items, int n_items, const double* lambdas_nm, const double* weights,
+                     int n_lambda, void* workspace, size_t workspace_bytes, int* out_lanes, double* out_ms,
+                     void* stream) {
+    int rc = check_batch(items, n_items, lambdas_nm, weights, n_lambda, 1);
+    if (rc) return rc;
+    if (n_items == 0 || !out_lanes) return set_error(SCINT_EINVAL, "scint_tune_batch needs items and out_lanes");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // lane counts tried: 4 and 8, or the item count when it is smaller
+    std::vector<int> lane_opts;
+    for (int l : {4, 8})
+        if (std::find(lane_opts.begin(), lane_opts.end(), std::min(l, n_items)) == lane_opts.end())
+            lane_opts.push_back(std::min(l, n_items));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone) return set_error(SCINT_EINVAL, "scint_tune_batch cannot run during capture");
+    std::vector<int> sizes;
+    for (int i = 0; i < n_items; ++i)
+        if (std::find(sizes.begin(), sizes.end(), items[i].params.n) == sizes.end()) sizes.push_back(items[i].params.n);
+    // candidate plan sets: per-size winners alone, all one-wavelength, all default packed
+    std::vector<std::vector<scint_plan>> sets(3, std::vector<scint_plan>(sizes.size()));
+    for (size_t k = 0; k < sizes.size(); ++k) {
+        if ((rc = scint_tune(sizes[k], n_lambda, &sets[0][k], stream))) return rc;
+        sets[1][k] = scint::one_wavelength_plan();
+        sets[2][k] = scint::packed_default_plan(sizes[k]);
+    }
+    auto same = [&](const std::vector<scint_plan>& a, const std::vector<scint_plan>& b) {
+        for (size_t k = 0; k < a.size(); ++k)
+            if (a[k].packed != b[k].packed || (a[k].packed && (a[k].points != b[k].points ||
+                a[k].row_twiddles != b[k].row_twiddles || a[k].col_twiddles != b[k].col_twiddles)))
+                return false;
+        return true;
+    };
+    const Sizes z = batch_sizes(items, n_items);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    double best = 1e300;
+    int best_set = -1, best_lanes = 0;
+    for (size_t c = 0; c < sets.size() && !rc; ++c) {
+        bool dup = false;
+        for (size_t d = 0; d < c; ++d) dup |= same(sets[c], sets[d]);
+        if (dup) continue;
+        for (size_t k = 0; k < sizes.size() && !rc; ++k) rc = scint::set_tuned_plan(sizes[k], sets[c][k], 0.0);
+        for (int lanes : lane_opts) {
+            if (rc) break;
+            if (workspace && workspace_bytes < (size_t)lanes * lane_bytes(z, 1)) continue;
+            double t = 1e300;
+            for (int rep = 0; rep < 3 && !rc; ++rep) {
+                if ((e = cudaEventRecord(e0, s)) != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
+                if (!rc) rc = scint_run_batch(items, n_items, lambdas_nm, weights, n_lambda, lanes, workspace,
+                                              workspace_bytes, stream);
+                if (!rc && ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess))
+                    rc = cuda_fail(e, "timing the batch");
+                float ms = 0.0f;
+                if (!rc && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t = std::min(t, (double)ms);
+            }
+            if (!rc && t < best) {
+                best = t;
+                best_set = (int)c;
+                best_lanes = lanes;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best_set < 0) return set_error(SCINT_ENOMEM, "the workspace holds too few lanes of this batch");
+    for (size_t k = 0; k < sizes.size(); ++k)
+        if ((rc = scint::set_tuned_plan(sizes[k], sets[best_set][k], best))) return rc;
+    *out_lanes = best_lanes;
+    if (out_ms) *out_ms = best;
+    return scint::clear_error();
+}
+
 }  // extern "C"
 
 // Called by scint_release: destroy the lanes of every device.

@@ -1,13 +1,14 @@
 // Shared-memory Stockham FFT for one line of N points held by a team of
 // threads (FP32 float2, FP64 double2 or double-float dfc).
 //
-// A team of T = N/E threads (E = 16 or 32) transforms one line; thread t holds the E values at
+// A team of T = N/E threads (E = 8, 16 or 32) transforms one line; thread t holds the E values at
 // positions t + m*T (m = 0..E-1) in registers, both on entry and on exit (the
 // Stockham autosort keeps that distribution, so a forward transform, a pointwise
 // multiply and an inverse transform chain with no extra data movement).
 //
 // Radix plan: the first stage is radix 16 (or N for N < 16), then radix-16
-// stages, then one radix 2/4/8 stage for the remaining bits.  Between stages the
+// stages, then one radix 2/4/8 stage for the remaining bits (with 8 values per
+// thread: radix-8 stages and a radix 2/4 tail).  Between stages the
 // line goes through the team's shared-memory buffer, padded by one element per
 // 16 so that the stride-16 stores of the first stage are bank-conflict free.
 //
@@ -141,22 +142,27 @@ SCINT_DEV void dft(C* x) {
 }
 
 // ---- plan ----------------------------------------------------------------
-// EPT = values held per thread (16 or 32); each stage's butterflies are spread
-// over the T = N/E threads of the line, E/R butterflies per thread.
+// EPT = values held per thread (8, 16 or 32); each stage's butterflies are spread
+// over the T = N/E threads of the line, E/R butterflies per thread.  The stages
+// are radix 16 (EPT 16 or 32) or radix 8 (EPT 8), then one smaller tail stage.
+// With EPT 8 every stage after the first must have N/R >= 16 (the padded
+// addressing of the loads below), i.e. N >= 128.
 template <int N, int EPT = 16>
 struct FftPlan {
     static_assert(N >= 2 && (N & (N - 1)) == 0, "N must be a power of two");
-    static_assert(EPT == 16 || EPT == 32, "16 or 32 values per thread");
+    static_assert(EPT == 8 || EPT == 16 || EPT == 32, "8, 16 or 32 values per thread");
     static constexpr int LOG2N = ilog2(N);
     static constexpr int E = N < EPT ? N : EPT;          // values per thread
     static constexpr int T = N / E;                      // threads per line
-    static constexpr int R0 = N < 16 ? N : 16;           // radix of the first stage
+    static constexpr int RB = EPT == 8 ? 8 : 16;         // radix of the full stages
+    static constexpr int LB = ilog2(RB);
+    static constexpr int R0 = N < RB ? N : RB;           // radix of the first stage
     static constexpr int REST = LOG2N - ilog2(R0);
-    static constexpr int N16 = REST / 4;                 // radix-16 stages after the first
-    static constexpr int TAIL = REST % 4;                // bits of the last small stage
+    static constexpr int N16 = REST / LB;                // full stages after the first
+    static constexpr int TAIL = REST % LB;               // bits of the last small stage
     static constexpr int NSTAGE = 1 + N16 + (TAIL ? 1 : 0);
     static constexpr int BUF = N + N / 16;               // padded buffer length
-    __host__ __device__ static constexpr int radix(int s) { return s == 0 ? R0 : (s <= N16 ? 16 : (1 << TAIL)); }
+    __host__ __device__ static constexpr int radix(int s) { return s == 0 ? R0 : (s <= N16 ? RB : (1 << TAIL)); }
     __host__ __device__ static constexpr int span(int s) { return s == 0 ? 1 : span(s - 1) * radix(s - 1); }
     // shared twiddle table: for each stage s >= 1, entries [k][r - 1] = W_{PR}^{r k}
     __host__ __device__ static constexpr int twoff(int s) {
@@ -167,9 +173,9 @@ struct FftPlan {
 
 // Fill a block's shared twiddle table from the global table tw[j * stride] = exp(-2 pi i j / N)
 // (stride 2: the table of a line twice as long).
-template <typename C, int N>
+template <typename C, int N, int EPT = 16>
 SCINT_DEV void fill_twiddle_table(C* tws, const C* __restrict__ tw, int tid, int nthreads, int stride = 1) {
-    using Pl = FftPlan<N>;
+    using Pl = FftPlan<N, EPT>;
 #pragma unroll
     for (int s = 1; s < Pl::NSTAGE; ++s) {
         const int R = Pl::radix(s), P = Pl::span(s), base = Pl::twoff(s);
@@ -377,9 +383,11 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
             int j = (i - k) * R + k;
             if constexpr (CS == 2) j &= HALF - 1;
             // P >= 16: pad16(j + r P) = pad16(j) + r P (17/16); P == 1: j = i R and r < R <= 16
+            // (j a multiple of R, so j + r stays in one group of 16); otherwise pad16 itself
             C* dst = wbuf + pad16(j) * LW;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[(P >= 16 ? r * (P + P / 16) : r) * LW] = u[b * R + r];
+            for (int r = 0; r < R; ++r)
+                dst[(P >= 16 ? r * (P + P / 16) : (P == 1 ? r : pad16(j + r * P) - pad16(j))) * LW] = u[b * R + r];
         }
         line_sync<CS>();
         fft_stage<C, N, DIR, EPT, LW, TWM, CS, S + 1, TS, PP>(v, buf, t, tw, tr, buf1);

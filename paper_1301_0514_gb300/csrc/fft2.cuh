@@ -198,10 +198,10 @@ SCINT_DEV void apply_twiddles(cp2* u, float2 w1, float2 w4, const float2* __rest
 // One stage of the packed transform (see fft_stage in fft.cuh for the indexing).
 // LW lines of pairs share the buffer lane-interleaved (element e of lane w at
 // pad16(e) LW + w; the caller offsets buf by w).
-template <int N, int DIR, int LW, int TWM, int S>
-SCINT_DEV void fft2_stage(cp2 (&v)[FftPlan<N>::E], cp2* buf, int t, const float2* __restrict__ tw,
-                          const TwiddleRegs<float2, N, 16>* tr, const PK& k) {
-    using Pl = FftPlan<N>;
+template <int N, int EPT, int DIR, int LW, int TWM, int S>
+SCINT_DEV void fft2_stage(cp2 (&v)[FftPlan<N, EPT>::E], cp2* buf, int t, const float2* __restrict__ tw,
+                          const TwiddleRegs<float2, N, EPT>* tr, const PK& k) {
+    using Pl = FftPlan<N, EPT>;
     constexpr int E = Pl::E, T = Pl::T;
     constexpr int R = Pl::radix(S), P = Pl::span(S), NB = E / R;
     constexpr bool FIRST = (S == 0), LAST = (S == Pl::NSTAGE - 1);
@@ -242,21 +242,23 @@ SCINT_DEV void fft2_stage(cp2 (&v)[FftPlan<N>::E], cp2* buf, int t, const float2
             const int j = (i - kk) * R + kk;
             cp2* dst = buf + pad16(j) * LW;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[(P >= 16 ? r * (P + P / 16) : r) * LW] = u[b * R + r];
+            for (int r = 0; r < R; ++r)
+                dst[(P >= 16 ? r * (P + P / 16) : (P == 1 ? r : pad16(j + r * P) - pad16(j))) * LW] = u[b * R + r];
         }
         __syncthreads();
-        fft2_stage<N, DIR, LW, TWM, S + 1>(v, buf, t, tw, tr, k);
+        fft2_stage<N, EPT, DIR, LW, TWM, S + 1>(v, buf, t, tw, tr, k);
     }
 }
 
 // Transform the team's pair of lines in place.  TWM 2: register bases tr (tw unused);
 // TWM 1: tw is the block's shared table (fill_twiddle_table).  Every thread of the
 // block must call this the same number of times.
-template <int N, int DIR, int LW, int TWM>
-SCINT_DEV void fft2_line(cp2 (&v)[FftPlan<N>::E], cp2* buf, int t, const float2* __restrict__ tw,
-                         const TwiddleRegs<float2, N, 16>* tr, const PK& k) {
+template <int N, int EPT, int DIR, int LW, int TWM>
+SCINT_DEV void fft2_line(cp2 (&v)[FftPlan<N, EPT>::E], cp2* buf, int t, const float2* __restrict__ tw,
+                         const TwiddleRegs<float2, N, EPT>* tr, const PK& k) {
     static_assert(TWM == 1 || TWM == 2, "shared table or register bases");
-    fft2_stage<N, DIR, LW, TWM, 0>(v, buf, t, tw, tr, k);
+    static_assert(EPT != 8 || N >= 128, "8 values per thread: N >= 128");
+    fft2_stage<N, EPT, DIR, LW, TWM, 0>(v, buf, t, tw, tr, k);
 }
 
 }  // namespace scint

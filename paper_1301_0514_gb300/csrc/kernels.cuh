@@ -93,10 +93,11 @@ cudaError_t launch_prop_rows(const PropArgs& a, bool conj, cudaStream_t s);
 cudaError_t launch_prop_cols(const PropArgs& a, bool conj, cudaStream_t s);
 // Transfer-function passes with two wavelengths per thread (propagate2.cu): the field
 // of wavelengths 2q, 2q + 1 is one array of 16-byte pixels at work + q N^2 (as cp2);
+// points: values per thread (16: radix-16 stages; 8: radix-8 stages, twice the threads);
 // twm: twiddles from register bases (2) or the block's shared table (1).
-bool packed_prop_supported(int n, int row_twm, int col_twm);
-cudaError_t launch_prop_rows2(const PropArgs& a, int twm, cudaStream_t s);
-cudaError_t launch_prop_cols2(const PropArgs& a, int twm, cudaStream_t s);
+bool packed_prop_supported(int n, int points, int row_twm, int col_twm);
+cudaError_t launch_prop_rows2(const PropArgs& a, int points, int twm, cudaStream_t s);
+cudaError_t launch_prop_cols2(const PropArgs& a, int points, int twm, cudaStream_t s);
 // Passband of one-FFT patterns: intensity (+)= sum_l w_l pattern_l resampled
 // bilinearly (periodic) at (k - n/2) r_l + n/2, r_l in 32.32 fixed point.
 struct ResampleArgs {

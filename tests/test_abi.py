@@ -277,7 +277,7 @@ def test_cpu_tensors_are_refused_no_fallback(lib):
 
 def test_plan_host_checks(lib):
     """Plan calls reject bad grid sizes and variants on the host (no GPU call is made)."""
-    pl = _lib.ScintPlan(packed=1, row_twiddles=3, col_twiddles=1)
+    pl = _lib.ScintPlan(packed=1, points=16, row_twiddles=3, col_twiddles=1)
     assert lib.scint_set_plan(1024, ctypes.byref(pl)) == 1
     assert lib.scint_set_plan(1000, ctypes.byref(pl)) == 1
     assert lib.scint_get_plan(1000, ctypes.byref(pl)) == 1

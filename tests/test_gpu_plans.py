@@ -25,16 +25,21 @@ I_TOL = 2e-4
 def _variants(n):
     """The plans built for n (set_plan accepts them); the plan of n is restored afterwards."""
     before = S.get_plan(n)
-    out = [(0, 2, 1)]
-    for r in (1, 2):
-        for c in (1, 2):
-            try:
-                S.set_plan(n, 1, r, c)
-            except S.ScintError:
-                continue
-            out.append((1, r, c))
-    S.set_plan(n, before["packed"], before["row_twiddles"], before["col_twiddles"])
+    out = [(0, 2, 1, 16)]
+    for pts in (16, 8):
+        for r in (1, 2):
+            for c in (1, 2):
+                try:
+                    S.set_plan(n, 1, r, c, pts)
+                except S.ScintError:
+                    continue
+                out.append((1, r, c, pts))
+    _restore(n, before)
     return out
+
+
+def _restore(n, pl):
+    S.set_plan(n, pl["packed"], pl["row_twiddles"], pl["col_twiddles"], pl["points"])
 
 
 @pytest.mark.parametrize("n,n_lam", [(64, 3), (256, 2), (1024, 5), (2048, 4), (4096, 3)])
@@ -57,11 +62,11 @@ def test_every_variant_matches_the_oracle(n, n_lam):
             maps[v] = got
             assert np.abs(got.cpu().numpy() - ref).max() <= I_TOL, v
         assert len(maps) >= (1 if n < 64 else 3)
-        base = maps[(0, 2, 1)]
+        base = maps[(0, 2, 1, 16)]
         for v, m in maps.items():
             assert (m - base).abs().max().item() <= 1e-5, v
     finally:
-        S.set_plan(n, before["packed"], before["row_twiddles"], before["col_twiddles"])
+        _restore(n, before)
 
 
 def test_packed_groups_and_accumulate():
@@ -73,7 +78,7 @@ def test_packed_groups_and_accumulate():
     lams = np.linspace(420.0, 690.0, 7)
     phi = O.make_screen(p_o)
     ref = 0.5 + O.sum_passband(phi, p_o, lams)
-    S.set_plan(n, 1, 2, 1)
+    S.set_plan(n, 1, 2, 1, 8)
     ws = torch.empty(S.workspace_bytes(p_g, 3), dtype=torch.uint8, device="cuda")
     out = torch.full((n, n), 0.5, device="cuda")
     S.sum_passband(p_g, torch.from_numpy(phi).cuda(), lams, out=out, accumulate=True, workspace=ws)
@@ -85,8 +90,8 @@ def test_tune_keeps_a_measured_plan():
     pl = S.tune(n, 8)
     assert pl["tuned"] == 1 and pl["ms"] > 0.0
     assert S.get_plan(n) == pl
-    assert (pl["packed"], pl["row_twiddles"], pl["col_twiddles"]) in _variants(n)
-    S.set_plan(n, pl["packed"], pl["row_twiddles"], pl["col_twiddles"])
+    assert (pl["packed"], pl["row_twiddles"], pl["col_twiddles"], pl["points"]) in _variants(n)
+    _restore(n, pl)
     again = S.get_plan(n)
     assert again["tuned"] == 0 and again["packed"] == pl["packed"]
 
@@ -104,6 +109,9 @@ def test_set_plan_rejects_variants_not_built():
     with pytest.raises(S.ScintError) as e:
         S.set_plan(1024, 1, 3, 1)
     assert e.value.code == 1      # SCINT_EINVAL
+    with pytest.raises(S.ScintError) as e:
+        S.set_plan(64, 1, 2, 1, 8)   # 8 values per thread need N >= 128
+    assert e.value.code == 5
 
 
 def test_batch_autotunes_unplanned_sizes_only_outside_capture():
@@ -134,3 +142,27 @@ def test_batch_autotunes_unplanned_sizes_only_outside_capture():
         assert torch.equal(ref, item2["intensity"])
     finally:
         S.autotune(old)
+
+
+def test_batch_tuner_keeps_the_fastest_plans_and_lanes():
+    """scint_tune_batch times the batch under candidate plan sets and lane counts; afterwards the
+    batch's sizes carry measured plans and a run with the returned lanes equals the single calls."""
+    lams = [480.0, 540.0, 600.0, 660.0]
+    entries = []
+    for i, n in enumerate((256, 512, 256, 512, 256)):
+        kw = dict(n=n, pixel_km=15.0, r_diff_km=70.0, lambda_nm=540.0, lambda_ref_nm=540.0, seed=40 + i, screen_id=i)
+        entries.append(dict(params=S.params(**kw), phi=torch.empty((n, n), dtype=torch.float64, device="cuda"),
+                            intensity=torch.empty((n, n), device="cuda")))
+    batch = S.batch_items(entries)
+    lanes, ms = S.tune_batch(batch, lams)
+    assert lanes in (4, 5) and ms > 0.0
+    for n in (256, 512):
+        pl = S.get_plan(n)
+        assert pl["tuned"] == 1 and pl["ms"] == pytest.approx(ms)
+    S.run_batch(batch, lams, n_lanes=lanes)
+    torch.cuda.synchronize()
+    for e in entries:
+        p = e["params"]
+        ref = S.sum_passband(p, S.make_screen(p), lams)
+        S.smooth_source(p, ref)
+        assert torch.equal(ref, e["intensity"])
