@@ -605,6 +605,8 @@ SynthArgs synth_args(const scint_params* p) {
     a.amp_rel_lo = (float)((a.amp - (double)a.amp32) / (double)a.amp32);
     a.neg_beta_4_lo = (float)(a.neg_beta_4 - (double)a.neg_beta_4_32);
     a.out_scale = std::sqrt(2.0) / (L * L);
+    a.out_scale_df.hi = (float)a.out_scale;
+    a.out_scale_df.lo = (float)(a.out_scale - (double)a.out_scale_df.hi);
     return a;
 }
 

@@ -92,6 +92,23 @@ SCINT_DEV dfl operator*(dfl a, dfl b) {
 }
 SCINT_DEV double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
 
+// float -> double from the bits, with integer instructions only (exact for normal numbers
+// and zero; a subnormal float, below 1.2e-38, becomes 0; no inf or NaN arises here)
+SCINT_DEV double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) |       // 1023 - 127
+                                 ((unsigned long long)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double(e ? (long long)d : 0ll);
+}
+// s * a as a double: the product in double-float, then one FP64 addition (the FP64 pipe of
+// GB300 is narrow; the conversions of to_double and an FP64 multiply would cost three more)
+SCINT_DEV double scaled_to_double(dfl a, dfl s) {
+    const dfl p = a * s;
+    return f2d_bits(p.hi) + f2d_bits(p.lo);
+}
+
 // complex double-float (x real, y imaginary), 16 bytes like double2
 struct __align__(16) dfc {
     dfl x, y;

@@ -38,6 +38,7 @@ struct SynthArgs {
     float amp_rel_lo;             // (amp - amp32) / amp32
     float neg_beta_4_lo;          // -beta/4 - neg_beta_4_32
     double out_scale;    // sqrt(2) / L^2
+    dfl out_scale_df;    // the same as a double-float
     const dfc* tw;       // double-float twiddles for n
     dfc* work;           // (n/2 + 1) x n double-float complex, row-major: rows ky = 0..n/2 after the x transform
     double* phi;         // n*n, row-major

@@ -98,10 +98,21 @@ synth_rows_kernel(SynthArgs a) {
     const int ky = (blockIdx.x / CS) * B + team;
     const bool live = ky <= N / 2;                 // rows above N/2 are the conjugates of rows below
     dfc v[E];
+    dfc* buf = smem_df + team * (Pl::BUF / CS);
+    if constexpr (CS == 1) {
+        // the bins are drawn in a loop that is not unrolled (one copy of the Philox and
+        // Box-Muller code: unrolled sixteen times it overflowed the instruction cache) and
+        // staged in the line buffer, where each thread reads back its own entries
+#pragma unroll 1
+        for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = live ? hermitian_bin(a, t + m * T, ky) : make_c<dfc>(0.0, 0.0);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = live ? hermitian_bin(a, t + m * T, ky) : make_c<dfc>(0.0, 0.0);
+        for (int m = 0; m < E; ++m) v[m] = buf[pad16(t + m * T)];
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = live ? hermitian_bin(a, t + m * T, ky) : make_c<dfc>(0.0, 0.0);
+    }
     line_sync<CS>();
-    fft_line<dfc, N, +1, 16, 1, 0, CS>(v, smem_df + team * (Pl::BUF / CS), t, a.tw);
+    fft_line<dfc, N, +1, 16, 1, 0, CS>(v, buf, t, a.tw);
     if (live) {
 #pragma unroll
         for (int m = 0; m < E; ++m) a.work[(size_t)ky * N + t + m * T] = v[m];
@@ -136,8 +147,8 @@ synth_cols_kernel(SynthArgs a) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         double* o = a.phi + (size_t)(t + m * T) * N + xa;
-        o[0] = a.out_scale * to_double(v[m].x);
-        o[1] = a.out_scale * to_double(v[m].y);
+        o[0] = scaled_to_double(v[m].x, a.out_scale_df);
+        o[1] = scaled_to_double(v[m].y, a.out_scale_df);
     }
     if constexpr (CS == 2) line_sync<CS>();
 }
@@ -164,9 +175,13 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_rows_split_
 #pragma unroll 1
     for (int ky = blockIdx.x / 2; ky <= N / 2; ky += gridDim.x / 2) {
         dfc v[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = hermitian_bin(a, 2 * (t + m * T) + r, ky);
         cluster_wait();
+        // bins drawn in a loop that is not unrolled and staged in the line buffer (see synth_rows_kernel)
+#pragma unroll 1
+        for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = hermitian_bin(a, 2 * (t + m * T) + r, ky);
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = buf[pad16(t + m * T)];
+        __syncthreads();
         fft_line<dfc, H2, +1, 16, 1, 0, 1, 2>(v, buf, t, a.tw);
         dfc* row = a.work + (size_t)ky * N;
         split_combine<dfc, H2>(v, buf, t, r, a.tw, [&](int, int n, dfc y0, dfc y1) {
@@ -205,11 +220,11 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_cols_split_
         fft_line<dfc, H2, +1, 16, 1, 0, 1, 2>(v, buf, t, a.tw);
         split_combine<dfc, H2>(v, buf, t, r, a.tw, [&](int, int n, dfc y0, dfc y1) {
             double* o = a.phi + (size_t)n * N + xa;
-            o[0] = a.out_scale * to_double(y0.x);
-            o[1] = a.out_scale * to_double(y0.y);
+            o[0] = scaled_to_double(y0.x, a.out_scale_df);
+            o[1] = scaled_to_double(y0.y, a.out_scale_df);
             o = a.phi + (size_t)(n + H2) * N + xa;
-            o[0] = a.out_scale * to_double(y1.x);
-            o[1] = a.out_scale * to_double(y1.y);
+            o[0] = scaled_to_double(y1.x, a.out_scale_df);
+            o[1] = scaled_to_double(y1.y, a.out_scale_df);
         });
     }
     cluster_wait();
