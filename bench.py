@@ -340,7 +340,10 @@ def run_ours(args):
                     m_map=m_map[i], m_curves=m_curve[i], intensity=par_I if i == par_i else None)
                for i, (p, it) in enumerate(zip(P, items))]
     batch = S.batch_items(entries)
-    ws = torch.empty(max(S.batch_workspace_bytes(batch, n_lam, args.lanes),
+    old_mode = S.batch_mode(1)        # the persistent form needs the larger workspace
+    ws_persist = S.batch_workspace_bytes(batch, n_lam, args.lanes)
+    S.batch_mode(old_mode)
+    ws = torch.empty(max(S.batch_workspace_bytes(batch, n_lam, args.lanes), ws_persist,
                          max(S.workspace_bytes(p, 1) for p in P)), dtype=torch.uint8, device=dev)
     # plain form: its own maps, one per grid size
     phi = {n: torch.empty((n, n), dtype=torch.float64, device=dev) for n in sizes}
@@ -369,10 +372,12 @@ def run_ours(args):
     # or a fixed choice (--plans unpacked / packed)
     lanes = args.lanes
     tuned_batch = None
+    if args.batch_mode != "tune":
+        S.batch_mode(1 if args.batch_mode == "persistent" else 0)
     if args.plans == "tune":
         # the batch tuner times the whole batch under candidate plan sets and lane counts
-        lanes, tuned_ms = S.tune_batch(batch, lams, wts, workspace=ws)
-        tuned_batch = {"lanes": lanes, "ms": tuned_ms}
+        lanes, tuned_ms, mode = S.tune_batch(batch, lams, wts, workspace=ws)
+        tuned_batch = {"lanes": lanes, "ms": tuned_ms, "mode": "persistent" if mode == 1 else "lanes"}
         plans = {str(n): S.get_plan(n) for n in sizes}
     else:
         for n in sizes:
@@ -1120,6 +1125,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch-mode", default="tune", choices=["tune", "lanes", "persistent"],
+                    help="batch form: chosen by the batch tuner, or fixed")
     ap.add_argument("--plans", default="tune", choices=["tune", "unpacked", "packed"],
                     help="propagation plans: autotuned per grid size, or fixed")
     ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "large16384", "screen_check", "conjugate",

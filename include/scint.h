@@ -132,7 +132,7 @@ size_t scint_workspace_bytes(const scint_params* p, int n_lambda);
  * about 44 significant bits) and phi is written in FP64.  Against the FP64
  * oracle the screen agrees to better than 2e-6 rad (the measured worst cases are
  * stated with the tests of the full-size workloads).
- *   phi   device, N*N doubles, written.
+ *   phi   device, N*N doubles, written; 16-byte aligned (SCINT_EINVAL otherwise).
  * Needs workspace (16 N^2 bytes).
  */
 int scint_make_screen(const scint_params* p, double* phi,
@@ -191,6 +191,21 @@ int scint_structure_function_rec(const scint_params* p, const double* s_rec, int
  */
 int scint_propagate(const scint_params* p, const double* phi, float* intensity,
                     void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * The plain method in FP64 (Eq. hxy, Sect. 3.2.1): scint_propagate with every step in
+ * double precision, for grids n <= 4096 (SCINT_EUNSUPPORTED above).  The field is
+ * A_in = SF(x) SF(y) exp(i phi lambda_ref / lambda), propagated by the transfer function
+ * (FFT, H = exp(-i pi lambda z |k|^2), inverse FFT, along x then y) with FP64 sines,
+ * cosines and line transforms; the chirp phase is reduced exactly (its constant split so
+ * that the product with m^2 carries no rounding).  One wavelength (p->lambda_nm).
+ *   phi        device, N*N doubles (radians at lambda_ref).
+ *   intensity  device, N*N doubles, written (|A_out|^2, the unobstructed wave = 1).
+ * Needs workspace (16 N^2 + 16 N bytes).  Much slower than the FP32 path on GB300
+ * (its FP64 pipe is narrow); it is the reference-precision form of config-1 sizes.
+ */
+int scint_propagate64(const scint_params* p, const double* phi, double* intensity,
+                      void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * scint_propagate without any device allocation.  The paper has no
@@ -495,22 +510,53 @@ int scint_set_plan(int n, const scint_plan* plan);
 int scint_tune(int n, int n_lambda, scint_plan* out, void* stream);
 
 /*
+ * Batch execution form (build-side; the paper has no counterpart).
+ *   0  lanes (default): every screen through the single-screen entry points on
+ *      up to n_lanes internal streams.
+ *   1  persistent propagation: the screens' syntheses on the lanes, then the
+ *      propagation passes of every screen in ONE persistent launch (one block per
+ *      SM walking a work list of (screen, pass, block of lines) items; a screen's
+ *      column work waits for its row work, and a screen's row work for the column
+ *      work of the screen that used its field slot before it, through counters in
+ *      the workspace), then smoothing and observables on the lanes.  Used when every
+ *      grid size is in [256, 4096], at most 256 screens, and every size's plan is
+ *      the one-wavelength passes; otherwise the call runs on lanes.  Results equal
+ *      the single-screen calls bit for bit.  It needs a larger workspace
+ *      (scint_batch_workspace_bytes accounts for it while the mode is 1): one field
+ *      slot per lane for the whole passband, plus each screen's phase and intensity
+ *      map where the item leaves them NULL.
+ * Every wait of the persistent kernel is bounded: after about 2 s it gives up, sets
+ * a status word to SCINT_ETIMEOUT and ends the launch (the outputs are then
+ * incomplete).  scint_batch_status reads that word.  Returns the previous mode, or
+ * -1 (SCINT_EINVAL in scint_last_error) for a mode other than 0 or 1.
+ */
+int scint_batch_mode(int mode);
+
+/* Waits for `stream`, then returns SCINT_OK, or SCINT_ETIMEOUT if the last persistent
+ * batch launched on the current device gave up a dependency wait (SCINT_ECUDA if the
+ * stream reports an error). */
+int scint_batch_status(void* stream);
+
+/*
  * Batch autotuner: the plans that win alone are not always the fastest when
  * several screens run at once on the batch executor's lanes (blocks that need
  * more shared memory leave less room for the other lanes' kernels).  This times
- * scint_run_batch on the given batch under each candidate: plan sets {the
- * per-size winners of scint_tune, every size on the one-wavelength passes, every
- * size on the default packed passes} x lanes {4, 8} (those the workspace holds,
- * at most n_items), one warm-up and two timed runs each with CUDA events on
- * `stream`, and keeps the fastest: its plans become the plans of the batch's
- * grid sizes (tuned = 1, ms = the batch time) and its lane count is returned in
- * *out_lanes (*out_ms: its time).  Runs the batch's whole forward path about 20
- * times; writes the items' outputs.  Synchronous; not allowed during capture.
- *   workspace, workspace_bytes  as for scint_run_batch (NULL: the pool).
+ * scint_run_batch on the given batch under each candidate: on lanes, plan sets
+ * {the per-size winners of scint_tune, every size on the one-wavelength passes,
+ * every size on the packed passes}, and the persistent form (scint_batch_mode 1,
+ * one-wavelength passes) where the batch allows it; each with lanes {4, 8} (those
+ * the workspace holds, at most n_items), one warm-up and two timed runs with CUDA
+ * events on `stream`.  It keeps the fastest: its plans become the plans of the
+ * batch's grid sizes (tuned = 1, ms = the batch time), its form the batch mode
+ * (*out_mode, may be NULL), and its lane count is returned in *out_lanes (*out_ms:
+ * its time).  Runs the batch's whole forward path about 25 times; writes the
+ * items' outputs.  Synchronous; not allowed during capture.
+ *   workspace, workspace_bytes  as for scint_run_batch (NULL: the pool); the
+ *   persistent candidate is skipped when the workspace is too small for it.
  */
 int scint_tune_batch(const scint_batch_item* items, int n_items, const double* lambdas_nm, const double* weights,
                      int n_lambda, void* workspace, size_t workspace_bytes, int* out_lanes, double* out_ms,
-                     void* stream);
+                     int* out_mode, void* stream);
 
 /* Autotuning on first use (off by default): while on, scint_run_batch calls
  * scint_tune for every grid size of its items that has no plan on the current

@@ -50,6 +50,17 @@ int scint_fft_lines64(int n, int dir, double* data, int n_lines, void* stream);
  */
 int scint_phase_fixed(const double* phi, int64_t* P, int64_t n, void* stream);
 
+/*
+ * Failure injection for the persistent batch kernel (scint_batch_mode 1), on the
+ * host: the next launches count screen `withhold` (its index in the batch) as
+ * having one more row item than it has, so the waits for its row work cannot
+ * succeed, and give up each wait after `wait_limit` counter reads (about 0.2 us
+ * apart; <= 0 restores the default of about 2 s).  withhold < 0 turns it off.
+ * The launch then ends early with SCINT_ETIMEOUT in its status word
+ * (scint_batch_status) and incomplete outputs; nothing faults or hangs.
+ */
+void scint_testing_persist(int withhold, int wait_limit);
+
 #ifdef __cplusplus
 }
 #endif

@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
         "scint_make_screen": ([_P, _vp, _vp, _sz, _vp], _i),
         "scint_propagate": ([_P, _vp, _vp, _vp, _sz, _vp], _i),
         "scint_propagate_noalloc": ([_P, _vp, _vp, _vp], _i),
+        "scint_propagate64": ([_P, _vp, _vp, _vp, _sz, _vp], _i),
         "scint_sum_passband": ([_P, _vp, _vp, _vp, _i, _vp, _i, _vp, _sz, _vp], _i),
         "scint_smooth_source": ([_P, _vp, _vp, _sz, _vp], _i),
         "scint_lightcurve": ([_P, _vp, _vp, _i, _i, _vp, _vp], _i),
@@ -153,8 +154,11 @@ def lib() -> ctypes.CDLL:
         "scint_set_plan": ([_i, ctypes.POINTER(ScintPlan)], _i),
         "scint_tune": ([_i, _i, ctypes.POINTER(ScintPlan), _vp], _i),
         "scint_autotune": ([_i], _i),
+        "scint_batch_mode": ([_i], _i),
+        "scint_batch_status": ([_vp], _i),
+        "scint_testing_persist": ([_i, _i], None),
         "scint_tune_batch": ([ctypes.POINTER(BatchItem), _i, _vp, _vp, _i, _vp, _sz, ctypes.POINTER(_i),
-                              ctypes.POINTER(ctypes.c_double), _vp], _i),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i), _vp], _i),
         "scint_profile_enable": ([_i], _i),
         "scint_profile_read": ([ctypes.POINTER(KernelStat), _i, ctypes.POINTER(_i)], _i),
     }
@@ -240,6 +244,17 @@ def propagate(p: ScintParams, phi: torch.Tensor, out: Optional[torch.Tensor] = N
     ws, wp, wb = _workspace(p, 1, workspace, phi.device)
     _check_warn(lib().scint_propagate(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
                                  _dev(out, torch.float32, p.n * p.n, "intensity"), wp, wb, _stream(stream)))
+    return out
+
+
+def propagate64(p: ScintParams, phi: torch.Tensor, out: Optional[torch.Tensor] = None, workspace=None,
+                stream=None) -> torch.Tensor:
+    """The plain method in FP64 (scint_propagate64): an FP64 intensity map, n <= 4096."""
+    if out is None:
+        out = torch.empty((p.n, p.n), dtype=torch.float64, device=phi.device)
+    ws, wp, wb = _workspace(p, 1, workspace, phi.device)
+    _check_warn(lib().scint_propagate64(ctypes.byref(p), _dev(phi, torch.float64, p.n * p.n, "phi"),
+                                   _dev(out, torch.float64, p.n * p.n, "intensity"), wp, wb, _stream(stream)))
     return out
 
 
@@ -577,17 +592,31 @@ def tune(n: int, n_lambda: int = 32, stream=None) -> dict:
 
 def tune_batch(items, lambdas_nm, weights=None, workspace: Optional[torch.Tensor] = None, stream=None):
     """Time the batch under candidate plan sets and lane counts and keep the fastest
-    (scint_tune_batch).  Returns (lanes, ms); the plans of the batch's grid sizes are set."""
+    (scint_tune_batch).  Returns (lanes, ms, mode); the plans of the batch's grid sizes and the
+    batch mode are set."""
     arr = items if isinstance(items, ctypes.Array) else batch_items(items)
     lam = np.ascontiguousarray(lambdas_nm, dtype=np.float64)
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
     wp, wb = (None, 0) if workspace is None else (ctypes.c_void_p(workspace.data_ptr()),
                                                   workspace.numel() * workspace.element_size())
-    lanes, ms = _i(0), ctypes.c_double(0.0)
+    lanes, ms, mode = _i(0), ctypes.c_double(0.0), _i(0)
     _check(lib().scint_tune_batch(arr, len(arr), lam.ctypes.data_as(ctypes.c_void_p),
                                   None if w is None else w.ctypes.data_as(ctypes.c_void_p), len(lam), wp, wb,
-                                  ctypes.byref(lanes), ctypes.byref(ms), _stream(stream)))
-    return lanes.value, ms.value
+                                  ctypes.byref(lanes), ctypes.byref(ms), ctypes.byref(mode), _stream(stream)))
+    return lanes.value, ms.value, mode.value
+
+
+def batch_mode(mode: int) -> int:
+    """Batch execution form (scint_batch_mode): 0 lanes, 1 persistent propagation; returns the old one."""
+    old = lib().scint_batch_mode(int(mode))
+    if old < 0:
+        raise ScintError(1, lib().scint_last_error().decode())
+    return old
+
+
+def batch_status(stream=None):
+    """Raise ScintError (SCINT_ETIMEOUT) if the last persistent batch gave up a wait (scint_batch_status)."""
+    _check(lib().scint_batch_status(ctypes.c_void_p(_stream(stream))))
 
 
 def autotune(on: bool = True) -> bool:

@@ -17,6 +17,7 @@
 #include "../../include/scint_testing.h"
 #include "api_internal.h"
 #include "kernels.cuh"
+#include "persist.cuh"
 
 namespace scint {
 cudaError_t launch_fft_lines32(int n, int dir, float2* data, int n_lines, const float2* tw, cudaStream_t s);
@@ -132,6 +133,7 @@ size_t ws_prop(int n, int g) {
     return up((size_t)n * 8) + up((size_t)g * n * 4) + up((size_t)field_slots(g) * n * n * 8) +
            (n >= kSplitN ? up((size_t)n * n * 4) : 0);
 }
+size_t ws_prop64(int n) { return n <= kMax64N ? up((size_t)n * 16) + up((size_t)n * n * 16) : 0; }
 size_t ws_smooth(int n) { return up((size_t)n * 8) + up((size_t)(n / 2 + 1) * n * 8); }
 // adjoint: twiddles, g_I map, half spectrum for its disk filter, then the propagation group buffers
 size_t ws_adjoint(int n, int g) {
@@ -257,13 +259,14 @@ int cached_twiddles(int n, int kind, cudaStream_t s, const void** out) {
 enum KClass {
     K_TWIDDLES, K_SYNTH_ROWS, K_SYNTH_COLS, K_PROP_TABLES, K_PROP_ROWS, K_PROP_COLS,
     K_SMOOTH_FWD, K_SMOOTH_ROWS, K_SMOOTH_INV, K_LIGHTCURVE, K_MOMENTS,
-    K_LC_ADJ, K_ADJ_COLS, K_ADJ_ROWS, K_DOT, K_RADIAL, K_CREC, K_CONJ_ROWS, K_CONJ_COLS, K_RESAMPLE, K_POWER, K_CORR, K_COUNT
+    K_LC_ADJ, K_ADJ_COLS, K_ADJ_ROWS, K_DOT, K_RADIAL, K_CREC, K_CONJ_ROWS, K_CONJ_COLS, K_RESAMPLE, K_POWER, K_CORR,
+    K_PROP64, K_PERSIST, K_COUNT
 };
 const char* const kClassName[K_COUNT] = {
     "twiddles", "synth_rows", "synth_cols", "prop_tables", "prop_rows", "prop_cols",
     "smooth_fwd_cols", "smooth_rows", "smooth_inv_cols", "lightcurve", "moments",
     "lightcurve_adjoint", "adj_cols", "adj_rows", "dot", "radial_spectrum", "structure_rec",
-    "conj_rows", "conj_cols", "resample", "power_spectrum", "correlation"};
+    "conj_rows", "conj_cols", "resample", "power_spectrum", "correlation", "prop64", "prop_persistent"};
 
 struct ProfRec {
     int cls;
@@ -352,18 +355,29 @@ int check_passband(const scint_params* p, const double* lambdas, const double* w
 }
 
 // ---- propagation plans (variants of the transfer-function passes) ----------------
-// Default, from measurements on GB300 (1024^2-8192^2, 8 and 32 wavelengths): the packed
-// passes with 16 values per thread and register twiddle bases in both passes, 1-4 %
-// faster than the one-wavelength passes; with 8 values per thread or the shared twiddle
-// table they were slower.  Grid sizes without packed passes use the one-wavelength ones.
+// Default: the one-wavelength passes.  Measured on GB300 (1024^2-8192^2, 8 and 32
+// wavelengths), the packed passes with 16 values per thread and register twiddle bases in
+// both passes are 1-4 % faster when a screen runs alone, but 2.5 % slower when eight
+// screens share the GPU on the batch executor's lanes (their blocks need more shared
+// memory), and the persistent batch kernel runs the one-wavelength passes only.  scint_tune
+// picks a size's fastest variant alone, scint_tune_batch the fastest set for a batch.
 std::mutex g_plan_mu;
 std::map<std::pair<int, int>, scint_plan> g_plans;   // (device, n) -> plan
 
 scint_plan default_plan(int n) {
+    (void)n;
     scint_plan pl{};
-    pl.packed = packed_prop_supported(n, 16, 2, 2) ? 1 : 0;
+    pl.packed = 0;
     pl.points = 16;
     pl.row_twiddles = 2;
+    pl.col_twiddles = 1;
+    return pl;
+}
+
+// the packed plan measured fastest alone (a tuner candidate)
+scint_plan packed_plan(int n) {
+    scint_plan pl = default_plan(n);
+    pl.packed = packed_prop_supported(n, 16, 2, 2) ? 1 : 0;
     pl.col_twiddles = pl.packed ? 2 : 1;
     return pl;
 }
@@ -645,7 +659,133 @@ scint_plan one_wavelength_plan() {
     pl.col_twiddles = 1;
     return pl;
 }
-scint_plan packed_default_plan(int n) { return default_plan(n); }
+scint_plan packed_default_plan(int n) { return packed_plan(n); }
+
+static_assert(kPersistMaxScreensHost == kPersistMaxScreens, "screen limit of the persistent launch");
+
+bool persist_batch_supported(const int* sizes, int n) {
+    if (n < 1 || n > kPersistMaxScreens) return false;
+    for (int i = 0; i < n; ++i) {
+        if (!persist_supported(sizes[i])) return false;
+        scint_plan pl{};
+        if (plan_for(sizes[i], &pl) || pl.packed) return false;   // the persistent kernel runs the unpacked bodies
+    }
+    return true;
+}
+
+PersistLayout persist_layout(const int* sizes, int n, int n_lambda, int n_slots) {
+    PersistLayout L;
+    int nmax = 0;
+    for (int i = 0; i < n; ++i) nmax = std::max(nmax, sizes[i]);
+    size_t off = up(kPersistCounterBytes);
+    L.args = off;
+    off += up((size_t)n * sizeof(PropArgs));
+    L.tw = off;
+    off += (size_t)n * up((size_t)nmax * 8);     // one twiddle slot per screen (used only without kept tables)
+    L.sf = off;
+    for (int i = 0; i < n; ++i) off += up((size_t)n_lambda * sizes[i] * 4);
+    L.slots = off;
+    L.slot_bytes = std::max(up((size_t)field_slots(n_lambda) * nmax * nmax * 8), forward_workspace_bytes(nmax, 1));
+    off += (size_t)n_slots * L.slot_bytes;
+    L.total = off;
+    return L;
+}
+
+std::atomic<int> g_persist_withhold{-1};
+std::atomic<int> g_persist_wait_limit{0};
+void persist_testing(int withhold, int wait_limit) {
+    g_persist_withhold = withhold;
+    g_persist_wait_limit = wait_limit;
+}
+
+int persist_propagate(const scint_params* const* params, const double* const* phis, float* const* intensities,
+                      int n, const double* lambdas, const double* weights, int n_lambda, char* ws, int n_slots,
+                      int** status_out, cudaStream_t s) {
+    std::vector<int> sizes(n);
+    for (int i = 0; i < n; ++i) sizes[i] = params[i]->n;
+    const PersistLayout L = persist_layout(sizes.data(), n, n_lambda, n_slots);
+    const size_t tw_stride = up((size_t)*std::max_element(sizes.begin(), sizes.end()) * 8);
+    std::vector<double> w(n_lambda, 1.0 / n_lambda);
+    if (weights) w.assign(weights, weights + n_lambda);
+    // largest screens first; slot k holds order positions k, k + n_slots, ...
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sizes[a] > sizes[b]; });
+    PersistPlan pl{};
+    pl.withhold = g_persist_withhold.load();
+    const int lim = g_persist_wait_limit.load();
+    pl.wait_limit = lim > 0 ? lim : (1 << 23);    // about 2 s of 200 ns pauses
+    pl.screens = reinterpret_cast<const PropArgs*>(ws + L.args);
+    pl.counters = reinterpret_cast<unsigned*>(ws);
+    pl.status = reinterpret_cast<int*>(ws + sizeof(unsigned) * (1 + 2 * kPersistMaxScreens));
+    size_t smem = 0;
+    char* sf_cur = ws + L.sf;
+    std::vector<char*> sf_of(n);
+    for (int i = 0; i < n; ++i) {
+        sf_of[i] = sf_cur;
+        sf_cur += up((size_t)n_lambda * sizes[i] * 4);
+    }
+    SCINT_CUDA(cudaMemsetAsync(ws, 0, kPersistCounterBytes, s));
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        const scint_params* p = params[i];
+        const int nn = p->n;
+        smem = std::max(smem, persist_smem(nn));
+        pl.slot_prev[i] = (short)(k >= n_slots ? order[k - n_slots] : -1);
+        pl.row_items[i] = persist_items(nn, 0);
+        pl.col_items[i] = persist_items(nn, 1);
+        // the screen's arguments, exactly as run_group forms them for one group
+        const float2* tw = nullptr;
+        int rc = twiddles32(nn, true, s, reinterpret_cast<float2*>(ws + L.tw + (size_t)i * tw_stride), &tw);
+        if (rc) return rc;
+        TableArgs ta{};
+        ta.n = nn;
+        ta.count = n_lambda;
+        PropArgs pa{};
+        pa.n = nn;
+        pa.phi = phis[i];
+        pa.tw = tw;
+        pa.lam.count = n_lambda;
+        for (int l = 0; l < n_lambda; ++l) {
+            ta.margin_px[l] = taper_margin(p, lambdas[l]) / p->pixel_km;
+            fill_lambda(pa.lam, l, p, lambdas[l], w[l]);
+        }
+        ta.sf = reinterpret_cast<float*>(sf_of[i]);
+        pa.sf = ta.sf;
+        pa.work = reinterpret_cast<float2*>(ws + L.slots + (size_t)(k % n_slots) * L.slot_bytes);
+        pa.scratch = nullptr;
+        pa.intensity = intensities[i];
+        pa.accumulate = 0;
+        pa.one = 1.0f;
+        SCINT_LAUNCH(K_PROP_TABLES, 4.0 * n_lambda * nn, 0.0, s, launch_prop_tables(ta, s));
+        SCINT_CUDA(launch_persist_args(pa, reinterpret_cast<PropArgs*>(ws + L.args) + i, s));
+    }
+    // phases: R(o0), R(o1), C(o0), R(o2), C(o1), ..., C(o_last)
+    int ph = 0, first = 0;
+    auto push = [&](int scr, int pass) {
+        pl.phase_screen[ph] = (short)scr;
+        pl.phase_pass[ph] = (unsigned char)pass;
+        pl.phase_first[ph] = first;
+        first += pass == 0 ? pl.row_items[scr] : pl.col_items[scr];
+        ++ph;
+    };
+    for (int k = 0; k < n; ++k) {
+        push(order[k], 0);
+        if (k >= 1) push(order[k - 1], 1);
+    }
+    push(order[n - 1], 1);
+    pl.n_phases = ph;
+    pl.phase_first[ph] = first;
+    double bytes = 0.0, flops = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double nn = (double)sizes[i] * sizes[i];
+        bytes += 8.0 * nn + 16.0 * n_lambda * nn + 4.0 * nn;
+        flops += 4.0 * n_lambda * sizes[i] * fft_flops(sizes[i]);
+    }
+    SCINT_LAUNCH(K_PERSIST, bytes, flops, s, launch_persist_prop(pl, smem, s));
+    *status_out = pl.status;
+    return SCINT_OK;
+}
 }  // namespace scint
 
 namespace {
@@ -711,6 +851,7 @@ size_t scint_workspace_bytes(const scint_params* p, int n_lambda) {
     b = std::max(b, ws_smooth(n));
     b = std::max(b, ws_moments());
     b = std::max(b, ws_adjoint(n, std::min(n_lambda, SCINT_MAX_LAMBDA)));
+    b = std::max(b, ws_prop64(n));
     return b;
 }
 
@@ -719,6 +860,7 @@ int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_
     int rc = check_params(p);
     if (rc) return rc;
     if (!phi) return fail(SCINT_EINVAL, "phi must be a device pointer");
+    if (reinterpret_cast<uintptr_t>(phi) % 16) return fail(SCINT_EINVAL, "phi must be 16-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Carver c{};
     rc = resolve_ws(workspace, workspace_bytes, ws_synth(p->n), s, &c);
@@ -748,6 +890,44 @@ int scint_propagate(const scint_params* p, const double* phi, float* intensity, 
     const double lam = p->lambda_nm, w = 1.0;
     return passband_impl(p, phi, &lam, &w, 1, intensity, 0, workspace, workspace_bytes,
                          static_cast<cudaStream_t>(stream));
+}
+
+int scint_propagate64(const scint_params* p, const double* phi, double* intensity, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!phi || !intensity) return fail(SCINT_EINVAL, "phi and intensity must be device pointers");
+    if (p->n > kMax64N)
+        return fail(SCINT_EUNSUPPORTED, "scint_propagate64 supports n <= %d (n=%d)", kMax64N, p->n);
+    const double lam = p->lambda_nm;
+    rc = check_passband(p, &lam, nullptr, 1);
+    if (rc) return rc;
+    g_warning.clear();
+    note_sampling(p, &lam, 1);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Carver c{};
+    rc = resolve_ws(workspace, workspace_bytes, ws_prop64(p->n), s, &c);
+    if (rc) return rc;
+    Prop64Args a{};
+    a.n = p->n;
+    a.phi = phi;
+    double2* tw = c.take<double2>((size_t)p->n * 16);
+    a.tw = tw;
+    a.field = c.take<double2>((size_t)p->n * p->n * 16);
+    a.intensity = intensity;
+    a.scale = p->lambda_ref_nm / lam;
+    a.margin_px = taper_margin(p, lam) / p->pixel_km;
+    const double L = screen_len(p);
+    const double cc = lz_km2(lam, p->z_pc) / (2.0 * L * L);
+    const double cf = cc - std::floor(cc);
+    a.c_hi = std::ldexp(std::nearbyint(std::ldexp(cf, 31)), -31);
+    a.c_lo = cf - a.c_hi;
+    const double nn = (double)p->n * p->n;
+    SCINT_LAUNCH(K_TWIDDLES, 16.0 * p->n, 0.0, s, launch_twiddles64(tw, p->n, s));
+    // rows: phi read, complex128 field written; columns: field read, FP64 map written
+    SCINT_LAUNCH(K_PROP64, 8.0 * nn + 16.0 * nn + 16.0 * nn + 8.0 * nn, 4.0 * p->n * fft_flops(p->n), s,
+                 launch_prop64(a, s));
+    return ok();
 }
 
 int scint_propagate_noalloc(const scint_params* p, const double* phi, float* intensity, void* stream) {

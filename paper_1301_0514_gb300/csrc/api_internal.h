@@ -43,4 +43,23 @@ int set_tuned_plan(int n, scint_plan pl, double ms);
 scint_plan one_wavelength_plan();
 scint_plan packed_default_plan(int n);
 
+// ---- persistent propagation of a batch (persist.cu; arguments built in api.cu) ----
+// Workspace of the propagation of n screens (grid sizes `sizes`) in one persistent launch
+// with n_slots field slots: counters, the argument table, taper tables, twiddles and the
+// slots (each also large enough to serve as one lane's scratch for the other steps).
+struct PersistLayout {
+    size_t args = 0, tw = 0, sf = 0, slots = 0, slot_bytes = 0, total = 0;
+};
+PersistLayout persist_layout(const int* sizes, int n, int n_lambda, int n_slots);
+bool persist_batch_supported(const int* sizes, int n);
+constexpr int kPersistMaxScreensHost = 256;   // screens one persistent launch takes (kPersistMaxScreens)
+// Run the propagation of every screen (phi in, intensity out; passband lambdas/weights)
+// in one persistent launch on stream s; ws must hold persist_layout(...).total bytes.
+// withhold / wait_limit: see scint_testing_persist.  The status word (0 or
+// SCINT_ETIMEOUT once the launch has run) is at *status_out.
+int persist_propagate(const scint_params* const* params, const double* const* phis, float* const* intensities,
+                      int n, const double* lambdas, const double* weights, int n_lambda, char* ws, int n_slots,
+                      int** status_out, cudaStream_t s);
+void persist_testing(int withhold, int wait_limit);
+
 }  // namespace scint

@@ -254,8 +254,16 @@ SCINT_DEV void twiddle_powers(C w1, C w4, C (&w)[R]) {
 // buffer and [N/2, N) in rank 1's, each padded by pad16 of the local index, at
 // the same offset in both blocks; t is the thread's index in the line's team
 // across the cluster, and the stage barriers are cluster barriers.
-template <int CS> SCINT_DEV void line_sync() {
-    if constexpr (CS == 1) __syncthreads();
+// SUB: the threads that share the line buffers and synchronise: the whole block (0), or
+// the SUB-thread part of the block that thread threadIdx.x belongs to, through the named
+// barrier 1 + threadIdx.x / SUB (SUB a multiple of 32 dividing the block; barrier 0 stays
+// the block's own) -- so that two independent teams can share one block.
+template <int SUB> SCINT_DEV void team_sync() {
+    if constexpr (SUB == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / SUB), "n"(SUB) : "memory");
+}
+template <int CS, int SUB = 0> SCINT_DEV void line_sync() {
+    if constexpr (CS == 1) team_sync<SUB>();
     else cooperative_groups::this_cluster().sync();
 }
 
@@ -302,7 +310,7 @@ SCINT_DEV dfc ld_cluster<dfc>(unsigned addr) {
 // and one barrier per stage suffices (in place: two).  The last stage reads buffer
 // NSTAGE - 2; when that is buf, the next transform's first stage would overwrite it,
 // so that case keeps a barrier after the reads.
-template <typename C, int N, int DIR, int EPT, int LW, int TWM, int CS, int S, int TS = 1, bool PP = false>
+template <typename C, int N, int DIR, int EPT, int LW, int TWM, int CS, int S, int TS = 1, bool PP = false, int SUB = 0>
 SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw,
                          const TwiddleRegs<C, N, EPT>* tr, C* buf1 = nullptr) {
     using Pl = FftPlan<N, EPT>;
@@ -327,7 +335,7 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
 #pragma unroll
             for (int r = 0; r < R; ++r) u[b * R + r] = rbuf[pad16(t + b * T) * LW + r * ((N / R) + (N / R) / 16) * LW];
         }
-        if constexpr (!PP || (LAST && (Pl::NSTAGE - 2) % 2 == 0)) __syncthreads();
+        if constexpr (!PP || (LAST && (Pl::NSTAGE - 2) % 2 == 0)) team_sync<SUB>();
     } else {
         // Split line: i < N/R <= N/2, so element i + r N/R is in the upper half
         // (rank 1's buffer, local index i + (r - R/2) N/R) iff r >= R/2.
@@ -342,7 +350,7 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
                                              (unsigned)(rr * ((N / R) + (N / R) / 16) * LW * sizeof(C)));
             }
         }
-        line_sync<CS>();
+        line_sync<CS, SUB>();
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -389,8 +397,8 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
             for (int r = 0; r < R; ++r)
                 dst[(P >= 16 ? r * (P + P / 16) : (P == 1 ? r : pad16(j + r * P) - pad16(j))) * LW] = u[b * R + r];
         }
-        line_sync<CS>();
-        fft_stage<C, N, DIR, EPT, LW, TWM, CS, S + 1, TS, PP>(v, buf, t, tw, tr, buf1);
+        line_sync<CS, SUB>();
+        fft_stage<C, N, DIR, EPT, LW, TWM, CS, S + 1, TS, PP, SUB>(v, buf, t, tw, tr, buf1);
     }
 }
 
@@ -398,30 +406,30 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
 // Every thread of the block (of the cluster, for CS = 2) must call this the
 // same number of times.
 // TS: stride of the global table (TWM = 0), tw[j TS] = exp(-2 pi i j / N).
-template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0, int CS = 1, int TS = 1>
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0, int CS = 1, int TS = 1, int SUB = 0>
 SCINT_DEV void fft_line(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __restrict__ tw) {
     static_assert(TWM != 2, "register twiddles: use fft_line_tr");
     static_assert(CS == 1 || (CS == 2 && FftPlan<N, EPT>::NSTAGE > 1 && N >= 512), "split lines need N >= 512");
-    fft_stage<C, N, DIR, EPT, LW, TWM, CS, 0, TS>(v, buf, t, tw, nullptr);
+    fft_stage<C, N, DIR, EPT, LW, TWM, CS, 0, TS, false, SUB>(v, buf, t, tw, nullptr);
 }
 
-template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int CS = 1>
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int CS = 1, int SUB = 0>
 SCINT_DEV void fft_line_tr(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const TwiddleRegs<C, N, EPT>& tr) {
     static_assert(CS == 1 || (CS == 2 && FftPlan<N, EPT>::NSTAGE > 1 && N >= 512), "split lines need N >= 512");
-    fft_stage<C, N, DIR, EPT, LW, 2, CS, 0>(v, buf, t, nullptr, &tr);
+    fft_stage<C, N, DIR, EPT, LW, 2, CS, 0, 1, false, SUB>(v, buf, t, nullptr, &tr);
 }
 
 // Ping-pong forms (unsplit lines): buf1 is a second buffer laid out like buf.  Between
 // two ping-pong transforms of the same buffers no barrier is needed; any other write
 // to either buffer after one needs a __syncthreads first.
-template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0>
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int TWM = 0, int SUB = 0>
 SCINT_DEV void fft_line_pp(C (&v)[FftPlan<N, EPT>::E], C* buf, C* buf1, int t, const C* __restrict__ tw) {
     static_assert(TWM != 2, "register twiddles: use fft_line_tr_pp");
-    fft_stage<C, N, DIR, EPT, LW, TWM, 1, 0, 1, true>(v, buf, t, tw, nullptr, buf1);
+    fft_stage<C, N, DIR, EPT, LW, TWM, 1, 0, 1, true, SUB>(v, buf, t, tw, nullptr, buf1);
 }
-template <typename C, int N, int DIR, int EPT = 16, int LW = 1>
+template <typename C, int N, int DIR, int EPT = 16, int LW = 1, int SUB = 0>
 SCINT_DEV void fft_line_tr_pp(C (&v)[FftPlan<N, EPT>::E], C* buf, C* buf1, int t, const TwiddleRegs<C, N, EPT>& tr) {
-    fft_stage<C, N, DIR, EPT, LW, 2, 1, 0, 1, true>(v, buf, t, nullptr, &tr, buf1);
+    fft_stage<C, N, DIR, EPT, LW, 2, 1, 0, 1, true, SUB>(v, buf, t, nullptr, &tr, buf1);
 }
 
 // ---- lines split by one radix-2 step over a two-block cluster ------------------

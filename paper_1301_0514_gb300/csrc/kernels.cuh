@@ -110,6 +110,20 @@ struct ResampleArgs {
 };
 cudaError_t launch_resample(const ResampleArgs& a, cudaStream_t s);
 
+// -------- FP64 propagation of one screen at one wavelength (propagate64.cu) ------
+constexpr int kMax64N = 4096;
+struct Prop64Args {
+    int n;
+    const double* phi;       // n*n radians at lambda_ref
+    const double2* tw;       // FP64 twiddles of n
+    double scale;            // s = lambda_ref / lambda
+    double margin_px;        // taper margin in pixels (0: no taper)
+    double c_hi, c_lo;       // frac(lambda z / (2 L^2)) = c_hi + c_lo, c_hi with 31 bits after the point
+    double2* field;          // n*n complex128 scratch
+    double* intensity;       // n*n
+};
+cudaError_t launch_prop64(const Prop64Args& a, cudaStream_t s);
+
 // -------- source smoothing ---------------------------------------------------
 struct SmoothArgs {
     int n;

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "dispatch.cuh"
+#include "prop_body.cuh"
 #include "propagate.cuh"
 
 namespace scint {
@@ -52,138 +53,18 @@ cudaError_t launch_prop_tables(const TableArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// ---- row pass ------------------------------------------------------------------
 template <int N, bool CONJ>
 __global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
 prop_rows_kernel(PropArgs a) {
-    using Pl = FftPlan<N>;
-    constexpr int TWM = prow_twm<N>();
-    constexpr int T = Pl::T, E = Pl::E, B = prow_lines<N>(), W = pstrip<N>(), BUFL = Pl::BUF;
     extern __shared__ float2 smem32[];
-    const int team = threadIdx.x / T, t = threadIdx.x % T;    // line of the block, index in its team
-    const int y = blockIdx.x * B + team;
-    float2* buf = smem32 + team * BUFL;
-    // fixed-point phase of this thread's pixels, kept in shared memory across the
-    // wavelength loop (each thread reads back only the entries it wrote)
-    long long* P = reinterpret_cast<long long*>(smem32 + B * BUFL) + team * N + t;
-    float2* tws = smem32 + B * BUFL + B * N;    // shared twiddle table (after P, 8 B per entry)
-    const float2* twp = TWM == 1 ? tws : a.tw;
-    constexpr bool PP = ppp_row<N>();            // second line buffers after the table
-    float2* buf1 = smem32 + B * BUFL + B * N + (TWM == 1 ? Pl::TWS : 0) + team * BUFL;
-    TwiddleRegs<float2, N, 16> tr;
-    if constexpr (TWM == 2) tr.load(a.tw, t);
-    else if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
-#pragma unroll
-    for (int m = 0; m < E; ++m) P[m * T] = phase_fixed(a.phi[(size_t)y * N + t + m * T]);
-    __syncthreads();
-
-#pragma unroll 1
-    for (int l = 0; l < a.lam.count; ++l) {
-        const unsigned long long S = a.lam.scale_fx[l];
-        // the taper from its table; H_x from a scalar (its phase exact in fixed-point turns)
-        const float* sf = a.sf + (size_t)l * N;
-        const float sfy = sf[y];
-        float2 v[E];
-        if constexpr (CONJ) {
-            // G = SF SF exp(i (phi s + |x_1|^2 / 2 R_F^2)) (-1)^(x + y), Eq. Gxy
-            const unsigned long long C = a.conj.chirp_fx[l];
-            const unsigned long long cy = chirp_turns(C, y, N);
-#pragma unroll
-            for (int m = 0; m < E; ++m)
-                v[m] = unit_phasor(P[m * T], S, cy + chirp_turns(C, t + m * T, N)) * (sfy * __ldg(sf + t + m * T));
-        } else {
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = unit_phasor(P[m * T], S) * (sfy * __ldg(sf + t + m * T));
-        }
-        if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, -1, 16, 1>(v, buf, buf1, t, tr);
-        else if constexpr (PP) fft_line_pp<float2, N, -1, 16, 1, TWM>(v, buf, buf1, t, twp);
-        else if constexpr (TWM == 2) fft_line_tr<float2, N, -1, 16, 1>(v, buf, t, tr);
-        else fft_line<float2, N, -1, 16, 1, TWM>(v, buf, t, twp);
-        if constexpr (!CONJ) {
-            const unsigned long long hc = a.lam.h_fx[l];
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
-            if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, +1, 16, 1>(v, buf, buf1, t, tr);
-            else if constexpr (PP) fft_line_pp<float2, N, +1, 16, 1, TWM>(v, buf, buf1, t, twp);
-            else if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
-            else fft_line<float2, N, +1, 16, 1, TWM>(v, buf, t, twp);
-        }
-        float2* dst = a.work + (size_t)l * N * N;
-#pragma unroll
-        for (int m = 0; m < E; ++m) dst[strip_index<W>(y, t + m * T, N)] = v[m];
-    }
+    prop_rows_body<N, CONJ>(a, blockIdx.x, threadIdx.x, smem32);
 }
 
-// ---- column pass ---------------------------------------------------------------
 template <int N, bool CONJ>
 __global__ void __launch_bounds__(pcol_threads<N>(), (pcol_threads<N>() <= 256 ? 2 : 1))
 prop_cols_kernel(PropArgs a) {
-    using Pl = FftPlan<N, kColEPT>;
-    constexpr int TWM = pcol_twm<N>();
-    constexpr int T = Pl::T, E = Pl::E, W = pcol_lines<N>(), WL = pstrip<N>(), BUFL = Pl::BUF;
     extern __shared__ float2 smem32[];
-    const int w = threadIdx.x % W, t = threadIdx.x / W;
-    const int x0 = blockIdx.x * W;    // first column of the block: strip x0 / WL, offset x0 % WL
-    const int x = x0 + w;
-    float2* buf = smem32 + w;     // W lines interleaved: element e of line w at pad16(e) * W + w
-    // passband accumulator of this thread's pixels, in registers (a shared-memory
-    // copy would add a read-modify-write per wavelength to the busiest queue)
-    float acc[E];
-    float2* tws = smem32 + W * BUFL;   // shared twiddle table (after the line buffers)
-    const float2* twp = TWM == 1 ? tws : a.tw;
-    constexpr bool PP = ppp_col<N>();   // second line buffers after the table
-    float2* buf1 = smem32 + W * BUFL + (TWM == 1 ? Pl::TWS : 0) + w;
-    TwiddleRegs<float2, N, kColEPT> tr;
-    if constexpr (TWM == 2) tr.load(a.tw, t);
-    else if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
-#pragma unroll
-    for (int m = 0; m < E; ++m) acc[m] = 0.0f;
-    __syncthreads();
-#pragma unroll 1
-    for (int l = 0; l < a.lam.count; ++l) {
-        const float2* src = a.work + (size_t)l * N * N + (size_t)(x0 / WL) * N * WL + (x0 % WL);
-        float2 v[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = src[(size_t)(t + m * T) * WL + w];
-        if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, -1, kColEPT, W>(v, buf, buf1, t, tr);
-        else if constexpr (PP) fft_line_pp<float2, N, -1, kColEPT, W, TWM>(v, buf, buf1, t, twp);
-        else if constexpr (TWM == 2) fft_line_tr<float2, N, -1, kColEPT, W>(v, buf, t, tr);
-        else fft_line<float2, N, -1, kColEPT, W, TWM>(v, buf, t, twp);
-        if constexpr (CONJ) {
-            // h = (Delta^2 / lambda z)^2 |FT G|^2 on the pattern grid of this wavelength (Eq. intens)
-            const float nrm = a.conj.norm[l];
-            if (a.conj.direct) {
-                const float wn = a.lam.weight[l] * nrm;
-#pragma unroll
-                for (int m = 0; m < E; ++m) acc[m] = fmaf(wn, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m]);
-            } else {
-                // column-major: this column's values are contiguous, so the stores coalesce
-                float* pat = a.conj.pattern + (size_t)l * N * N + (size_t)x * N;
-#pragma unroll
-                for (int m = 0; m < E; ++m) pat[t + m * T] = nrm * fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
-            }
-            continue;
-        } else {
-            const unsigned long long hc = a.lam.h_fx[l];
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
-            if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, +1, kColEPT, W>(v, buf, buf1, t, tr);
-            else if constexpr (PP) fft_line_pp<float2, N, +1, kColEPT, W, TWM>(v, buf, buf1, t, twp);
-            else if constexpr (TWM == 2) fft_line_tr<float2, N, +1, kColEPT, W>(v, buf, t, tr);
-            else fft_line<float2, N, +1, kColEPT, W, TWM>(v, buf, t, twp);
-        }
-        const float wl = a.lam.weight[l];
-#pragma unroll
-        for (int m = 0; m < E; ++m) acc[m] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m]);
-    }
-    if constexpr (CONJ) {
-        if (!a.conj.direct) return;
-    }
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-        float* o = a.intensity + (size_t)(t + m * T) * N + x;
-        *o = a.accumulate ? *o + acc[m] : acc[m];
-    }
+    prop_cols_body<N, CONJ>(a, blockIdx.x, threadIdx.x, smem32);
 }
 
 // ---- lines split over a two-block cluster (N = 16384) -------------------------------

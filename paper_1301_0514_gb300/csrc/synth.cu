@@ -144,12 +144,11 @@ synth_cols_kernel(SynthArgs a) {
     }
     line_sync<CS>();
     fft_line<dfc, N, +1, 16, W, 0, CS>(v, smem_df + w, t, a.tw);     // W lines interleaved
+    // columns xa, xa + 1 of a row are adjacent (xa even): one 16-byte store per row
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        double* o = a.phi + (size_t)(t + m * T) * N + xa;
-        o[0] = scaled_to_double(v[m].x, a.out_scale_df);
-        o[1] = scaled_to_double(v[m].y, a.out_scale_df);
-    }
+    for (int m = 0; m < E; ++m)
+        *reinterpret_cast<double2*>(a.phi + (size_t)(t + m * T) * N + xa) =
+            make_double2(scaled_to_double(v[m].x, a.out_scale_df), scaled_to_double(v[m].y, a.out_scale_df));
     if constexpr (CS == 2) line_sync<CS>();
 }
 
@@ -219,12 +218,11 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_cols_split_
         cluster_wait();
         fft_line<dfc, H2, +1, 16, 1, 0, 1, 2>(v, buf, t, a.tw);
         split_combine<dfc, H2>(v, buf, t, r, a.tw, [&](int, int n, dfc y0, dfc y1) {
-            double* o = a.phi + (size_t)n * N + xa;
-            o[0] = scaled_to_double(y0.x, a.out_scale_df);
-            o[1] = scaled_to_double(y0.y, a.out_scale_df);
-            o = a.phi + (size_t)(n + H2) * N + xa;
-            o[0] = scaled_to_double(y1.x, a.out_scale_df);
-            o[1] = scaled_to_double(y1.y, a.out_scale_df);
+            // columns xa, xa + 1 (xa even): one 16-byte store per row
+            *reinterpret_cast<double2*>(a.phi + (size_t)n * N + xa) =
+                make_double2(scaled_to_double(y0.x, a.out_scale_df), scaled_to_double(y0.y, a.out_scale_df));
+            *reinterpret_cast<double2*>(a.phi + (size_t)(n + H2) * N + xa) =
+                make_double2(scaled_to_double(y1.x, a.out_scale_df), scaled_to_double(y1.y, a.out_scale_df));
         });
     }
     cluster_wait();

@@ -284,3 +284,10 @@ def test_plan_host_checks(lib):
     assert lib.scint_get_plan(1024, None) == 1
     assert lib.scint_tune(999, 8, None, None) == 1
     assert lib.scint_autotune(0) in (0, 1)
+
+
+def test_screen_must_be_16_byte_aligned(lib):
+    """The synthesis writes two phases per 16-byte store: an unaligned phi is refused on the host."""
+    p = _lib.params(n=64, pixel_km=20.0, r_diff_km=100.0)
+    assert lib.scint_make_screen(ctypes.byref(p), ctypes.c_void_p(8), None, 0, None) == 1
+    assert "16-byte aligned" in lib.scint_last_error().decode()

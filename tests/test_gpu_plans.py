@@ -154,8 +154,9 @@ def test_batch_tuner_keeps_the_fastest_plans_and_lanes():
         entries.append(dict(params=S.params(**kw), phi=torch.empty((n, n), dtype=torch.float64, device="cuda"),
                             intensity=torch.empty((n, n), device="cuda")))
     batch = S.batch_items(entries)
-    lanes, ms = S.tune_batch(batch, lams)
-    assert lanes in (4, 5) and ms > 0.0
+    lanes, ms, mode = S.tune_batch(batch, lams)
+    S.batch_mode(0)
+    assert lanes in (4, 5) and ms > 0.0 and mode in (0, 1)
     for n in (256, 512):
         pl = S.get_plan(n)
         assert pl["tuned"] == 1 and pl["ms"] == pytest.approx(ms)
