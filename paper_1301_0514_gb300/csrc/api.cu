@@ -602,8 +602,29 @@ int fiducial_zone(const scint_params* p, int* i0, int* i1) {
     return 1;
 }
 
+// rms phase (rad) that the FFT bins outside the square |mx|, |my| <= K carry: the
+// spectrum's variance outside the disk |q| <= K/L (a bound for the square's outside),
+// 2 pi int_{K/L}^inf S(q) q dq = 2 pi C R_diff^-beta (K/L)^(2 - beta) / (beta - 2).
+double outer_phase_rms(double r_diff, double beta, double L, int K) {
+    const double C = r_diff * r_diff / (2.0 * std::pow(2.0 * kPi, beta - 1.0) * f_beta(beta));
+    return std::sqrt(2.0 * kPi * C * std::pow(r_diff, -beta) * std::pow(K / L, 2.0 - beta) / (beta - 2.0));
+}
+
+// The FP64 square of a screen: the smallest K in {32, 64, 128, 256} whose outside
+// carries no more phase than the outside of K = 256 on the worst screen validated
+// against the oracle at full size (4096^2, 10 km pixels, R_diff = 30 km, Kolmogorov:
+// 2.6e-7 rad); 256 when none does.  The FP32 bins' phase error scales with that rms.
+int fp64_square(const scint_params* p) {
+    static const double target = outer_phase_rms(30.0, 11.0 / 3.0, 40960.0, 256);
+    const double L = screen_len(p);
+    for (int K = 32; K < 256; K *= 2)
+        if (outer_phase_rms(p->r_diff_km, p->beta, L, K) <= target) return K;
+    return 256;
+}
+
 SynthArgs synth_args(const scint_params* p) {
     SynthArgs a{};
+    a.low_k = fp64_square(p);
     const double L = screen_len(p);
     const double rd = p->r_diff_km, beta = p->beta;
     const double C = rd * rd / (2.0 * std::pow(2.0 * kPi, beta - 1.0) * f_beta(beta));

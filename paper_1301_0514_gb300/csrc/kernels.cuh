@@ -31,6 +31,7 @@ cudaError_t launch_twiddles64(double2* tw, int n, cudaStream_t s);
 // -------- synthesis (FP64) -------------------------------------------------
 struct SynthArgs {
     int n;
+    int low_k;           // bins with |mx|, |my| <= low_k are drawn in FP64, the others in FP32
     uint32_t screen_id, key0, key1;
     double amp;          // sigma(k) = amp * (mx^2 + my^2)^(-beta/4), includes 1/sqrt(2)
     double neg_beta_4;   // -beta/4

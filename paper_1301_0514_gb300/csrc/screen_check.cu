@@ -109,7 +109,7 @@ radial_kernel(SynthArgs a, int n_hist, unsigned long long* sums, unsigned long l
                 ++cnt;
             } else if (j < n_hist && m2 > 0) {
                 const u32x4 w = philox4x32_10(u32x4{(uint32_t)kx, (uint32_t)ky, a.screen_id, 0u}, a.key0, a.key1);
-                acc += low_bin(mx, my) ? to_fixed(power_low(a, w, m2), shift) : to_fixed(power_high(a, w, m2), shift);
+                acc += low_bin(a, mx, my) ? to_fixed(power_low(a, w, m2), shift) : to_fixed(power_high(a, w, m2), shift);
             }
         }
         if (cur >= 0 && cur < n_hist) {

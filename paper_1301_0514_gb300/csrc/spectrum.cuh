@@ -31,14 +31,13 @@ SCINT_DEV float neg_log_ua32(const u32x4& w) {
     return -logf(ua);
 }
 
-// Bins with |mx| <= kLowK and |my| <= kLowK carry almost all of the phase
+// Bins with |mx| <= K and |my| <= K (K = a.low_k) carry almost all of the phase
 // variance (S ~ q^-beta): their noise and amplitude are computed in FP64.  The
 // other bins have small amplitudes, so FP32 Box-Muller and pow give phase errors
-// of ~1e-7 of their (small) rms contribution, which falls as kLowK^((2 - beta)/2)
-// with the square's size.  At kLowK = 32 the screens with the largest phases (rms
-// 72 rad at 4096^2, R_diff = 30 km) were 2.4e-6 rad off the FP64 oracle; 256
-// keeps them well inside 1e-6 rad for 0.1-1 % of the bins.
-constexpr int kLowK = 256;
+// of ~1e-7 of their (small) rms contribution, which falls as K^((2 - beta)/2)
+// with the square's size.  The host picks K per screen (32 to 256) from that rms
+// (api.cu, fp64_square); with K = 32 everywhere the screens with the largest phases
+// (rms 72 rad at 4096^2, R_diff = 30 km) were 2.4e-6 rad off the FP64 oracle.
 
 // A bin's shaped value F[ky][kx] = sqrt(L^2 S(q)) (g_re + i g_im) / sqrt(2), in the
 // precision it is computed in: FP64 for the low bins (low = true, d), FP32 for the
@@ -91,7 +90,7 @@ SCINT_DEV BinValue spectrum_value(const SynthArgs& a, int kx, int ky) {
     v.d = make_double2(0.0, 0.0);
     v.f = make_float2(0.0f, 0.0f);
     if (m2 == 0) return v;
-    if (abs(mx) <= kLowK && abs(my) <= kLowK) {
+    if (abs(mx) <= a.low_k && abs(my) <= a.low_k) {
         v.d = shaped_low(w, amplitude_low(a, m2));
         return v;
     }
@@ -124,7 +123,7 @@ SCINT_DEV void spectrum_pair_df(const SynthArgs& a, int kx, int ky, dfc& f, dfc&
     const int m2 = mx * mx + my * my;
     if (m2 == 0) {
         f = g = dfc{dfl(0.0f, 0.0f), dfl(0.0f, 0.0f)};
-    } else if (abs(mx) <= kLowK && abs(my) <= kLowK) {
+    } else if (abs(mx) <= a.low_k && abs(my) <= a.low_k) {
         const double sig = amplitude_low(a, m2);
         const double2 d1 = shaped_low(w1, sig), d2 = shaped_low(w2, sig);
         f = dfc{dfl(d1.x), dfl(d1.y)};
@@ -140,8 +139,8 @@ SCINT_DEV void spectrum_pair_df(const SynthArgs& a, int kx, int ky, dfc& f, dfc&
 // |F[ky][kx]|^2 = sigma^2 (g_re^2 + g_im^2) / 2 = sigma^2 (-2 ln u_a) / 2 of a
 // bin with Philox words w and m2 = mx^2 + my^2 > 0 (the Box-Muller angle
 // cancels), in the precision spectrum_bin uses for it: FP64 for the low bins
-// (|mx|, |my| <= kLowK), FP32 for the others.
-SCINT_DEV bool low_bin(int mx, int my) { return abs(mx) <= kLowK && abs(my) <= kLowK; }
+// (|mx|, |my| <= a.low_k), FP32 for the others.
+SCINT_DEV bool low_bin(const SynthArgs& a, int mx, int my) { return abs(mx) <= a.low_k && abs(my) <= a.low_k; }
 SCINT_DEV double power_low(const SynthArgs& a, const u32x4& w, int m2) {
     const double sig = amplitude_low(a, m2);
     return sig * sig * (2.0 * neg_log_ua64(w));
