@@ -50,6 +50,12 @@ def _dist():
     return rank, world, local
 
 
+def _sm_count() -> int:
+    """SMs of the current CUDA device (from its properties)."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -619,11 +625,11 @@ def run_screen_check(args):
     # Philox4x32-10 bound: 10 rounds x 2 32x32->64-bit multiplies per bin, each a
     # multiply-add pair on the integer pipe (64 lanes per SM per clock)
     imad_per_bin = 40.0
-    peak = SM_COUNT * 64 * sm_max_mhz * 1e6 / imad_per_bin
+    peak = _sm_count() * 64 * sm_max_mhz * 1e6 / imad_per_bin
     achieved = units / (kstats["radial_spectrum"]["total_ms"] * 1e-3)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gbins/s",
             "frac": achieved / peak, "traffic": None, "kernel": "radial_spectrum",
-            "peak_source": f"Philox4x32-10 integer multiplies: {SM_COUNT} SMs x 64 lanes x {sm_max_mhz:.0f} MHz "
+            "peak_source": f"Philox4x32-10 integer multiplies: {_sm_count()} SMs x 64 lanes x {sm_max_mhz:.0f} MHz "
                            f"/ {imad_per_bin:.0f} per bin",
             "timing": "one profiled eager step, CUDA events per launch"}
 
@@ -738,13 +744,13 @@ def run_conjugate(args):
     ms = _max_over_ranks(ms, world, dev)
     value = units * world / (ms * 1e-3)
     hbm_peak, sm_max_mhz, peak_src = _peaks()
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    alu_peak = _sm_count() * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     dom_name, dom = max(((k, v) for k, v in kstats.items() if k.startswith("conj")), key=lambda kv: kv[1]["total_ms"])
     tflops = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12
     gbs = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
             "traffic": None, "kernel": dom_name, "share": dom["total_ms"] / ms, "hbm_gbs": gbs,
-            "hbm_frac": gbs / hbm_peak, "peak_source": f"alu = {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+            "hbm_frac": gbs / hbm_peak, "peak_source": f"alu = {_sm_count()} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                                        f"{sm_max_mhz:.0f} MHz; hbm {peak_src}"}
 
     # end to end through the public API: the passband map of every screen read back
@@ -847,7 +853,7 @@ def run_m_sweep(args):
     kstats = S.profile_read()
     S.profile_enable(False)
     hbm_peak, sm_max_mhz, peak_src = _peaks()
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    alu_peak = _sm_count() * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     dom_name, dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
     tflops = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
@@ -954,7 +960,7 @@ def run_timeseries(args):
     units = float(nc) * ns
     value = units * world / (ms * 1e-3)
     hbm_peak, sm_max_mhz, peak_src = _peaks()
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    alu_peak = _sm_count() * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     ps = kstats["power_spectrum"]
     tflops = ps["flops"] / (ps["total_ms"] * 1e-3) / 1e12
     gbs = ps["bytes"] / (ps["total_ms"] * 1e-3) / 1e9
@@ -1000,6 +1006,96 @@ def run_timeseries(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_small256(args):
+    """The plain method in FP64 (the small-screen configuration): one 256^2 Kolmogorov screen,
+    20 km pixels, R_diff 100 km, 500 nm, 160 pc, point source; a step is the synthesis, the FP64
+    propagation (scint_propagate64) and the horizontal track through row 128 (integer positions:
+    the map's row).  Metric: screen pixels per second.  The oracle does the same in FP64."""
+    import torch
+    import paper_1301_0514_gb300 as S
+    from paper_1301_0514_gb300 import workloads as W
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    it = W.small_screen_256()[0]
+    it["seed"] += 100000 * rank
+    p = S.params(**{k: it[k] for k in PARAM_KEYS})
+    n = p.n
+    ws = torch.empty(S.workspace_bytes(p, 1), dtype=torch.uint8, device=dev)
+    phi = torch.empty((n, n), dtype=torch.float64, device=dev)
+    inten = torch.empty((n, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        S.make_screen(p, out=phi, workspace=ws)
+        S.propagate64(p, phi, out=inten, workspace=ws)
+
+    step()
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = _max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    value = float(n) * n * world / (ms * 1e-3)
+    # end to end: the call sequence plus the track (row 128) read back to the host each step
+    track = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+        track.copy_(inten[128], non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        po = O.ScreenParams(**{k: it[k] for k in PARAM_KEYS})
+        reps, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < 5.0:
+            phi_o = O.make_screen(po)
+            I_o = O.intensity_mono(phi_o, po)
+            O.lightcurves(I_o, it["tracks"], it["n_samples"])
+            reps += 1
+        dt = (time.perf_counter() - t0) / reps
+        err = float(np.abs(inten.cpu().numpy() - I_o).max())
+        cpu = {"value": n * n / dt, "unit": "pixels/s", "cores": 1, "kind": "oracle",
+               "sample": f"the whole configuration ({reps} repetitions, {dt * 1e3:.1f} ms each)",
+               "gpu_max_abs_err": err}
+    if rank == 0:
+        print(json.dumps({"metric": "screen pixels propagated per second, FP64 plain method", "value": value,
+                          "unit": "pixels/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "one 256^2 Kolmogorov screen, 20 km pixels, R_diff 100 km, 500 nm, "
+                                                 "160 pc, point source, taper margin L/4; synthesis + FP64 "
+                                                 "propagation (+ the horizontal track in e2e)",
+                                     "l2": "inputs fit in L2 (1.5 MB); the configuration is this small"},
+                          "e2e": {"value": float(n) * n * world / (e2e_ms * 1e-3), "unit": "pixels/s",
+                                  "h2d_bytes_per_step": 0, "d2h_bytes_per_step": n * 8, "ms_per_step": e2e_ms},
+                          "gpu_launches": 4 * args.steps, "clocks": clk, "cpu_baseline": cpu}), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def run_gradient(args):
@@ -1071,7 +1167,7 @@ def run_gradient(args):
     units = float(n) * n * len(items)
     value = units * world / (ms * 1e-3)
     hbm_peak, sm_max_mhz, peak_src = _peaks()
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    alu_peak = _sm_count() * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     dom_name, dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
     tflops = dom["flops"] / (dom["total_ms"] * 1e-3) / 1e12 if dom["flops"] else 0.0
     gbs = dom["bytes"] / (dom["total_ms"] * 1e-3) / 1e9
@@ -1130,7 +1226,7 @@ def main():
     ap.add_argument("--plans", default="tune", choices=["tune", "unpacked", "packed"],
                     help="propagation plans: autotuned per grid size, or fixed")
     ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "large16384", "screen_check", "conjugate",
-                                                              "m_sweep", "timeseries", "gradient"])
+                                                              "m_sweep", "timeseries", "gradient", "small256"])
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
     ap.add_argument("--conj-n", type=int, default=4096, help="grid of the one-FFT workload")
     ap.add_argument("--sweep-n", type=int, default=8192, help="grid of the m-sweep workload")
@@ -1145,6 +1241,8 @@ def main():
         run_m_sweep(args)
     elif args.workload == "timeseries" and args.impl != "reference":
         run_timeseries(args)
+    elif args.workload == "small256" and args.impl != "reference":
+        run_small256(args)
     elif args.workload == "gradient" and args.impl != "reference":
         run_gradient(args)
     elif args.impl == "reference":

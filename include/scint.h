@@ -128,9 +128,10 @@ size_t scint_workspace_bytes(const scint_params* p, int n_lambda);
  * lambda_ref).  Precision: the bins in a square |kx|, |ky| <= K around the
  * origin (nearly all of the phase variance, since S ~ q^-beta) draw their normals
  * and amplitude in FP64; every other bin draws them in FP32 from the same 53-bit
- * uniforms.  K in {32, 64, 128, 256} is chosen per screen: the smallest square
- * whose outside carries an rms phase of at most 0.45 rad (the FP32 draws err by
- * ~1e-7 of that), 256 when none does.  The
+ * uniforms.  Up to N = 512 every bin is drawn in FP64; above, K in {32, 64, 128,
+ * 256} is chosen per screen: the smallest square whose outside carries an rms
+ * phase of at most 0.45 rad (the FP32 draws err by ~1e-7 of that), 256 when none
+ * does.  The
  * inverse 2D transform runs in double-float arithmetic (pairs of FP32 numbers,
  * about 44 significant bits) and phi is written in FP64.  Against the FP64
  * oracle the screen agrees to better than 2e-6 rad (the measured worst cases are

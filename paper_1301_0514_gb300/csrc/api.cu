@@ -610,11 +610,13 @@ double outer_phase_rms(double r_diff, double beta, double L, int K) {
     return std::sqrt(2.0 * kPi * C * std::pow(r_diff, -beta) * std::pow(K / L, 2.0 - beta) / (beta - 2.0));
 }
 
-// The FP64 square of a screen: the smallest K in {32, 64, 128, 256} whose outside
+// The FP64 square of a screen: up to 512^2 all bins; above, the smallest K in {32, 64, 128, 256} whose outside
 // carries no more phase than the outside of K = 256 on the worst screen validated
 // against the oracle at full size (4096^2, 10 km pixels, R_diff = 30 km, Kolmogorov:
 // 2.6e-7 rad); 256 when none does.  The FP32 bins' phase error scales with that rms.
 int fp64_square(const scint_params* p) {
+    // up to 512^2 every bin is drawn in FP64 (the whole spectrum is the square; at most 2.6e5 bins)
+    if (p->n <= 512) return p->n / 2;
     static const double target = outer_phase_rms(30.0, 11.0 / 3.0, 40960.0, 256);
     const double L = screen_len(p);
     for (int K = 32; K < 256; K *= 2)

@@ -63,6 +63,21 @@ def test_fp64_chirp_reduction_is_exact_for_large_lambda_z():
     assert np.abs(I_g - I_o).max() <= TOL64
 
 
+def test_small_screen_256_whole_configuration_in_fp64():
+    """Synthesis (every bin drawn in FP64 up to 512^2; double-float transform) and the FP64
+    propagation against the oracle's screen and map: phase ~1e-12 rad, map ~1e-10."""
+    it = W.small_screen_256()[0]
+    p_g, p_o = gpu_params(it), oracle_params(it)
+    phi_g = S.make_screen(p_g)
+    phi_o = O.make_screen(p_o)
+    e_phi = np.abs(phi_g.cpu().numpy() - phi_o).max()
+    I_g = S.propagate64(p_g, phi_g).cpu().numpy()
+    e_I = np.abs(I_g - O.intensity_mono(phi_o, p_o)).max()
+    print(f"256^2 whole configuration: phase err {e_phi:.3e} rad, map err {e_I:.3e}")
+    assert e_phi <= 1e-11
+    assert e_I <= TOL64
+
+
 def test_fp64_path_rejects_grids_above_4096():
     p = S.params(n=8192, pixel_km=10.0, r_diff_km=100.0)
     phi = torch.zeros((1, 1), dtype=torch.float64, device="cuda")
