@@ -122,6 +122,10 @@ SCINT_DEV void run_item(const PropArgs& a, int pass, int item, float2* smem) {
 __global__ void __launch_bounds__(kPersistThreads, 1) persist_prop_kernel(PersistPlan pl) {
     extern __shared__ float2 psmem[];
     __shared__ int s_item, s_ok;
+    // the current screen's arguments, staged in shared memory: the bodies read them many times
+    // per wavelength, and from global memory those reads were the launch's main latency stall
+    __shared__ PropArgs sa;
+    int staged = -1;
     unsigned* next = pl.counters;
     unsigned* rows_done = pl.counters + 1;
     unsigned* cols_done = pl.counters + 1 + kPersistMaxScreens;
@@ -155,7 +159,14 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_prop_kernel(Persis
         }
         __syncthreads();
         if (!s_ok) return;
-        const PropArgs& a = pl.screens[s];
+        if (s != staged) {    // uniform across the block
+            const int* src = reinterpret_cast<const int*>(pl.screens + s);
+            int* dst = reinterpret_cast<int*>(&sa);
+            for (int i = threadIdx.x; i < (int)(sizeof(PropArgs) / sizeof(int)); i += kPersistThreads) dst[i] = src[i];
+            __syncthreads();
+            staged = s;
+        }
+        const PropArgs& a = sa;
         switch (a.n) {
             case 256: run_item<256>(a, pass, item, psmem); break;
             case 512: run_item<512>(a, pass, item, psmem); break;
