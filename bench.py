@@ -65,17 +65,18 @@ def _peaks():
         return 6800.0, 2070.0, "fallback"
 
 
-def _workload(name: str, rank: int):
+def _workload(name: str, rank: int, screens: int = 1):
     from paper_1301_0514_gb300 import workloads as W
     if name == "batched":
         items = W.batched_polychromatic()
         desc = ("batched: 48 screens (16 each of 1024^2, 2048^2, 4096^2, 10 km pixels, R_diff U[30,300] km) "
                 "x 32 wavelengths 400-700 nm, disk sources U[0.1,2] R_ref, 8 tracks/screen")
     elif name == "profile":
-        items = [x for x in W.batched_polychromatic() if x["n"] == 4096][:1]
-        items[0]["lambdas_nm"] = items[0]["lambdas_nm"][::4]
-        desc = ("profiling case: one 4096^2 screen of the batched workload x 8 wavelengths "
-                "(~1.2 GB on the device, above the L2 size)")
+        items = [x for x in W.batched_polychromatic() if x["n"] == 4096][:screens]
+        for it in items:
+            it["lambdas_nm"] = it["lambdas_nm"][::4]
+        desc = (f"profiling case: {len(items)} 4096^2 screen(s) of the batched workload x 8 wavelengths "
+                f"(~{1.2 * len(items):.1f} GB on the device, above the L2 size)")
     elif name == "large16384":
         items = [W.large_screen_16384(beta=11.0 / 3.0, disk=True)]
         desc = ("one 16384^2 screen (lines split over two-block clusters), 5 km pixels, R_diff 100 km, "
@@ -329,7 +330,7 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    items, desc = _workload(args.workload, rank)
+    items, desc = _workload(args.workload, rank, args.profile_screens)
     P = [S.params(**{k: it[k] for k in PARAM_KEYS}) for it in items]
     sizes = sorted({p.n for p in P})
     lams, wts = items[0]["lambdas_nm"], items[0]["weights"]
@@ -1227,6 +1228,7 @@ def main():
                     help="propagation plans: autotuned per grid size, or fixed")
     ap.add_argument("--workload", default="batched", choices=["batched", "single4096", "profile", "large16384", "screen_check", "conjugate",
                                                               "m_sweep", "timeseries", "gradient", "small256"])
+    ap.add_argument("--profile-screens", type=int, default=1, help="4096^2 screens of the profile workload (1..16)")
     ap.add_argument("--check-n", type=int, default=14000, help="grid of the screen-check workload")
     ap.add_argument("--conj-n", type=int, default=4096, help="grid of the one-FFT workload")
     ap.add_argument("--sweep-n", type=int, default=8192, help="grid of the m-sweep workload")
