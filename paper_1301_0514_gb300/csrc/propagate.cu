@@ -53,8 +53,13 @@ cudaError_t launch_prop_tables(const TableArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Resident row blocks per SM the register budget is set for (build-time choice, 2 by default;
+// 3 caps the pass at 80 registers).
+#ifndef SCINT_ROW_MIN_BLOCKS
+#define SCINT_ROW_MIN_BLOCKS 2
+#endif
 template <int N, bool CONJ>
-__global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? 2 : 1))
+__global__ void __launch_bounds__(prow_threads<N>(), (prow_threads<N>() <= 256 ? SCINT_ROW_MIN_BLOCKS : 1))
 prop_rows_kernel(PropArgs a) {
     extern __shared__ float2 smem32[];
     prop_rows_body<N, CONJ>(a, blockIdx.x, threadIdx.x, smem32);
