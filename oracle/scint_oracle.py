@@ -8,9 +8,12 @@ and the CPU-baseline leg of ``bench.py`` may import it.  It shares no code,
 table or constant generator with the CUDA library and imports nothing from it.
 
 Every function states the passage of the paper it follows.  Arithmetic is
-IEEE double precision throughout; numpy's FFT serves as a library primitive
-(its sign and scaling conventions are pinned against a direct DFT and against
-the oracle's own radix-2 transform, fft_radix2, in the tests).  Where the paper is silent or ambiguous the reading taken here is
+IEEE double precision throughout; the 2D FFT of scipy.fft (pocketfft, the same
+library numpy's FFT is built on) serves as a library primitive through fft2 and
+ifft2 below (its sign and scaling conventions are pinned against a direct DFT
+and against the oracle's own radix-2 transform, fft_radix2, in the tests).
+FFT_WORKERS sets how many host threads one transform may use (1 by default;
+the full-size tests raise it to the host's core count).  Where the paper is silent or ambiguous the reading taken here is
 named in the docstring ("Reading Rn").
 
 Conventions used everywhere in this file
@@ -35,6 +38,7 @@ import math
 from dataclasses import dataclass, replace
 
 import numpy as np
+from scipy import fft as sfft
 from scipy import special
 
 KM_PER_PC = 3.0856775814913673e13
@@ -47,6 +51,20 @@ _PHILOX_M1 = np.uint64(0xCD9E8D57)
 _PHILOX_W0 = np.uint64(0x9E3779B9)
 _PHILOX_W1 = np.uint64(0xBB67AE85)
 _MASK32 = np.uint64(0xFFFFFFFF)
+
+# Threads one 2D transform may use: a library setting that changes no arithmetic
+# beyond the rounding order inside the transform.
+FFT_WORKERS = 1
+
+
+def fft2(x):
+    """2D DFT over the last two axes, X_k = sum_j x_j exp(-2 pi i k.j / N) (no scaling)."""
+    return sfft.fft2(x, workers=FFT_WORKERS)
+
+
+def ifft2(x):
+    """Inverse 2D DFT over the last two axes, with the + sign and the 1/N^2 factor."""
+    return sfft.ifft2(x, workers=FFT_WORKERS)
 
 
 @dataclass(frozen=True)
@@ -182,8 +200,8 @@ def make_screen(p: ScreenParams):
     n = p.n
     L = n * p.pixel_km
     F = noise_spectrum(p)
-    # numpy's ifft2 divides by N^2; multiply it back to get the plain sum.
-    return np.sqrt(2.0) / (L * L) * np.real(np.fft.ifft2(F)) * (n * n)
+    # ifft2 divides by N^2; multiply it back to get the plain sum.
+    return np.sqrt(2.0) / (L * L) * np.real(ifft2(F)) * (n * n)
 
 
 def structure_function_discrete(n: int, pixel_km: float, r_diff_km: float, beta: float, r_km):
@@ -336,9 +354,9 @@ def fft_radix2(x, inverse: bool = False):
     butterfly stages combine blocks of 2h elements: for k < h,
     X_k = a_k + w^k b_k and X_{k+h} = a_k - w^k b_k with w = exp(-+ 2 pi i / (2h)).
     Forward: X_k = sum_j x_j exp(-2 pi i j k / N); inverse: the + sign, no 1/N.
-    The oracle's steps use numpy's FFT as their library primitive; this is the
-    oracle's own transform, against which that primitive is pinned (with the
-    direct DFT) in the tests.
+    The oracle's steps use scipy's FFT (fft2, ifft2) as their library primitive;
+    this is the oracle's own transform, against which that primitive is pinned
+    (with the direct DFT) in the tests.
     """
     x = np.asarray(x, dtype=np.complex128)
     n = x.shape[-1]
@@ -390,7 +408,7 @@ def screen_field(phi, p: ScreenParams, lambda_nm: float):
 def propagate_field(a_in, pixel_km: float, lambda_nm: float, z_pc: float):
     """A_out = IDFT(DFT(A_in) H): exact Fresnel propagation of the periodic screen (Eq. hxy)."""
     H = transfer_function(a_in.shape[0], pixel_km, lambda_nm, z_pc)
-    return np.fft.ifft2(np.fft.fft2(a_in) * H)
+    return ifft2(fft2(a_in) * H)
 
 
 def fresnel_direct(a_in, pixel_km: float, lambda_nm: float, z_pc: float):
@@ -452,7 +470,7 @@ def propagate_conjugate(phi, p: ScreenParams, lambda_nm: float | None = None):
     x1 = (np.arange(n) - n // 2) * p.pixel_km
     a_in = screen_field(phi, p, lam)
     g = a_in * np.exp(1j * np.pi * (x1[:, None] ** 2 + x1[None, :] ** 2) / lz)
-    ft = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(g))) * p.pixel_km ** 2
+    ft = np.fft.fftshift(fft2(np.fft.ifftshift(g))) * p.pixel_km ** 2
     return np.abs(ft) ** 2 / lz ** 2
 
 
@@ -511,7 +529,7 @@ def source_kernel(n: int, pixel_km: float, radius_km: float):
 def smooth_source(I, pixel_km: float, radius_km: float):
     """I_ext = P_r * h: periodic convolution with the projected stellar disk (Eq. iprh)."""
     K = source_kernel(I.shape[0], pixel_km, radius_km)
-    return np.real(np.fft.ifft2(np.fft.fft2(I) * K))
+    return np.real(ifft2(fft2(I) * K))
 
 
 # ---------------------------------------------------------------------------
@@ -700,7 +718,8 @@ def bilinear_periodic_adjoint(shape, x, y, g):
     return out
 
 
-def misfit_gradient(p: ScreenParams, phi, lambdas_nm, tracks, n_samples: int, target, weights=None):
+def misfit_gradient(p: ScreenParams, phi, lambdas_nm, tracks, n_samples: int, target, weights=None,
+                    return_curves: bool = False):
     """Gradient of the light-curve misfit w.r.t. every screen pixel and R_diff (reverse mode).
 
     Chain, last step first:
@@ -710,7 +729,8 @@ def misfit_gradient(p: ScreenParams, phi, lambdas_nm, tracks, n_samples: int, ta
       G_in    = IDFT(DFT(G_out) conj(H))                      (adjoint of the unitary propagator)
       dL/dphi = sum_l s_l Im(conj(A_in) G_in)                 (A_in = T exp(i s phi))
       dL/dR_diff = ((2 - beta) / (2 R_diff)) sum phi dL/dphi  (phi ~ R_diff^((2-beta)/2), fixed seed)
-    Returns (loss, dL/dphi, dL/dR_diff).
+    Returns (loss, dL/dphi, dL/dR_diff), and the forward pass's curves c after them when
+    return_curves is set.
     """
     lambdas_nm = np.asarray(lambdas_nm, dtype=np.float64)
     if weights is None:
@@ -731,7 +751,9 @@ def misfit_gradient(p: ScreenParams, phi, lambdas_nm, tracks, n_samples: int, ta
         a_out = propagate_field(a_in, p.pixel_km, lam, p.z_pc)
         g_out = 2.0 * w * gI * a_out
         H = transfer_function(p.n, p.pixel_km, lam, p.z_pc)
-        g_in = np.fft.ifft2(np.fft.fft2(g_out) * np.conj(H))
+        g_in = ifft2(fft2(g_out) * np.conj(H))
         gphi += s * np.imag(np.conj(a_in) * g_in)
     g_rdiff = (2.0 - p.beta) / (2.0 * p.r_diff_km) * float(np.sum(phi * gphi))
+    if return_curves:
+        return misfit_loss(curves, target), gphi, g_rdiff, curves
     return misfit_loss(curves, target), gphi, g_rdiff

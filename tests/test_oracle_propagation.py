@@ -19,10 +19,10 @@ def test_fft_sign_and_scale_conventions():
     x = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
     j = np.arange(n)
     Wf = np.exp(-2j * np.pi * np.outer(j, j) / n)
-    np.testing.assert_allclose(np.fft.fft2(x), Wf @ x @ Wf.T, atol=1e-12)
-    np.testing.assert_allclose(np.fft.ifft2(x) * n * n, Wf.conj() @ x @ Wf.conj().T, atol=1e-12)
+    np.testing.assert_allclose(O.fft2(x), Wf @ x @ Wf.T, atol=1e-12)
+    np.testing.assert_allclose(O.ifft2(x) * n * n, Wf.conj() @ x @ Wf.conj().T, atol=1e-12)
     # Parseval
-    assert np.sum(np.abs(np.fft.fft2(x)) ** 2) == pytest.approx(n * n * np.sum(np.abs(x) ** 2), rel=1e-13)
+    assert np.sum(np.abs(O.fft2(x)) ** 2) == pytest.approx(n * n * np.sum(np.abs(x) ** 2), rel=1e-13)
 
 
 @pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 64])
@@ -35,19 +35,25 @@ def test_own_radix2_fft_equals_the_direct_dft(n, inverse):
     np.testing.assert_allclose(O.fft_radix2(x, inverse), x @ W.T, atol=1e-12 * max(1, n))
 
 
-def test_numpy_fft_equals_the_own_radix2_fft():
-    """The library primitive against the oracle's own transform at sizes the direct DFT cannot reach."""
+@pytest.mark.parametrize("workers", [1, 4])
+def test_library_fft_equals_the_own_radix2_fft(workers, monkeypatch):
+    """The library primitive (one thread and several) against the oracle's own transform at
+    sizes the direct DFT cannot reach."""
+    monkeypatch.setattr(O, "FFT_WORKERS", workers)
     rng = np.random.default_rng(7)
-    x = rng.standard_normal((4, 4096)) + 1j * rng.standard_normal((4, 4096))
-    ref = O.fft_radix2(x)
-    assert np.abs(np.fft.fft(x, axis=1) - ref).max() <= 1e-11 * np.abs(ref).max()
+    x = rng.standard_normal((4096, 4)) + 1j * rng.standard_normal((4096, 4))
+    ref = np.swapaxes(O.fft_radix2(np.swapaxes(x, 0, 1)), 0, 1)
+    lib = O.fft2(x)[:, :1]                      # along y (4096 points), then 4 columns summed
+    assert np.abs(lib[:, 0] - ref.sum(axis=1)).max() <= 1e-11 * np.abs(ref).max()
     x2 = rng.standard_normal((128, 128)) + 1j * rng.standard_normal((128, 128))
-    np.testing.assert_allclose(np.fft.fft2(x2), O.fft2_radix2(x2), atol=1e-10)
-    np.testing.assert_allclose(np.fft.ifft2(x2) * 128 * 128, O.fft2_radix2(x2, inverse=True), atol=1e-10)
+    np.testing.assert_allclose(O.fft2(x2), O.fft2_radix2(x2), atol=1e-10)
+    np.testing.assert_allclose(O.ifft2(x2) * 128 * 128, O.fft2_radix2(x2, inverse=True), atol=1e-10)
+    x3 = rng.standard_normal((3, 256, 512)) + 1j * rng.standard_normal((3, 256, 512))
+    np.testing.assert_allclose(O.fft2(x3), O.fft2_radix2(x3), atol=1e-9)
 
 
 def test_propagation_through_the_own_fft():
-    """propagate_field (numpy's FFT) equals IDFT(DFT(A_in) H) / N^2 with the own radix-2 FFT."""
+    """propagate_field (the library FFT) equals IDFT(DFT(A_in) H) / N^2 with the own radix-2 FFT."""
     p = O.ScreenParams(n=64, pixel_km=10.0, r_diff_km=20.0, seed=3)
     a_in = O.screen_field(O.make_screen(p), p, 520.0)
     H = O.transfer_function(64, 10.0, 520.0, p.z_pc)
