@@ -199,7 +199,10 @@ def make_screen(p: ScreenParams):
     """
     n = p.n
     L = n * p.pixel_km
-    F = noise_spectrum(p)
+    # the spectrum bin by bin, drawn a few rows at a time (each bin's draw depends on
+    # its own counter only, so the rows can be taken in any grouping)
+    step = max(1, (1 << 16) // n)
+    F = np.concatenate([noise_spectrum(p, rows=np.arange(r, min(r + step, n))) for r in range(0, n, step)])
     # ifft2 divides by N^2; multiply it back to get the plain sum.
     return np.sqrt(2.0) / (L * L) * np.real(ifft2(F)) * (n * n)
 
@@ -387,11 +390,16 @@ def fft2_radix2(x, inverse: bool = False):
 
 
 def transfer_function(n: int, pixel_km: float, lambda_nm: float, z_pc: float):
-    """Fresnel transfer function H(k) = exp(-i pi lambda z (k_x^2 + k_y^2)) (Reading R6)."""
+    """Fresnel transfer function H(k) = exp(-i pi lambda z (k_x^2 + k_y^2)) (Reading R6).
+
+    The exponential of the sum is the product h(k_y) h(k_x) of the 1D factors
+    h(k) = exp(-i pi lambda z k^2) = cos(pi lambda z k^2) - i sin(pi lambda z k^2).
+    """
     k = fft_freqs(n, pixel_km)
     lz = lambda_nm * KM_PER_NM * z_pc * KM_PER_PC
-    K2 = k[:, None] ** 2 + k[None, :] ** 2
-    return np.exp(-1j * np.pi * lz * K2)
+    theta = np.pi * lz * k ** 2
+    h = np.cos(theta) - 1j * np.sin(theta)
+    return h[:, None] * h[None, :]
 
 
 def screen_field(phi, p: ScreenParams, lambda_nm: float):
@@ -402,7 +410,8 @@ def screen_field(phi, p: ScreenParams, lambda_nm: float):
     """
     s = p.lambda_ref_nm / lambda_nm
     sf = taper_1d(p.n, p.pixel_km, taper_margin_km(p, lambda_nm))
-    return (sf[:, None] * sf[None, :]) * np.exp(1j * (phi * s))
+    t = phi * s
+    return (sf[:, None] * sf[None, :]) * (np.cos(t) + 1j * np.sin(t))
 
 
 def propagate_field(a_in, pixel_km: float, lambda_nm: float, z_pc: float):
