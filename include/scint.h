@@ -133,11 +133,14 @@ size_t scint_workspace_bytes(const scint_params* p, int n_lambda);
  * phase of at most 0.45 rad (the FP32 draws err by ~1e-7 of that), 256 when none
  * does.  The
  * inverse 2D transform runs in double-float arithmetic (pairs of FP32 numbers,
- * about 44 significant bits) and phi is written in FP64.  Against the FP64
+ * about 44 significant bits), except the x transforms of the spectral rows with
+ * |ky| > K (FP32 bins only, a small share of the phase), which run in FP32; phi
+ * is written in FP64.  Against the FP64
  * oracle the screen agrees to better than 2e-6 rad (the measured worst cases are
  * stated with the tests of the full-size workloads).
  *   phi   device, N*N doubles, written; 16-byte aligned (SCINT_EINVAL otherwise).
- * Needs workspace (16 N^2 bytes).
+ * Needs workspace (about 8 N^2 bytes: (N/2 + 1) N double-float values and the
+ * twiddle tables).
  */
 int scint_make_screen(const scint_params* p, double* phi,
                       void* workspace, size_t workspace_bytes, void* stream);

@@ -41,6 +41,7 @@ struct SynthArgs {
     double out_scale;    // sqrt(2) / L^2
     dfl out_scale_df;    // the same as a double-float
     const dfc* tw;       // double-float twiddles for n
+    const float2* tw32;  // FP32 twiddles for n (the transforms of rows outside the FP64 square)
     dfc* work;           // (n/2 + 1) x n double-float complex, row-major: rows ky = 0..n/2 after the x transform
     double* phi;         // n*n, row-major
 };

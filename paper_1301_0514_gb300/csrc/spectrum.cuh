@@ -136,6 +136,17 @@ SCINT_DEV void spectrum_pair_df(const SynthArgs& a, int kx, int ky, dfc& f, dfc&
     }
 }
 
+// F at (kx, ky) and at the mirror bin in FP32, for bins outside the FP64 square
+// (|mx| > low_k or |my| > low_k): the values spectrum_pair_df gives them, lo = 0.
+SCINT_DEV void spectrum_pair_high(const SynthArgs& a, int kx, int ky, float2& f, float2& g) {
+    const int n = a.n;
+    const u32x4 w1 = bin_words(a, kx, ky), w2 = bin_words(a, (n - kx) & (n - 1), (n - ky) & (n - 1));
+    const int mx = signed_freq(kx, n), my = signed_freq(ky, n);
+    const float sig = amplitude_high(a, mx * mx + my * my);
+    f = shaped_high(w1, sig);
+    g = shaped_high(w2, sig);
+}
+
 // |F[ky][kx]|^2 = sigma^2 (g_re^2 + g_im^2) / 2 = sigma^2 (-2 ln u_a) / 2 of a
 // bin with Philox words w and m2 = mx^2 + my^2 > 0 (the Box-Muller angle
 // cancels), in the precision spectrum_bin uses for it: FP64 for the low bins

@@ -86,6 +86,39 @@ SCINT_DEV dfc hermitian_bin(const SynthArgs& a, int kx, int ky) {
     return dfc{half(f.x + g.x), half(f.y - g.y)};
 }
 
+// Rows outside the FP64 square (|my| > low_k) hold only bins drawn in FP32, whose
+// phase contribution is small (an rms below ~0.5 rad for every screen, by the choice
+// of low_k), so their x transform runs in FP32: its rounding is ~1e-7 of that small
+// contribution.  The rows inside the square carry nearly all of the phase variance and
+// keep the double-float transform; the column pass, where every row's contribution
+// meets, stays in double-float.  Outputs go to the same double-float rows (lo = 0).
+SCINT_DEV float2 hermitian_bin32(const SynthArgs& a, int kx, int ky) {
+    float2 f, g;
+    spectrum_pair_high(a, kx, ky, f, g);
+    return make_float2(0.5f * (f.x + g.x), 0.5f * (f.y - g.y));
+}
+SCINT_DEV dfc widen(float2 v) { return dfc{dfl(v.x, 0.0f), dfl(v.y, 0.0f)}; }
+
+template <int N>
+SCINT_DEV void synth_row32(const SynthArgs& a, int ky, bool live, int t, float2* buf) {
+    using Pl = FftPlan<N>;
+    constexpr int T = Pl::T, E = Pl::E;
+    float2 v[E];
+    // drawn in a loop that is not unrolled and staged in the line buffer (as in the rows below)
+#pragma unroll 1
+    for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = live ? hermitian_bin32(a, t + m * T, ky) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = buf[pad16(t + m * T)];
+    TwiddleRegs<float2, N, 16> tr;
+    tr.load(a.tw32, t);
+    __syncthreads();
+    fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
+    if (live) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) a.work[(size_t)ky * N + t + m * T] = widen(v[m]);
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(synth_threads<N>())
 synth_rows_kernel(SynthArgs a) {
@@ -97,6 +130,13 @@ synth_rows_kernel(SynthArgs a) {
     const int t = synth_rank<CS>() * TL + threadIdx.x % TL;
     const int ky = (blockIdx.x / CS) * B + team;
     const bool live = ky <= N / 2;                 // rows above N/2 are the conjugates of rows below
+    if constexpr (CS == 1) {
+        // every row of the block outside the square (the choice is uniform over the block)
+        if ((blockIdx.x / CS) * B > a.low_k) {
+            synth_row32<N>(a, ky, live, t, reinterpret_cast<float2*>(smem_df) + team * Pl::BUF);
+            return;
+        }
+    }
     dfc v[E];
     dfc* buf = smem_df + team * (Pl::BUF / CS);
     if constexpr (CS == 1) {
@@ -173,8 +213,26 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_rows_split_
     cluster_arrive();
 #pragma unroll 1
     for (int ky = blockIdx.x / 2; ky <= N / 2; ky += gridDim.x / 2) {
-        dfc v[E];
         cluster_wait();
+        dfc* row = a.work + (size_t)ky * N;
+        if (ky > a.low_k) {    // outside the FP64 square: FP32 transform (see synth_row32)
+            float2* b32 = reinterpret_cast<float2*>(buf);
+            float2 u[E];
+#pragma unroll 1
+            for (int m = 0; m < E; ++m) b32[pad16(t + m * T)] = hermitian_bin32(a, 2 * (t + m * T) + r, ky);
+#pragma unroll
+            for (int m = 0; m < E; ++m) u[m] = b32[pad16(t + m * T)];
+            TwiddleRegs<float2, H2, 16> tr;
+            tr.load(a.tw32, t, 2);    // the N-point table at even indices
+            __syncthreads();
+            fft_line_tr<float2, H2, +1, 16, 1>(u, b32, t, tr);
+            split_combine<float2, H2>(u, b32, t, r, a.tw32, [&](int, int n, float2 y0, float2 y1) {
+                row[n] = widen(y0);
+                row[n + H2] = widen(y1);
+            });
+            continue;
+        }
+        dfc v[E];
         // bins drawn in a loop that is not unrolled and staged in the line buffer (see synth_rows_kernel)
 #pragma unroll 1
         for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = hermitian_bin(a, 2 * (t + m * T) + r, ky);
@@ -182,7 +240,6 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_rows_split_
         for (int m = 0; m < E; ++m) v[m] = buf[pad16(t + m * T)];
         __syncthreads();
         fft_line<dfc, H2, +1, 16, 1, 0, 1, 2>(v, buf, t, a.tw);
-        dfc* row = a.work + (size_t)ky * N;
         split_combine<dfc, H2>(v, buf, t, r, a.tw, [&](int, int n, dfc y0, dfc y1) {
             row[n] = y0;
             row[n + H2] = y1;
