@@ -123,7 +123,10 @@ constexpr size_t kAlign = 256;
 constexpr int kRdiffRecIterations = 64;   // bisection steps for R_diff^rec (resolution L 2^-65)
 size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
-size_t ws_synth(int n) { return up((size_t)n * 16) + up((size_t)n * 8) + up((size_t)(n / 2 + 1) * n * 16); }
+size_t ws_synth(int n) {
+    return up((size_t)n * 16) + up((size_t)n * 8) + up((size_t)(n / 2) * (n + 4) * 16) +
+           (n >= kSplitN ? up((size_t)n * n * 8) : 0);
+}
 // twiddles, the taper table per wavelength, one field per wavelength of the group, and at
 // n = 16384 the column pass's column-major intensity
 // (a group of g > 1 wavelengths holds fields for g rounded up to even: the packed passes
@@ -895,7 +898,8 @@ int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_
     if (rc) return rc;
     a.tw = kept ? static_cast<const dfc*>(kept) : tw_slot;
     float2* tw32_slot = c.take<float2>((size_t)p->n * 8);
-    a.work = c.take<dfc>((size_t)(p->n / 2 + 1) * p->n * 16);
+    a.work = c.take<dfc>((size_t)(p->n / 2) * (p->n + 4) * 16);
+    a.pairs = p->n >= kSplitN ? c.take<double2>((size_t)p->n * p->n * 8) : nullptr;
     a.phi = phi;
     const double nn = (double)p->n * p->n;
     if (!kept) SCINT_LAUNCH(K_TWIDDLES, 16.0 * p->n, 0.0, s, launch_twiddles_df(tw_slot, p->n, s));
@@ -904,7 +908,8 @@ int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_
     const double half = (double)(p->n / 2 + 1) * p->n * 16.0;
     // rows: the noise is generated in registers, rows 0..n/2 of the x-transformed field are written
     SCINT_LAUNCH(K_SYNTH_ROWS, half, (p->n / 2 + 1) * fft_flops(p->n), s, launch_synth_rows(a, s));
-    // columns: two real columns per complex transform
+    // columns: two real columns per complex transform (at n >= kSplitN through a column-major
+    // scratch and a transpose, timed with the pass)
     SCINT_LAUNCH(K_SYNTH_COLS, half + 8.0 * nn, (p->n / 2) * fft_flops(p->n), s, launch_synth_cols(a, s));
     return ok();
 }

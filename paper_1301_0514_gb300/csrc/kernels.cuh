@@ -42,8 +42,9 @@ struct SynthArgs {
     dfl out_scale_df;    // the same as a double-float
     const dfc* tw;       // double-float twiddles for n
     const float2* tw32;  // FP32 twiddles for n (the transforms of rows outside the FP64 square)
-    dfc* work;           // (n/2 + 1) x n double-float complex, row-major: rows ky = 0..n/2 after the x transform
+    dfc* work;           // rows ky = 0..n/2 after the x transform, n/2 strips of one column pair (n + 4 values each)
     double* phi;         // n*n, row-major
+    double2* pairs;      // n >= kSplitN: n*n doubles, the column pairs column-major before the transpose
 };
 cudaError_t launch_twiddles_df(dfc* tw, int n, cudaStream_t s);
 cudaError_t launch_synth_rows(const SynthArgs& a, cudaStream_t s);

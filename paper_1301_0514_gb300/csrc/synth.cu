@@ -11,7 +11,8 @@
 // Column pass: two real columns per complex transform: Z(ky) = G_a(ky) + i
 //   G_b(ky) over all ky (Hermitian extension), inverse transform along y, and
 //   phi_a = sqrt(2)/L^2 Re, phi_b = sqrt(2)/L^2 Im.
-// This halves the transform work and the intermediate (row-major, (N/2+1) x N).
+// This halves the transform work and the intermediate ((N/2+1) x N values, kept
+// column pair by column pair: synth_idx below).
 // The noise is never stored.
 //
 // Precision: the transforms run in double-float arithmetic (dfc: pairs of FP32
@@ -68,10 +69,25 @@ template <int N> __host__ __device__ constexpr int synth_cs() { return N >= kSpl
 template <int N> __host__ __device__ constexpr int synth_lines() { return N >= kTile64 ? 1 : (kTile64 / N < N ? kTile64 / N : N); }
 template <int N> __host__ __device__ constexpr int synth_threads() { return synth_lines<N>() * FftPlan<N>::T / synth_cs<N>(); }
 // column pass: complex lines (each two real output columns) per block, at most N/2
-template <int N> __host__ __device__ constexpr int synth_col_lines() { return synth_lines<N>() < N / 2 ? synth_lines<N>() : N / 2; }
+// (two at N = 4096, 139 KB of shared memory: 0.236 -> 0.201 ms per 4096^2 pass against one)
+template <int N> __host__ __device__ constexpr int synth_col_lines() {
+    return N == 4096 ? 2 : (synth_lines<N>() < N / 2 ? synth_lines<N>() : N / 2);
+}
 template <int N> __host__ __device__ constexpr int synth_col_threads() { return synth_col_lines<N>() * FftPlan<N>::T / synth_cs<N>(); }
 template <int N> constexpr size_t synth_smem() { return (size_t)synth_lines<N>() * FftPlan<N>::BUF * sizeof(dfc) / synth_cs<N>(); }
 template <int N> constexpr size_t synth_col_smem() { return (size_t)synth_col_lines<N>() * FftPlan<N>::BUF * sizeof(dfc) / synth_cs<N>(); }
+
+// The intermediate G(ky, x), ky = 0..N/2, is stored in strips of one column pair
+// p = x/2 (synth_strip<N>() values each), so that a column pass reads contiguous memory:
+// below the split size the rows follow each other (two values per row); at N >= kSplitN
+// the rows of each parity are grouped (N/4 + 1 rows each), since block r of a column
+// cluster reads the rows of parity r.  The row pass's stores are whole 32-byte sectors.
+template <int N> __host__ __device__ constexpr int synth_strip() { return N + 4; }
+template <int N> SCINT_DEV size_t synth_idx(int ky, int x) {
+    const size_t strip = (size_t)(x >> 1) * synth_strip<N>() + (x & 1);
+    if constexpr (N >= kSplitN) return strip + (size_t)(ky & 1) * (synth_strip<N>() / 2) + (size_t)(ky >> 1) * 2;
+    else return strip + (size_t)ky * 2;
+}
 
 template <int CS> SCINT_DEV int synth_rank() {
     if constexpr (CS == 1) return 0;
@@ -115,7 +131,7 @@ SCINT_DEV void synth_row32(const SynthArgs& a, int ky, bool live, int t, float2*
     fft_line_tr<float2, N, +1, 16, 1>(v, buf, t, tr);
     if (live) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) a.work[(size_t)ky * N + t + m * T] = widen(v[m]);
+        for (int m = 0; m < E; ++m) a.work[synth_idx<N>(ky, t + m * T)] = widen(v[m]);
     }
 }
 
@@ -155,7 +171,7 @@ synth_rows_kernel(SynthArgs a) {
     fft_line<dfc, N, +1, 16, 1, 0, CS>(v, buf, t, a.tw);
     if (live) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) a.work[(size_t)ky * N + t + m * T] = v[m];
+        for (int m = 0; m < E; ++m) a.work[synth_idx<N>(ky, t + m * T)] = v[m];
     }
     if constexpr (CS == 2) line_sync<CS>();
 }
@@ -176,7 +192,7 @@ synth_cols_kernel(SynthArgs a) {
     for (int m = 0; m < E; ++m) {
         const int ky = t + m * T;
         const bool lo = ky <= N / 2;
-        const dfc* g = a.work + (size_t)(lo ? ky : N - ky) * N + xa;
+        const dfc* g = a.work + synth_idx<N>(lo ? ky : N - ky, xa);
         const dfc ga = g[0], gb = g[1];
         // G(ky) = conj G(N - ky) above N/2; Z = G_a + i G_b
         const dfc za = lo ? ga : conjc(ga), zb = lo ? gb : conjc(gb);
@@ -214,7 +230,6 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_rows_split_
 #pragma unroll 1
     for (int ky = blockIdx.x / 2; ky <= N / 2; ky += gridDim.x / 2) {
         cluster_wait();
-        dfc* row = a.work + (size_t)ky * N;
         if (ky > a.low_k) {    // outside the FP64 square: FP32 transform (see synth_row32)
             float2* b32 = reinterpret_cast<float2*>(buf);
             float2 u[E];
@@ -227,8 +242,8 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_rows_split_
             __syncthreads();
             fft_line_tr<float2, H2, +1, 16, 1>(u, b32, t, tr);
             split_combine<float2, H2>(u, b32, t, r, a.tw32, [&](int, int n, float2 y0, float2 y1) {
-                row[n] = widen(y0);
-                row[n + H2] = widen(y1);
+                a.work[synth_idx<N>(ky, n)] = widen(y0);
+                a.work[synth_idx<N>(ky, n + H2)] = widen(y1);
             });
             continue;
         }
@@ -241,8 +256,8 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_rows_split_
         __syncthreads();
         fft_line<dfc, H2, +1, 16, 1, 0, 1, 2>(v, buf, t, a.tw);
         split_combine<dfc, H2>(v, buf, t, r, a.tw, [&](int, int n, dfc y0, dfc y1) {
-            row[n] = y0;
-            row[n + H2] = y1;
+            a.work[synth_idx<N>(ky, n)] = y0;
+            a.work[synth_idx<N>(ky, n + H2)] = y1;
         });
     }
     cluster_wait();
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_cols_split_
         for (int m = 0; m < E; ++m) {
             const int ky = 2 * (t + m * T) + r;
             const bool lo = ky <= N / 2;
-            const dfc* g = a.work + (size_t)(lo ? ky : N - ky) * N + xa;
+            const dfc* g = a.work + synth_idx<N>(lo ? ky : N - ky, xa);
             const dfc ga = g[0], gb = g[1];
             // G(ky) = conj G(N - ky) above N/2; Z = G_a + i G_b
             const dfc za = lo ? ga : conjc(ga), zb = lo ? gb : conjc(gb);
@@ -274,15 +289,30 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_cols_split_
         }
         cluster_wait();
         fft_line<dfc, H2, +1, 16, 1, 0, 1, 2>(v, buf, t, a.tw);
+        // the column pair goes out column-major (consecutive rows of a warp are consecutive 16-byte
+        // entries); pair_transpose_kernel puts it in place: row-major stores of one 16-byte pair
+        // per row had cost 2.6 of this pass's 6.9 ms at 16384^2
+        double2* col = a.pairs + (size_t)(xa / 2) * N;
         split_combine<dfc, H2>(v, buf, t, r, a.tw, [&](int, int n, dfc y0, dfc y1) {
-            // columns xa, xa + 1 (xa even): one 16-byte store per row
-            *reinterpret_cast<double2*>(a.phi + (size_t)n * N + xa) =
-                make_double2(scaled_to_double(y0.x, a.out_scale_df), scaled_to_double(y0.y, a.out_scale_df));
-            *reinterpret_cast<double2*>(a.phi + (size_t)(n + H2) * N + xa) =
-                make_double2(scaled_to_double(y1.x, a.out_scale_df), scaled_to_double(y1.y, a.out_scale_df));
+            col[n] = make_double2(scaled_to_double(y0.x, a.out_scale_df), scaled_to_double(y0.y, a.out_scale_df));
+            col[n + H2] = make_double2(scaled_to_double(y1.x, a.out_scale_df), scaled_to_double(y1.y, a.out_scale_df));
         });
     }
     cluster_wait();
+}
+
+// phi[y][2p + c] = pairs[p][y].{x, y}[c]: 32 pairs x 32 rows per block through shared memory
+// (reads along y and writes along x both coalesced); n is a multiple of 64
+__global__ void __launch_bounds__(256) pair_transpose_kernel(const double2* __restrict__ pairs, double* phi, int n) {
+    __shared__ double2 tile[32][33];
+    const int p0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+#pragma unroll
+    for (int k = ty; k < 32; k += 8) tile[k][tx] = pairs[(size_t)(p0 + k) * n + y0 + tx];   // [pair][y]
+    __syncthreads();
+#pragma unroll
+    for (int k = ty; k < 32; k += 8)
+        reinterpret_cast<double2*>(phi + (size_t)(y0 + k) * n)[p0 + tx] = tile[tx][k];
 }
 
 template <bool ROWS>
@@ -302,8 +332,12 @@ cudaError_t launch_synth_pass(const SynthArgs& a, cudaStream_t s) {
                 if ((e = active_clusters(k, 2, synth_split_threads<N>(), synth_split_smem<N>(), &nc)) != cudaSuccess)
                     return e;
                 const int lines = ROWS ? N / 2 + 1 : N / 2;
-                return launch_k(k, 2, dim3(2 * std::min(nc, lines)), dim3(synth_split_threads<N>()),
-                                synth_split_smem<N>(), s, a);
+                if (!ROWS && !a.pairs) return cudaErrorInvalidValue;
+                e = launch_k(k, 2, dim3(2 * std::min(nc, lines)), dim3(synth_split_threads<N>()),
+                             synth_split_smem<N>(), s, a);
+                if (e != cudaSuccess || ROWS) return e;
+                pair_transpose_kernel<<<dim3(N / 64, N / 32), 256, 0, s>>>(a.pairs, a.phi, N);
+                return cudaGetLastError();
             } else if (ROWS) {
                 if ((e = set_smem(synth_rows_kernel<N>, synth_smem<N>())) != cudaSuccess) return e;
                 const int rows = N / 2 + 1;
