@@ -137,10 +137,12 @@ size_t ws_prop(int n, int g) {
            (n >= kSplitN ? up((size_t)n * n * 4) : 0);
 }
 size_t ws_prop64(int n) { return n <= kMax64N ? up((size_t)n * 16) + up((size_t)n * n * 16) : 0; }
-size_t ws_smooth(int n) { return up((size_t)n * 8) + up((size_t)(n / 2 + 1) * n * 8); }
+size_t ws_smooth(int n) {
+    return up((size_t)n * 8) + up((size_t)(n / 2 + 1) * n * 8) + up(smooth_pairs_floats(n) * 4);
+}
 // adjoint: twiddles, g_I map, half spectrum for its disk filter, then the propagation group buffers
 size_t ws_adjoint(int n, int g) {
-    return up((size_t)n * n * 4) + up((size_t)(n / 2 + 1) * n * 8) + ws_prop(n, g);
+    return up((size_t)n * n * 4) + up((size_t)(n / 2 + 1) * n * 8) + up(smooth_pairs_floats(n) * 4) + ws_prop(n, g);
 }
 size_t ws_moments() { return up((size_t)kMomentBlocks * 2 * sizeof(double)); }
 
@@ -1145,6 +1147,7 @@ int scint_smooth_source(const scint_params* p, float* intensity, void* workspace
     a.radius_over_L = p->source_radius_km / screen_len(p);
     float2* tw_slot = c.take<float2>((size_t)p->n * 8);
     a.spec = c.take<float2>((size_t)(p->n / 2 + 1) * p->n * 8);
+    a.pairs = smooth_pairs_floats(p->n) ? c.take<float2>(smooth_pairs_floats(p->n) * 4) : nullptr;
     a.intensity = intensity;
     const int n = p->n;
     const double half = (double)(n / 2 + 1) * n * 8.0, nn = (double)n * n;
@@ -1294,6 +1297,7 @@ int scint_lightcurve_adjoint(const scint_params* p, const double* phi, const dou
     if (rc) return rc;
     float* gmap = c.take<float>((size_t)n * n * 4);
     float2* spec = c.take<float2>((size_t)(n / 2 + 1) * n * 8);
+    float2* spairs = smooth_pairs_floats(n) ? c.take<float2>(smooth_pairs_floats(n) * 4) : nullptr;
     Carver cp = c;                       // propagation buffers: twiddles, then group tables and fields
     const float2* tw = nullptr;
     rc = twiddles32(n, true, s, cp.take<float2>((size_t)n * 8), &tw);
@@ -1321,6 +1325,7 @@ int scint_lightcurve_adjoint(const scint_params* p, const double* phi, const dou
         sa.radius_over_L = p->source_radius_km / screen_len(p);
         sa.tw = tw;
         sa.spec = spec;
+        sa.pairs = spairs;
         sa.intensity = gmap;
         const double half = (double)(n / 2 + 1) * n * 8.0;
         SCINT_LAUNCH(K_SMOOTH_FWD, 4.0 * nn + half, (n / 2) * fft_flops(n), s, launch_smooth_pass(sa, 0, s));

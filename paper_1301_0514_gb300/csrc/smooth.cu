@@ -9,6 +9,7 @@
 #include "dispatch.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "pairs.cuh"
 
 namespace scint {
 
@@ -177,6 +178,12 @@ smooth_inv_cols_kernel(SmoothArgs a) {
 //   inverse column pass: block r reads the spectrum rows of its parity, inverse,
 //     decimation in time.
 // Grids are persistent: as many clusters as fit, each looping over lines.
+//   The map enters and leaves as column pairs (pairs.cuh: a.pairs, column-major, through
+//   tiled transposes), so that the column passes read and write consecutive 8-byte values:
+//   one 8-byte value per 64 KB row of the map had cost about half of their time (16384^2,
+//   measured without the map accesses: forward 1.87 -> 0.81 ms, inverse 2.18 -> 1.14 ms;
+//   with the transposes 1.41 and 1.53 ms).  The half spectrum stays row-major: in strips of
+//   four columns the column passes gained 0.25 ms each but the row pass lost 0.85 ms.
 template <int N> __host__ __device__ constexpr int ssplit_threads() { return FftPlan<N / 2>::T; }
 template <int N> constexpr size_t ssplit_smem() {
     return (size_t)(FftPlan<N / 2>::BUF + FftPlan<N / 2>::TWS) * sizeof(float2);
@@ -200,9 +207,8 @@ __global__ void __launch_bounds__(ssplit_threads<N>(), 1) smooth_fwd_cols_split_
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int e = t + m * T;
-            const float2 z0 = *reinterpret_cast<const float2*>(a.intensity + (size_t)e * N + xa);
-            const float2 z1 = *reinterpret_cast<const float2*>(a.intensity + (size_t)(e + H2) * N + xa);
-            v[m] = split_dif(z0, z1, r, e, a.tw);
+            const float2* col = a.pairs + (size_t)(xa / 2) * N;
+            v[m] = split_dif(col[e], col[e + H2], r, e, a.tw);
         }
         fft_line<float2, H2, -1, 16, 1, 1, 1>(v, buf, t, tws);     // v[m] = Z(2k + r), k = t + m T
 #pragma unroll
@@ -289,9 +295,10 @@ __global__ void __launch_bounds__(ssplit_threads<N>(), 1) smooth_inv_cols_split_
         }
         cluster_wait();
         fft_line<float2, H2, +1, 16, 1, 1, 1>(v, buf, t, tws);
+        float2* col = a.pairs + (size_t)(xa / 2) * N;
         split_combine<float2, H2>(v, buf, t, r, a.tw, [&](int, int n, float2 y0, float2 y1) {
-            *reinterpret_cast<float2*>(a.intensity + (size_t)n * N + xa) = y0;
-            *reinterpret_cast<float2*>(a.intensity + (size_t)(n + H2) * N + xa) = y1;
+            col[n] = y0;
+            col[n + H2] = y1;
         });
     }
     cluster_wait();
@@ -317,7 +324,11 @@ cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {
                 if ((e = set_smem(k, ssplit_smem<N>())) != cudaSuccess) return e;
                 if ((e = active_clusters(k, 2, ssplit_threads<N>(), ssplit_smem<N>(), &nc)) != cudaSuccess) return e;
                 const int lines = which == 1 ? N / 2 + 1 : N / 2;
-                return launch_k(k, 2, dim3(2 * std::min(nc, lines)), dim3(ssplit_threads<N>()), ssplit_smem<N>(), s, a);
+                if (!a.pairs) return cudaErrorInvalidValue;
+                if (which == 0 && (e = launch_rows_to_pairs(a.intensity, a.pairs, N, s)) != cudaSuccess) return e;
+                e = launch_k(k, 2, dim3(2 * std::min(nc, lines)), dim3(ssplit_threads<N>()), ssplit_smem<N>(), s, a);
+                if (e != cudaSuccess || which != 2) return e;
+                return launch_pairs_to_rows(a.pairs, a.intensity, N, s);
             } else {
             // every block (cluster) of the column passes holds W line pairs = 2W real columns
             const int col_blocks = N / (2 * scol_lines<N>()) * CS;

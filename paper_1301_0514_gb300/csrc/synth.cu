@@ -22,6 +22,7 @@
 #include "dispatch.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "pairs.cuh"
 #include "spectrum.cuh"
 
 namespace scint {
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_cols_split_
         cluster_wait();
         fft_line<dfc, H2, +1, 16, 1, 0, 1, 2>(v, buf, t, a.tw);
         // the column pair goes out column-major (consecutive rows of a warp are consecutive 16-byte
-        // entries); pair_transpose_kernel puts it in place: row-major stores of one 16-byte pair
+        // entries); a tiled transpose (pairs.cuh) puts it in place: row-major stores of one 16-byte pair
         // per row had cost 2.6 of this pass's 6.9 ms at 16384^2
         double2* col = a.pairs + (size_t)(xa / 2) * N;
         split_combine<dfc, H2>(v, buf, t, r, a.tw, [&](int, int n, dfc y0, dfc y1) {
@@ -299,20 +300,6 @@ __global__ void __launch_bounds__(synth_split_threads<N>(), 1) synth_cols_split_
         });
     }
     cluster_wait();
-}
-
-// phi[y][2p + c] = pairs[p][y].{x, y}[c]: 32 pairs x 32 rows per block through shared memory
-// (reads along y and writes along x both coalesced); n is a multiple of 64
-__global__ void __launch_bounds__(256) pair_transpose_kernel(const double2* __restrict__ pairs, double* phi, int n) {
-    __shared__ double2 tile[32][33];
-    const int p0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-#pragma unroll
-    for (int k = ty; k < 32; k += 8) tile[k][tx] = pairs[(size_t)(p0 + k) * n + y0 + tx];   // [pair][y]
-    __syncthreads();
-#pragma unroll
-    for (int k = ty; k < 32; k += 8)
-        reinterpret_cast<double2*>(phi + (size_t)(y0 + k) * n)[p0 + tx] = tile[tx][k];
 }
 
 template <bool ROWS>
@@ -336,8 +323,7 @@ cudaError_t launch_synth_pass(const SynthArgs& a, cudaStream_t s) {
                 e = launch_k(k, 2, dim3(2 * std::min(nc, lines)), dim3(synth_split_threads<N>()),
                              synth_split_smem<N>(), s, a);
                 if (e != cudaSuccess || ROWS) return e;
-                pair_transpose_kernel<<<dim3(N / 64, N / 32), 256, 0, s>>>(a.pairs, a.phi, N);
-                return cudaGetLastError();
+                return launch_pairs_to_rows(a.pairs, a.phi, N, s);
             } else if (ROWS) {
                 if ((e = set_smem(synth_rows_kernel<N>, synth_smem<N>())) != cudaSuccess) return e;
                 const int rows = N / 2 + 1;
