@@ -125,7 +125,7 @@ size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
 size_t ws_synth(int n) {
     return up((size_t)n * 16) + up((size_t)n * 8) + up((size_t)(n / 2) * (n + 4) * 16) +
-           (n >= kSplitN ? up((size_t)n * n * 8) : 0);
+           (n >= kSplitN ? up((size_t)n * n * 8) : 0) + (n <= kDrawN ? up((size_t)(n / 2 + 1) * n * 16) : 0);
 }
 // twiddles, the taper table per wavelength, one field per wavelength of the group, and at
 // n = 16384 the column pass's column-major intensity
@@ -621,7 +621,7 @@ double outer_phase_rms(double r_diff, double beta, double L, int K) {
 // 2.6e-7 rad); 256 when none does.  The FP32 bins' phase error scales with that rms.
 int fp64_square(const scint_params* p) {
     // up to 512^2 every bin is drawn in FP64 (the whole spectrum is the square; at most 2.6e5 bins)
-    if (p->n <= 512) return p->n / 2;
+    if (p->n <= kDrawN) return p->n / 2;
     static const double target = outer_phase_rms(30.0, 11.0 / 3.0, 40960.0, 256);
     const double L = screen_len(p);
     for (int K = 32; K < 256; K *= 2)
@@ -902,6 +902,7 @@ int scint_make_screen(const scint_params* p, double* phi, void* workspace, size_
     float2* tw32_slot = c.take<float2>((size_t)p->n * 8);
     a.work = c.take<dfc>((size_t)(p->n / 2) * (p->n + 4) * 16);
     a.pairs = p->n >= kSplitN ? c.take<double2>((size_t)p->n * p->n * 8) : nullptr;
+    a.drawn = p->n <= kDrawN ? c.take<dfc>((size_t)(p->n / 2 + 1) * p->n * 16) : nullptr;
     a.phi = phi;
     const double nn = (double)p->n * p->n;
     if (!kept) SCINT_LAUNCH(K_TWIDDLES, 16.0 * p->n, 0.0, s, launch_twiddles_df(tw_slot, p->n, s));

@@ -45,7 +45,9 @@ struct SynthArgs {
     dfc* work;           // rows ky = 0..n/2 after the x transform, n/2 strips of one column pair (n + 4 values each)
     double* phi;         // n*n, row-major
     double2* pairs;      // n >= kSplitN: n*n doubles, the column pairs column-major before the transpose
+    dfc* drawn;          // n <= kDrawN: the Hermitian bins of rows 0..n/2, row-major, drawn before the row pass
 };
+constexpr int kDrawN = 512;   // up to this size every bin is FP64 and the bins are drawn by their own kernel
 cudaError_t launch_twiddles_df(dfc* tw, int n, cudaStream_t s);
 cudaError_t launch_synth_rows(const SynthArgs& a, cudaStream_t s);
 cudaError_t launch_synth_cols(const SynthArgs& a, cudaStream_t s);

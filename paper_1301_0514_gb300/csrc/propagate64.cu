@@ -40,10 +40,14 @@ SCINT_DEV double2 transfer64(const Prop64Args& a, int i) {
 }
 
 template <int N> __host__ __device__ constexpr size_t p64_smem() { return (size_t)FftPlan<N>::BUF * sizeof(double2); }
+// values per thread: 8 up to N = 1024, so that a line has N/8 threads (at 256^2 sixteen values
+// per thread left less than one warp per SM on the FP64 pipe's latency)
+template <int N> __host__ __device__ constexpr int p64_ept() { return N <= 1024 ? 8 : 16; }
 
 template <int N>
-__global__ void __launch_bounds__(FftPlan<N>::T) prop64_rows_kernel(Prop64Args a) {
-    using Pl = FftPlan<N>;
+__global__ void __launch_bounds__(FftPlan<N, p64_ept<N>()>::T) prop64_rows_kernel(Prop64Args a) {
+    constexpr int EPT = p64_ept<N>();
+    using Pl = FftPlan<N, EPT>;
     constexpr int T = Pl::T, E = Pl::E;
     extern __shared__ double2 smem64[];
     const int y = blockIdx.x, t = threadIdx.x;
@@ -57,27 +61,28 @@ __global__ void __launch_bounds__(FftPlan<N>::T) prop64_rows_kernel(Prop64Args a
         const double w = sfy * taper64(x, N, a.margin_px);
         v[m] = make_double2(w * cs, w * sn);
     }
-    fft_line<double2, N, -1, 16, 1, 0>(v, smem64, t, a.tw);
+    fft_line<double2, N, -1, EPT, 1, 0>(v, smem64, t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer64(a, t + m * T));
-    fft_line<double2, N, +1, 16, 1, 0>(v, smem64, t, a.tw);
+    fft_line<double2, N, +1, EPT, 1, 0>(v, smem64, t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) a.field[(size_t)y * N + t + m * T] = v[m];
 }
 
 template <int N>
-__global__ void __launch_bounds__(FftPlan<N>::T) prop64_cols_kernel(Prop64Args a) {
-    using Pl = FftPlan<N>;
+__global__ void __launch_bounds__(FftPlan<N, p64_ept<N>()>::T) prop64_cols_kernel(Prop64Args a) {
+    constexpr int EPT = p64_ept<N>();
+    using Pl = FftPlan<N, EPT>;
     constexpr int T = Pl::T, E = Pl::E;
     extern __shared__ double2 smem64[];
     const int x = blockIdx.x, t = threadIdx.x;
     double2 v[E];
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = a.field[(size_t)(t + m * T) * N + x];
-    fft_line<double2, N, -1, 16, 1, 0>(v, smem64, t, a.tw);
+    fft_line<double2, N, -1, EPT, 1, 0>(v, smem64, t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer64(a, t + m * T));
-    fft_line<double2, N, +1, 16, 1, 0>(v, smem64, t, a.tw);
+    fft_line<double2, N, +1, EPT, 1, 0>(v, smem64, t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) a.intensity[(size_t)(t + m * T) * N + x] = v[m].x * v[m].x + v[m].y * v[m].y;
 }
@@ -91,9 +96,10 @@ cudaError_t launch_prop64(const Prop64Args& a, cudaStream_t s) {
             cudaError_t e = set_smem(prop64_rows_kernel<N>, p64_smem<N>());
             if (e == cudaSuccess) e = set_smem(prop64_cols_kernel<N>, p64_smem<N>());
             if (e != cudaSuccess) return e;
-            prop64_rows_kernel<N><<<N, FftPlan<N>::T, p64_smem<N>(), s>>>(a);
+            constexpr int T = FftPlan<N, p64_ept<N>()>::T;
+            prop64_rows_kernel<N><<<N, T, p64_smem<N>(), s>>>(a);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            prop64_cols_kernel<N><<<N, FftPlan<N>::T, p64_smem<N>(), s>>>(a);
+            prop64_cols_kernel<N><<<N, T, p64_smem<N>(), s>>>(a);
             return cudaGetLastError();
         }
     });

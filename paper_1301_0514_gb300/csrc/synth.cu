@@ -67,12 +67,19 @@ cudaError_t launch_twiddles64(double2* tw, int n, cudaStream_t s) {
 // Lines per block (all transformed together); N = 16384 lines (256 KB in
 // double-float) go to a cluster of two blocks (the split kernels below).
 template <int N> __host__ __device__ constexpr int synth_cs() { return N >= kSplitN ? 2 : 1; }
-template <int N> __host__ __device__ constexpr int synth_lines() { return N >= kTile64 ? 1 : (kTile64 / N < N ? kTile64 / N : N); }
+template <int N> __host__ __device__ constexpr int synth_tile_lines() { return N >= kTile64 ? 1 : (kTile64 / N < N ? kTile64 / N : N); }
+// Rows per row-pass block: the tile, but no more than leaves about two blocks per SM (the
+// N/2 + 1 rows over 304 blocks).  Up to N = 512 every bin is drawn in FP64, whose pipe is
+// narrow: at 256^2 sixteen rows per block had kept 9 SMs busy for 0.30 ms.
+template <int N> __host__ __device__ constexpr int synth_lines() {
+    constexpr int spread = (N / 2 + 1) / 304 > 1 ? (N / 2 + 1) / 304 : 1;
+    return synth_tile_lines<N>() < spread ? synth_tile_lines<N>() : spread;
+}
 template <int N> __host__ __device__ constexpr int synth_threads() { return synth_lines<N>() * FftPlan<N>::T / synth_cs<N>(); }
 // column pass: complex lines (each two real output columns) per block, at most N/2
 // (two at N = 4096, 139 KB of shared memory: 0.236 -> 0.201 ms per 4096^2 pass against one)
 template <int N> __host__ __device__ constexpr int synth_col_lines() {
-    return N == 4096 ? 2 : (synth_lines<N>() < N / 2 ? synth_lines<N>() : N / 2);
+    return N == 4096 ? 2 : (synth_tile_lines<N>() < N / 2 ? synth_tile_lines<N>() : N / 2);
 }
 template <int N> __host__ __device__ constexpr int synth_col_threads() { return synth_col_lines<N>() * FftPlan<N>::T / synth_cs<N>(); }
 template <int N> constexpr size_t synth_smem() { return (size_t)synth_lines<N>() * FftPlan<N>::BUF * sizeof(dfc) / synth_cs<N>(); }
@@ -136,6 +143,16 @@ SCINT_DEV void synth_row32(const SynthArgs& a, int ky, bool live, int t, float2*
     }
 }
 
+// Up to N = 512 every bin is drawn in FP64 on the narrow FP64 pipe; a row's team there has
+// only N/16 threads, so the Hermitian bins of rows 0..N/2 are drawn first, one per thread of
+// this kernel, into a.drawn (row-major), and the row pass reads them.
+__global__ void __launch_bounds__(256) synth_draw_kernel(SynthArgs a) {
+    const int n = a.n;
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= (n / 2 + 1) * n) return;
+    a.drawn[i] = hermitian_bin(a, i % n, i / n);
+}
+
 template <int N>
 __global__ void __launch_bounds__(synth_threads<N>())
 synth_rows_kernel(SynthArgs a) {
@@ -157,13 +174,19 @@ synth_rows_kernel(SynthArgs a) {
     dfc v[E];
     dfc* buf = smem_df + team * (Pl::BUF / CS);
     if constexpr (CS == 1) {
-        // the bins are drawn in a loop that is not unrolled (one copy of the Philox and
-        // Box-Muller code: unrolled sixteen times it overflowed the instruction cache) and
-        // staged in the line buffer, where each thread reads back its own entries
-#pragma unroll 1
-        for (int m = 0; m < E; ++m) buf[pad16(t + m * T)] = live ? hermitian_bin(a, t + m * T, ky) : make_c<dfc>(0.0, 0.0);
+        if (a.drawn) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = buf[pad16(t + m * T)];
+            for (int m = 0; m < E; ++m) v[m] = live ? a.drawn[(size_t)ky * N + t + m * T] : make_c<dfc>(0.0, 0.0);
+        } else {
+            // the bins are drawn in a loop that is not unrolled (one copy of the Philox and
+            // Box-Muller code: unrolled sixteen times it overflowed the instruction cache) and
+            // staged in the line buffer, where each thread reads back its own entries
+#pragma unroll 1
+            for (int m = 0; m < E; ++m)
+                buf[pad16(t + m * T)] = live ? hermitian_bin(a, t + m * T, ky) : make_c<dfc>(0.0, 0.0);
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = buf[pad16(t + m * T)];
+        }
     } else {
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = live ? hermitian_bin(a, t + m * T, ky) : make_c<dfc>(0.0, 0.0);
@@ -326,6 +349,11 @@ cudaError_t launch_synth_pass(const SynthArgs& a, cudaStream_t s) {
                 return launch_pairs_to_rows(a.pairs, a.phi, N, s);
             } else if (ROWS) {
                 if ((e = set_smem(synth_rows_kernel<N>, synth_smem<N>())) != cudaSuccess) return e;
+                if (a.drawn) {
+                    const int bins = (N / 2 + 1) * N;
+                    synth_draw_kernel<<<(bins + 255) / 256, 256, 0, s>>>(a);
+                    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                }
                 const int rows = N / 2 + 1;
                 return launch_k(synth_rows_kernel<N>, CS, dim3((rows + synth_lines<N>() - 1) / synth_lines<N>() * CS),
                                 dim3(synth_threads<N>()), synth_smem<N>(), s, a);
