@@ -91,6 +91,21 @@ SCINT_DEV dfl operator*(dfl a, dfl b) {
     return fast_two_sum(p, e);
 }
 SCINT_DEV double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+// a b + c d with one renormalisation: the two high products and their sum exactly (two
+// products by FMA, one two-sum), the cross terms and errors folded into the low word
+// (19 FP32 operations where two products and a sum take 25); the error stays of the
+// order of 2^-44 (|a b| + |c d|), the normwise bound a transform needs.
+SCINT_DEV dfl dot2(dfl a, dfl b, dfl c, dfl d) {
+    const float p = a.hi * b.hi, q = c.hi * d.hi;
+    const float ep = fmaf(a.hi, b.hi, -p), eq = fmaf(c.hi, d.hi, -q);
+    const dfl s = two_sum(p, q);
+    float lo = s.lo + ep + eq;
+    lo = fmaf(a.hi, b.lo, lo);
+    lo = fmaf(a.lo, b.hi, lo);
+    lo = fmaf(c.hi, d.lo, lo);
+    lo = fmaf(c.lo, d.hi, lo);
+    return fast_two_sum(s.hi, lo);
+}
 
 // float -> double from the bits, with integer instructions only (exact for normal numbers
 // and zero; a subnormal float, below 1.2e-38, becomes 0; no inf or NaN arises here)
@@ -115,8 +130,8 @@ struct __align__(16) dfc {
 };
 SCINT_DEV dfc operator+(dfc a, dfc b) { return dfc{a.x + b.x, a.y + b.y}; }
 SCINT_DEV dfc operator-(dfc a, dfc b) { return dfc{a.x - b.x, a.y - b.y}; }
-SCINT_DEV dfc cmul(dfc a, dfc b) { return dfc{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
-SCINT_DEV dfc cmulc(dfc a, dfc b) { return dfc{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }
+SCINT_DEV dfc cmul(dfc a, dfc b) { return dfc{dot2(a.x, b.x, -a.y, b.y), dot2(a.x, b.y, a.y, b.x)}; }
+SCINT_DEV dfc cmulc(dfc a, dfc b) { return dfc{dot2(a.x, b.x, a.y, b.y), dot2(a.y, b.x, -a.x, b.y)}; }
 SCINT_DEV dfc conjc(dfc a) { return dfc{a.x, -a.y}; }
 template <int DIR> SCINT_DEV dfc mul_i(dfc a) { return DIR > 0 ? dfc{-a.y, a.x} : dfc{a.y, -a.x}; }
 template <> struct real_of<dfc> { using type = dfl; };

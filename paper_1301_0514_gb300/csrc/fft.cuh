@@ -22,6 +22,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -67,10 +68,14 @@ SCINT_DEV C rot16(C a) {
     } else {
         constexpr Rl c = (Rl)cos16(j);
         constexpr Rl s = (Rl)(DIR * cos16(j - 4));
-        C r;
-        r.x = a.x * c - a.y * s;
-        r.y = a.x * s + a.y * c;
-        return r;
+        if constexpr (std::is_same<C, dfc>::value) {
+            return cmul(a, dfc{c, s});
+        } else {
+            C r;
+            r.x = a.x * c - a.y * s;
+            r.y = a.x * s + a.y * c;
+            return r;
+        }
     }
 }
 
