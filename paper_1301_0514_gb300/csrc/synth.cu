@@ -1,4 +1,5 @@
-// FP64 phase-screen synthesis (Sect. 3.1, Eq. spectre, Eq. densite).
+// Phase-screen synthesis (Sect. 3.1, Eq. spectre, Eq. densite), to FP64 accuracy where
+// the phase variance lies.
 //
 // phi = sqrt(2)/L^2 Re sum_k F_k e^{+2 pi i k.x}; the real part of the inverse
 // transform of F equals the inverse transform of its Hermitian part
@@ -13,12 +14,14 @@
 //   phi_a = sqrt(2)/L^2 Re, phi_b = sqrt(2)/L^2 Im.
 // This halves the transform work and the intermediate ((N/2+1) x N values, kept
 // column pair by column pair: synth_idx below).
-// The noise is never stored.
+// The noise is never stored, except up to N = 512, where the bins are drawn by a kernel of
+// their own before the row pass (synth_draw_kernel).
 //
 // Precision: the transforms run in double-float arithmetic (dfc: pairs of FP32
 // numbers, ~44 significant bits; common.cuh) on the FP32 pipes, which on GB300
-// are 64 times wider than the FP64 pipe; the low bins are drawn in FP64 and
-// the phase is written in FP64.
+// are 64 times wider than the FP64 pipe, except the x transforms of the rows
+// outside the FP64 square (synth_row32), which run in FP32; the low bins are
+// drawn in FP64 and the phase is written in FP64.
 #include "dispatch.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
