@@ -507,16 +507,16 @@ def run_ours(args):
     # propagation pass (48 for the pair), 24 B per pixel for the smoothing, 40 B per pixel for
     # the synthesis (a three-pass design's minimal traffic)
     px = sum(p.n * p.n for p in P)
-    survey_step_bytes = 48.0 * units + 24.0 * sum(p.n * p.n for p in P if p.source_radius_km > 0) + 40.0 * px
+    plan_step_bytes = 48.0 * units + 24.0 * sum(p.n * p.n for p in P if p.source_radius_km > 0) + 40.0 * px
     dom_px_lambda = units / max(1, dom["launches"]) if dom_name in ("prop_rows", "prop_cols") else None
-    survey = {"step_bytes": survey_step_bytes, "step_GBps": survey_step_bytes / (ms * 1e-3) / 1e9,
-              "step_frac": survey_step_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
-              "note": "planning bytes: 48 B per pixel-wavelength for propagation, 24 B/px smoothing, "
-                      "40 B/px synthesis; the two-pass kernels move 16 B per pixel-wavelength"}
+    planning = {"step_bytes": plan_step_bytes, "step_GBps": plan_step_bytes / (ms * 1e-3) / 1e9,
+                "step_frac": plan_step_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
+                "note": "planning bytes: 48 B per pixel-wavelength for propagation, 24 B/px smoothing, "
+                        "40 B/px synthesis; the two-pass kernels move 16 B per pixel-wavelength"}
     if dom_px_lambda is not None:
         kb = 24.0 * dom_px_lambda / (per_launch_ms * 1e-3) / 1e9
-        survey.update({"kernel_bytes_per_px_lambda": 24.0, "kernel_GBps": kb, "kernel_frac": kb / hbm_peak})
-    roof["survey_bytes_hbm"] = survey
+        planning.update({"kernel_bytes_per_px_lambda": 24.0, "kernel_GBps": kb, "kernel_frac": kb / hbm_peak})
+    roof["planning_bytes_hbm"] = planning
     launches = sum(v["launches"] for v in kstats.values())
     kernels = {k: {"launches": v["launches"], "ms": v["total_ms"], "share": v["total_ms"] / ms_serial,
                    "GBps": v["bytes"] / max(v["total_ms"], 1e-9) / 1e6,
