@@ -7,6 +7,8 @@ transforms run on every host core):
   * 4096^2, 10 km pixels, R_diff in {30, 100, 300} km, 500 nm, point source,
     64 tracks of 2048 samples: phase screen, intensity map, curves, m of the
     map's fiducial zone and of every curve;
+  * 8192^2, 5 km pixels, R_diff = 100 km, Kolmogorov, a disk of one R_ref,
+    16 tracks of 4096 samples (the largest lines that are not split);
   * 16384^2, 5 km pixels, R_diff = 100 km: beta = 3.67 with a disk of one
     R_ref and beta = 3.3 with a point source, 16 tracks of 8192 samples;
   * the gradient of a light-curve misfit at 16384^2 (two wavelengths, disk
@@ -82,6 +84,13 @@ def test_single_screen_4096_whole_map(r_diff):
     """4096^2, R_diff in {30, 100, 300} km: the R_diff = 30 km screen has phases of ~60 rad rms."""
     it = W.single_screens_4096(r_diffs=(30.0, 100.0, 300.0))[(30.0, 100.0, 300.0).index(r_diff)]
     _forward_parity(it, f"4096^2 R_diff {r_diff:g} km")
+
+
+def test_screen_8192_whole_map():
+    """8192^2, 5 km pixels, Kolmogorov, a disk of one R_ref: the largest unsplit lines (one
+    512-thread block per line in every pass), used by the modulation-index sweeps."""
+    it = W.large_screen_16384(beta=11.0 / 3.0, disk=True, n=8192)
+    _forward_parity(it, "8192^2 Kolmogorov disk")
 
 
 @pytest.mark.parametrize("beta,disk", [(3.67, True), (3.3, False)])
