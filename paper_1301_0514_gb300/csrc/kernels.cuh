@@ -136,10 +136,12 @@ struct SmoothArgs {
     const float2* tw;
     float2* spec;            // (n/2 + 1) x n complex64, row-major [ky][x]
     float* intensity;        // n*n in/out
-    float2* pairs;           // n >= kSplitN: n*n floats, the map as column pairs (pairs.cuh)
+    float2* pairs;           // n >= kSmoothPairsN: n*n floats, the map as column pairs (pairs.cuh)
 };
-// floats of the smoothing's column-pair scratch
-__host__ __device__ constexpr size_t smooth_pairs_floats(int n) { return n >= kSplitN ? (size_t)n * n : 0; }
+// From this size a smoothing column block holds one column pair, and the map enters and
+// leaves the column passes as column pairs (pairs.cuh); floats of that scratch:
+constexpr int kSmoothPairsN = 8192;
+__host__ __device__ constexpr size_t smooth_pairs_floats(int n) { return n >= kSmoothPairsN ? (size_t)n * n : 0; }
 // which = 0: forward column pass, 1: row pass, 2: inverse column pass
 cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s);
 

@@ -20,7 +20,9 @@ template <int N> __host__ __device__ constexpr int scs() { return N >= kSplitN ?
 // scattered sector requests, not latency (two 512-thread blocks per SM were slower).  Measured
 // against two pairs per block: 4096^2 forward 79 -> 66 us, inverse 91 -> 62 us; 2048^2 19 -> 16,
 // 18.5 -> 15 us.
-template <int N> __host__ __device__ constexpr int scol_lines() { return N >= 8192 ? 1 : (16384 / N < N / 2 ? 16384 / N : N / 2); }
+// From N = kSmoothPairsN (8192) a block holds one pair, and the map is read and written as
+// column pairs through the transposes of pairs.cuh (one 8-byte value per row otherwise).
+template <int N> __host__ __device__ constexpr int scol_lines() { return N >= kSmoothPairsN ? 1 : (16384 / N < N / 2 ? 16384 / N : N / 2); }
 template <int N> __host__ __device__ constexpr int scol_threads() { return scol_lines<N>() * FftPlan<N>::T / scs<N>(); }
 template <int N> __host__ __device__ constexpr int srow_lines() { return N >= kTileRow32 ? 1 : (kTileRow32 / N < N / 2 ? kTileRow32 / N : N / 2); }
 template <int N> __host__ __device__ constexpr int srow_threads() { return srow_lines<N>() * FftPlan<N>::T / scs<N>(); }
@@ -51,9 +53,16 @@ smooth_fwd_cols_kernel(SmoothArgs a) {
     if constexpr (TWM == 1) fill_twiddle_table<float2, N>(tws, a.tw, threadIdx.x, blockDim.x);
     const float2* twp = TWM == 1 ? tws : a.tw;
     float2 v[E];
+    if constexpr (N >= kSmoothPairsN) {
+        // one pair per block: the map as column pairs (consecutive rows, consecutive 8-byte values)
+        static_assert(W == 1 && CS == 1, "column pairs with one pair per unsplit block");
 #pragma unroll
-    for (int m = 0; m < E; ++m)
-        v[m] = *reinterpret_cast<const float2*>(a.intensity + (size_t)(t + m * T) * N + xa);
+        for (int m = 0; m < E; ++m) v[m] = a.pairs[(size_t)(xa / 2) * N + t + m * T];
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            v[m] = *reinterpret_cast<const float2*>(a.intensity + (size_t)(t + m * T) * N + xa);
+    }
     line_sync<CS>();
     fft_line<float2, N, -1, 16, W, TWM, CS>(v, buf, t, twp);
     // Z[N-k] lives in another thread: go through shared memory (natural order)
@@ -160,9 +169,14 @@ smooth_inv_cols_kernel(SmoothArgs a) {
     const float2* twp = TWM == 1 ? tws : a.tw;
     line_sync<CS>();
     fft_line<float2, N, +1, 16, W, TWM, CS>(v, smem32 + w, t, twp);
+    if constexpr (N >= kSmoothPairsN) {
 #pragma unroll
-    for (int m = 0; m < E; ++m)
-        *reinterpret_cast<float2*>(a.intensity + (size_t)(t + m * T) * N + xa) = v[m];
+        for (int m = 0; m < E; ++m) a.pairs[(size_t)(xa / 2) * N + t + m * T] = v[m];
+    } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            *reinterpret_cast<float2*>(a.intensity + (size_t)(t + m * T) * N + xa) = v[m];
+    }
     if constexpr (CS == 2) line_sync<CS>();
 }
 
@@ -332,8 +346,10 @@ cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {
             } else {
             // every block (cluster) of the column passes holds W line pairs = 2W real columns
             const int col_blocks = N / (2 * scol_lines<N>()) * CS;
+            if (N >= kSmoothPairsN && !a.pairs) return cudaErrorInvalidValue;
             if (which == 0) {
                 if ((e = set_smem(smooth_fwd_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
+                if (N >= kSmoothPairsN && (e = launch_rows_to_pairs(a.intensity, a.pairs, N, s)) != cudaSuccess) return e;
                 return launch_k(smooth_fwd_cols_kernel<N>, CS, dim3(col_blocks), dim3(scol_threads<N>()), scol_smem<N>(), s, a);
             } else if (which == 1) {
                 if ((e = set_smem(smooth_rows_kernel<N>, srow_smem<N>())) != cudaSuccess) return e;
@@ -342,7 +358,9 @@ cudaError_t launch_smooth_pass(const SmoothArgs& a, int which, cudaStream_t s) {
                                 dim3(srow_threads<N>()), srow_smem<N>(), s, a);
             } else {
                 if ((e = set_smem(smooth_inv_cols_kernel<N>, scol_smem<N>())) != cudaSuccess) return e;
-                return launch_k(smooth_inv_cols_kernel<N>, CS, dim3(col_blocks), dim3(scol_threads<N>()), scol_smem<N>(), s, a);
+                e = launch_k(smooth_inv_cols_kernel<N>, CS, dim3(col_blocks), dim3(scol_threads<N>()), scol_smem<N>(), s, a);
+                if (e != cudaSuccess || N < kSmoothPairsN) return e;
+                return launch_pairs_to_rows(a.pairs, a.intensity, N, s);
             }
             }
         }
