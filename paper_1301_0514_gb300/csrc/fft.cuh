@@ -146,6 +146,92 @@ SCINT_DEV void dft(C* x) {
     }
 }
 
+// ---- radix 16 in FP32 with the twiddle products fused into the butterflies ----
+// A radix-4 butterfly whose second and fourth inputs carry a twiddle (a0 + a2 w2,
+// a0 - a2 w2, ...) takes the product into the sum by FMAs: y + x w in four FMAs and
+// the difference as 2 y - (y + x w) in two, where a product then a sum and a difference
+// take eight.  In a radix-16 butterfly this applies to the external twiddles of the
+// first layer (stages after the first) and to the internal W16 rotations of the second,
+// 26 of its ~290 instructions.  The rounding differs from the plain form only in
+// the order of the operations.
+SCINT_DEV float2 cfma(float2 x, float2 w, float2 y) {     // y + x w
+    return make_float2(fmaf(x.x, w.x, fmaf(-x.y, w.y, y.x)), fmaf(x.x, w.y, fmaf(x.y, w.x, y.y)));
+}
+SCINT_DEV float2 twice_minus(float2 a, float2 b) {       // 2 a - b
+    return make_float2(fmaf(2.0f, a.x, -b.x), fmaf(2.0f, a.y, -b.y));
+}
+// the factor rot16<J16, DIR> multiplies by, as a complex number
+template <int J16, int DIR> SCINT_DEV float2 rot16_w() {
+    return make_float2((float)cos16(J16), (float)(DIR * cos16(J16 - 4)));
+}
+// external twiddle of the stage: x W^rk for the forward transform, x conj(W^rk) for the inverse
+template <int DIR> SCINT_DEV float2 tw_w(float2 w) { return DIR < 0 ? w : conjc(w); }
+
+// the radix-16 butterfly of dft<16, DIR> on x[r] w[r] (w[0] = 1; TW = false: no external twiddles)
+template <int DIR, bool TW>
+SCINT_DEV void dft16_fused(float2* x, const float2* w) {
+    // first layer over n2 for each n1 (n = n1 + 4 n2): inputs x[n1 + 4 n2] (times w[n1 + 4 n2])
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+        float2 t0, t1, t2, d;
+        if constexpr (TW) {
+            const float2 a0 = n1 == 0 ? x[0] : cmul(x[n1], tw_w<DIR>(w[n1]));
+            const float2 a1 = cmul(x[n1 + 4], tw_w<DIR>(w[n1 + 4]));
+            t0 = cfma(x[n1 + 8], tw_w<DIR>(w[n1 + 8]), a0);
+            t1 = twice_minus(a0, t0);
+            t2 = cfma(x[n1 + 12], tw_w<DIR>(w[n1 + 12]), a1);
+            d = twice_minus(a1, t2);
+        } else {
+            t0 = x[n1] + x[n1 + 8];
+            t1 = x[n1] - x[n1 + 8];
+            t2 = x[n1 + 4] + x[n1 + 12];
+            d = x[n1 + 4] - x[n1 + 12];
+        }
+        const float2 t3 = mul_i<DIR>(d);
+        x[n1] = t0 + t2;
+        x[n1 + 8] = t0 - t2;
+        x[n1 + 4] = t1 + t3;
+        x[n1 + 12] = t1 - t3;
+    }
+    // second layer over n1 for each k2: inputs x[4 k2 + n1] W16^(n1 k2)
+    {   // k2 = 0: no rotation
+        const float2 t0 = x[0] + x[2], t1 = x[0] - x[2], t2 = x[1] + x[3];
+        const float2 t3 = mul_i<DIR>(x[1] - x[3]);
+        x[0] = t0 + t2; x[2] = t0 - t2; x[1] = t1 + t3; x[3] = t1 - t3;
+    }
+    {   // k2 = 1: W^1, W^2, W^3
+        const float2 t0 = cfma(x[6], rot16_w<2, DIR>(), x[4]);
+        const float2 t1 = twice_minus(x[4], t0);
+        const float2 a1 = rot16<1, DIR>(x[5]);
+        const float2 t2 = cfma(x[7], rot16_w<3, DIR>(), a1);
+        const float2 t3 = mul_i<DIR>(twice_minus(a1, t2));
+        x[4] = t0 + t2; x[6] = t0 - t2; x[5] = t1 + t3; x[7] = t1 - t3;
+    }
+    {   // k2 = 2: W^2, W^4 (a quarter turn), W^6
+        const float2 b2 = rot16<4, DIR>(x[10]);
+        const float2 t0 = x[8] + b2, t1 = x[8] - b2;
+        const float2 a1 = rot16<2, DIR>(x[9]);
+        const float2 t2 = cfma(x[11], rot16_w<6, DIR>(), a1);
+        const float2 t3 = mul_i<DIR>(twice_minus(a1, t2));
+        x[8] = t0 + t2; x[10] = t0 - t2; x[9] = t1 + t3; x[11] = t1 - t3;
+    }
+    {   // k2 = 3: W^3, W^6, W^9
+        const float2 t0 = cfma(x[14], rot16_w<6, DIR>(), x[12]);
+        const float2 t1 = twice_minus(x[12], t0);
+        const float2 a1 = rot16<3, DIR>(x[13]);
+        const float2 t2 = cfma(x[15], rot16_w<9, DIR>(), a1);
+        const float2 t3 = mul_i<DIR>(twice_minus(a1, t2));
+        x[12] = t0 + t2; x[14] = t0 - t2; x[13] = t1 + t3; x[15] = t1 - t3;
+    }
+    float2 y[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) y[4 * k1 + k2] = x[k1 + 4 * k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = y[i];
+}
+
 // ---- plan ----------------------------------------------------------------
 // EPT = values held per thread (8, 16 or 32); each stage's butterflies are spread
 // over the T = N/E threads of the line, E/R butterflies per thread.  The stages
@@ -360,6 +446,21 @@ SCINT_DEV void fft_stage(C (&v)[FftPlan<N, EPT>::E], C* buf, int t, const C* __r
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int i = t + b * T;
+        if constexpr (std::is_same<C, float2>::value && R == 16) {
+            C w[R];
+            if constexpr (!FIRST) {
+                const int k = i & (P - 1);
+                if constexpr (TWM == 2) {
+                    twiddle_powers<R>(tr->w[S][b][0], tr->w[S][b][1], w);
+                } else {
+#pragma unroll
+                    for (int r = 1; r < R; ++r)
+                        w[r] = TWM == 1 ? tw[Pl::twoff(S) + k * (R - 1) + (r - 1)] : ld_tw(tw + r * k * (N / (P * R)) * TS);
+                }
+            }
+            dft16_fused<DIR, !FIRST>(&u[b * R], w);
+            continue;
+        }
         if constexpr (!FIRST) {
             const int k = i & (P - 1);
             if constexpr (TWM == 2) {
