@@ -139,8 +139,9 @@ size_t scint_workspace_bytes(const scint_params* p, int n_lambda);
  * oracle the screen agrees to better than 2e-6 rad (the measured worst cases are
  * stated with the tests of the full-size workloads).
  *   phi   device, N*N doubles, written; 16-byte aligned (SCINT_EINVAL otherwise).
- * Needs workspace (about 8 N^2 bytes: (N/2 + 1) N double-float values and the
- * twiddle tables).
+ * Needs workspace (scint_workspace_bytes): about 8 N^2 bytes for (N/2 + 1) N
+ * double-float values and the twiddle tables, 16 N^2 at N = 16384 (the column
+ * pairs before their transpose) and up to N = 512 (the drawn bins).
  */
 int scint_make_screen(const scint_params* p, double* phi,
                       void* workspace, size_t workspace_bytes, void* stream);
@@ -282,7 +283,8 @@ double scint_conjugate_pixel_km(const scint_params* p, double lambda_nm);
  * pixel k samples pattern l bilinearly (periodic, like the discrete transform)
  * at (k - N/2) lambda_nm/lambda_l + N/2 of its pixels, and
  *   intensity (+)= sum_l w_l h_l(resampled).
- * Arguments as scint_sum_passband.  Workspace: ws_prop plus 4 N^2 bytes per
+ * Arguments as scint_sum_passband.  Workspace: that of the transfer-function
+ * passband plus 4 N^2 bytes per
  * wavelength of a group (smaller workspaces give smaller groups).
  */
 int scint_sum_passband_conjugate(const scint_params* p, const double* phi,
