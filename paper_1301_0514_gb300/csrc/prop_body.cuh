@@ -39,7 +39,9 @@ SCINT_DEV void prop_rows_body(const PropArgs& a, int bid, int tid, float2* smem3
         const unsigned long long S = a.lam.scale_fx[l];
         // the taper from its table; H_x from a scalar (its phase exact in fixed-point turns)
         const float* sf = a.sf + (size_t)l * N;
-        const float sfy = sf[y];
+        // the inverse transform's 1/N rides on the taper of the row (a power of two: exact, so the
+        // field equals that of H/N applied after the forward transform, bit for bit)
+        const float sfy = CONJ ? sf[y] : sf[y] * (1.0f / N);
         float2 v[E];
         if constexpr (CONJ) {
             // G = SF SF exp(i (phi s + |x_1|^2 / 2 R_F^2)) (-1)^(x + y), Eq. Gxy
@@ -59,7 +61,7 @@ SCINT_DEV void prop_rows_body(const PropArgs& a, int bid, int tid, float2* smem3
         if constexpr (!CONJ) {
             const unsigned long long hc = a.lam.h_fx[l];
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
+            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_phasor(hc, t + m * T, N));
             if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, +1, 16, 1, SUB>(v, buf, buf1, t, tr);
             else if constexpr (PP) fft_line_pp<float2, N, +1, 16, 1, TWM, SUB>(v, buf, buf1, t, twp);
             else if constexpr (TWM == 2) fft_line_tr<float2, N, +1, 16, 1, 1, SUB>(v, buf, t, tr);
@@ -124,13 +126,14 @@ SCINT_DEV void prop_cols_body(const PropArgs& a, int bid, int tid, float2* smem3
         } else {
             const unsigned long long hc = a.lam.h_fx[l];
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_at(hc, t + m * T, N));
+            for (int m = 0; m < E; ++m) v[m] = cmul(v[m], transfer_phasor(hc, t + m * T, N));
             if constexpr (PP && TWM == 2) fft_line_tr_pp<float2, N, +1, kColEPT, W, SUB>(v, buf, buf1, t, tr);
             else if constexpr (PP) fft_line_pp<float2, N, +1, kColEPT, W, TWM, SUB>(v, buf, buf1, t, twp);
             else if constexpr (TWM == 2) fft_line_tr<float2, N, +1, kColEPT, W, 1, SUB>(v, buf, t, tr);
             else fft_line<float2, N, +1, kColEPT, W, TWM, 1, 1, SUB>(v, buf, t, twp);
         }
-        const float wl = a.lam.weight[l];
+        // the 1/N of H_y, squared, rides on the weight (powers of two: the sums are unchanged bit for bit)
+        const float wl = a.lam.weight[l] * (1.0f / ((float)N * (float)N));
 #pragma unroll
         for (int m = 0; m < E; ++m) acc[m] = fmaf(wl, fmaf(v[m].x, v[m].x, v[m].y * v[m].y), acc[m]);
     }

@@ -100,12 +100,14 @@ SCINT_DEV float2 unit_phasor(long long P, unsigned long long S, unsigned long lo
     return make_float2(cs, sn);
 }
 
-// H_x(k)/n = exp(-i pi lambda z k^2)/n at FFT index i, from C = frac(-lambda z / 2L^2) 2^64:
+// H_x(k) = exp(-i pi lambda z k^2) at FFT index i, from C = frac(-lambda z / 2L^2) 2^64:
 // the phase C m^2 mod 2^64 (m the signed frequency index) is exact in fixed-point turns.
-SCINT_DEV float2 transfer_at(unsigned long long C, int i, int n) {
+SCINT_DEV float2 transfer_phasor(unsigned long long C, int i, int n) {
     const long long m = sfreq(i, n);
-    return unit_phasor(0, 0ull, C * (unsigned long long)(m * m)) * (1.0f / n);
+    return unit_phasor(0, 0ull, C * (unsigned long long)(m * m));
 }
+// H_x(k)/n (the inverse transform's normalisation)
+SCINT_DEV float2 transfer_at(unsigned long long C, int i, int n) { return transfer_phasor(C, i, n) * (1.0f / n); }
 
 // One-FFT mode: chirp |x_1|^2 / (2 R_F^2) with x_1 = (i - n/2) Delta in fixed-point
 // turns, C (i - n/2)^2 mod 2^64 (exact), plus half a turn for odd i: the factor
