@@ -11,7 +11,8 @@ Every function states the passage of the paper it follows.  Arithmetic is
 IEEE double precision throughout; the 2D FFT of scipy.fft (pocketfft, the same
 library numpy's FFT is built on) serves as a library primitive through fft2 and
 ifft2 below (its sign and scaling conventions are pinned against a direct DFT
-and against the oracle's own radix-2 transform, fft_radix2, in the tests).
+and against the oracle's own radix-2 transform, fft_radix2, in the tests);
+numpy's 1D real FFT serves the periodogram.
 FFT_WORKERS sets how many host threads one transform may use (1 by default;
 the full-size tests raise it to the host's core count).  Where the paper is silent or ambiguous the reading taken here is
 named in the docstring ("Reading Rn").
